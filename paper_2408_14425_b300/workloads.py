@@ -1,0 +1,121 @@
+"""Seeded synthetic inputs for the radiance-cascade solver.
+
+This module holds input generators only -- none of the method's arithmetic.
+It serves both the CUDA path and the FP64 oracle, which import nothing from
+each other.  Every generator is deterministic in its seed and returns numpy
+arrays laid out [n_lambda][nz][nx] (x fastest).
+
+Recipes (the paper's own MHD snapshot is not available, so these synthetic
+fields stand in for it):
+
+* ``disc_field``: 64x64 unit voxels, background chi = 1e-2, eta = 0; a central
+  disc of radius 8 voxels (cells whose centre lies within the radius) with
+  chi = 1, eta = 1 (source function 1).
+* ``grf_fields``: per wavelength two independent 2D Gaussian random fields
+  with a k^-5/3 power spectrum (white noise -> FFT -> amplitude |k|^-5/6,
+  k = 0 removed -> inverse FFT), each min-max mapped: log10 chi to [-6, 2]
+  and log10 S to [-1, 1]; eta = S chi.  Seeds 1000 + l (chi) and 2000 + l (S)
+  for wavelength l of a single domain; ``seed_base`` offsets both for the
+  batched multi-domain workload.
+* ``opaque_disc_field`` / ``thin_disc_field``: the circle tests of Sec. 2.5 and
+  the optically thin disc with a closed-form J.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+
+def disc_field(n: int = 64, radius: float = 8.0, chi_bg: float = 1e-2,
+               chi_disc: float = 1.0, eta_disc: float = 1.0):
+    """Disc of radius `radius` (cell centres inside) in a weakly absorbing background."""
+    c = n / 2.0
+    x = np.arange(n) + 0.5
+    X, Z = np.meshgrid(x, x)
+    inside = (X - c) ** 2 + (Z - c) ** 2 <= radius ** 2
+    chi = np.full((n, n), chi_bg, dtype=np.float64)
+    eta = np.zeros((n, n), dtype=np.float64)
+    chi[inside] = chi_disc
+    eta[inside] = eta_disc
+    return chi[None].astype(np.float32), eta[None].astype(np.float32)
+
+
+def opaque_disc_field(n: int, radius: float, chi_disc: float = 1e2, source: float = 1.0):
+    """Opaque emissive disc in vacuum (cells whose centre is inside; Sec. 2.5 circle test)."""
+    c = n / 2.0
+    x = np.arange(n) + 0.5
+    X, Z = np.meshgrid(x, x)
+    inside = (X - c) ** 2 + (Z - c) ** 2 <= radius ** 2
+    chi = np.zeros((n, n))
+    eta = np.zeros((n, n))
+    chi[inside] = chi_disc
+    eta[inside] = chi_disc * source
+    return chi, eta
+
+
+def thin_disc_field(n: int, radius: float, chi_disc: float = 1e-9, eta_disc: float = 1.0,
+                    supersample: int = 16):
+    """Optically thin emitting disc in vacuum with per-cell area coverage (anti-aliased)."""
+    c = n / 2.0
+    s = supersample
+    sub = (np.arange(n * s) + 0.5) / s
+    X, Z = np.meshgrid(sub, sub)
+    inside = ((X - c) ** 2 + (Z - c) ** 2 <= radius ** 2).astype(np.float64)
+    cov = inside.reshape(n, s, n, s).mean(axis=(1, 3))
+    chi = chi_disc * cov
+    eta = eta_disc * cov
+    return chi, eta
+
+
+def grf(nx: int, nz: int, seed: int, slope: float = -5.0 / 3.0) -> np.ndarray:
+    """Zero-mean 2D Gaussian random field with power spectrum ~ |k|^slope."""
+    rng = np.random.default_rng(seed)
+    w = rng.standard_normal((nz, nx))
+    F = np.fft.rfft2(w)
+    kx = np.fft.rfftfreq(nx)
+    kz = np.fft.fftfreq(nz)
+    k = np.sqrt(kx[None, :] ** 2 + kz[:, None] ** 2)
+    amp = np.zeros_like(k)
+    nzk = k > 0
+    amp[nzk] = k[nzk] ** (slope / 2.0)
+    return np.fft.irfft2(F * amp, s=(nz, nx))
+
+
+def _minmax(g: np.ndarray, lo: float, hi: float) -> np.ndarray:
+    gmin = g.min()
+    gmax = g.max()
+    return lo + (hi - lo) * (g - gmin) / (gmax - gmin)
+
+
+def grf_slab(nx: int, nz: int, lam: int, seed_base: int = 0,
+             log_chi=(-6.0, 2.0), log_s=(-1.0, 1.0)):
+    """(chi, eta) FP64 [nz][nx] of wavelength `lam` of the GRF recipe."""
+    lc = _minmax(grf(nx, nz, seed_base + 1000 + lam), *log_chi)
+    ls = _minmax(grf(nx, nz, seed_base + 2000 + lam), *log_s)
+    chi = 10.0 ** lc
+    eta = (10.0 ** ls) * chi
+    return chi, eta
+
+
+def grf_fields(n: int, n_lambda: int, nz: int | None = None, seed_base: int = 0,
+               lambdas=None, dtype=np.float32):
+    """GRF recipe, all (or the listed) wavelengths: chi, eta [n_l][nz][nx]."""
+    nx = n
+    nz = n if nz is None else nz
+    lams = list(range(n_lambda)) if lambdas is None else list(lambdas)
+    chi = np.empty((len(lams), nz, nx), dtype=dtype)
+    eta = np.empty((len(lams), nz, nx), dtype=dtype)
+    for j, l in enumerate(lams):
+        c, e = grf_slab(nx, nz, l, seed_base)
+        chi[j] = c
+        eta[j] = e
+    return chi, eta
+
+
+def batched_domains(n_domains: int = 16, seed: int = 7, side_min: int = 256,
+                    side_max: int = 2048, side_step: int = 64, nl_min: int = 32,
+                    nl_max: int = 128):
+    """Sizes of the uneven multi-domain workload: list of (side, n_lambda, seed_base)."""
+    rng = np.random.default_rng(seed)
+    sides = rng.integers(side_min // side_step, side_max // side_step + 1, size=n_domains) * side_step
+    nls = rng.integers(nl_min, nl_max + 1, size=n_domains)
+    return [(int(s), int(l), 100_000 * (d + 1)) for d, (s, l) in enumerate(zip(sides, nls))]

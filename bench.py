@@ -1,0 +1,363 @@
+#!/usr/bin/env python
+"""Benchmark of the radiance-cascade formal solution on B300.
+
+One step = one formal solution (pack + every cascade, top down, + J) of a batch
+of 64 wavelength slices of a 1024 x 1024 grid with 8 cascades (W0 = 4,
+branching 4, cascade-0 interval 1 voxel), fields from the seeded k^-5/3
+log-normal GRF recipe.  The slices are independent, so N GPUs each solve their
+own 64-wavelength batch (weak scaling, no data-path collective).
+
+Prints one JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle
+on the same workload instead (bounded sample: one wavelength per step).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "RC wavelength-slices/s at 1024² (HBM roofline %); NLTE time-to-1e-3 vs plain"
+UNIT = "wavelength-slices/s"
+N_SIDE, N_LAMBDA, N_CASC = 1024, 64, 8
+WORKLOAD = ("RC formal solution, 2D 1024x1024 unit voxels, 64 wavelengths per GPU, 8 cascades, "
+            "W0=4, branching 4, interval0=1 voxel (lengths x4), FP32 chi/eta from seeded "
+            "log-normal GRFs (k^-5/3, log10 chi in [-6,2], S in [0.1,10])")
+CROSS_KEY = "1024x1024_C8_W4_B4_L1.0_r0"
+KERNEL_SOURCES = ["paper_2408_14425_b300/csrc/rcx_fs_kernels.cu"]
+
+
+def _env_int(name, default):
+    try:
+        return int(os.environ.get(name, default))
+    except ValueError:
+        return default
+
+
+def _load_crossings():
+    with open(os.path.join(ROOT, "tests", "golden", "crossings.json")) as f:
+        return json.load(f)["plans"][CROSS_KEY]
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6400.0, "fallback"
+
+
+def _kernel_hash():
+    h = hashlib.sha256()
+    for rel in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def _ncu_traffic(kernel_hash):
+    """DRAM bytes per step of the march kernels from a committed ncu summary, if it was
+    taken on the current kernel source; else None."""
+    p = os.path.join(ROOT, "profiles", "traffic_rc_march_1024.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        d = json.load(f)
+    if d.get("kernel_source_sha256_16") != kernel_hash:
+        return None
+    return d.get("dram_bytes_per_step_march")
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples while the timed region runs."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[3:7]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _algorithmic_bytes(cross, plan, n_lambda):
+    """Per-launch algorithmic bytes of the march kernels (cascade i):
+    8 B (chi, S in FP32) per voxel crossing, + the merged interval R_i written once
+    (4 B per ray, cascades >= 1) + R_{i+1} read once (4 B per upper ray)
+    + J written once at cascade 0 (4 B per cell)."""
+    per = cross["per_cascade"]
+    C = len(per)
+    rays = [plan.cascade(i)["Px"] * plan.cascade(i)["Pz"] * plan.cascade(i)["W"] for i in range(C)]
+    out = []
+    for i in range(C):
+        b = 8 * per[i]
+        if i > 0:
+            b += 4 * rays[i]
+        if i < C - 1:
+            b += 4 * rays[i + 1]
+        if i == 0:
+            b += 4 * N_SIDE * N_SIDE
+        out.append(b * n_lambda)
+    return out, rays
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    from paper_2408_14425_b300 import build as rbuild
+    from paper_2408_14425_b300 import rcx, workloads
+
+    rank = _env_int("RANK", 0)
+    world = _env_int("WORLD_SIZE", 1)
+    local = _env_int("LOCAL_RANK", 0)
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    rbuild.build()
+
+    lams = list(range(rank * N_LAMBDA, (rank + 1) * N_LAMBDA))
+    chi_h, eta_h = workloads.grf_fields(N_SIDE, N_LAMBDA, lambdas=lams)
+    chi = torch.from_numpy(chi_h).cuda()
+    eta = torch.from_numpy(eta_h).cuda()
+    J = torch.empty_like(chi)
+    plan = rcx.Plan(N_SIDE, N_SIDE, N_CASC, dirs0=4, branching=4, interval0=1.0)
+    plan.reserve(N_LAMBDA)
+    stream = torch.cuda.current_stream()
+
+    for _ in range(args.warmup):
+        plan.formal_solve(chi, eta, J)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    time.sleep(0.3)
+    plan.set_timing(True)
+    per_launch = {}
+    launches = 0
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    for _ in range(args.steps):
+        plan.formal_solve(chi, eta, J)
+        launches += plan.last_launch_count()
+        for name, ms in plan.launch_times():  # waits for this step's events
+            per_launch[name] = per_launch.get(name, 0.0) + ms
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    plan.set_timing(False)
+    ms_step = ev0.elapsed_time(ev1) / args.steps
+    if dist:
+        t = torch.tensor([ms_step], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_step = float(t.item())
+        dist.barrier()
+    value = world * N_LAMBDA / (ms_step / 1e3)
+
+    # end to end through the host-buffer entry point (pinned host memory, copies inside)
+    e2e = None
+    if not args.no_e2e:
+        chi_p = torch.from_numpy(chi_h).pin_memory()
+        eta_p = torch.from_numpy(eta_h).pin_memory()
+        J_p = torch.empty_like(chi_p).pin_memory()
+        plan.formal_solve_host(chi_p, eta_p, J_p)
+        if dist:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            plan.formal_solve_host(chi_p, eta_p, J_p)
+        t_e2e = (time.perf_counter() - t0) / args.steps
+        if dist:
+            t = torch.tensor([t_e2e], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            t_e2e = float(t.item())
+        slab = N_LAMBDA * N_SIDE * N_SIDE * 4
+        e2e = {"value": world * N_LAMBDA / t_e2e, "unit": UNIT,
+               "h2d_bytes_per_step": 2 * slab, "d2h_bytes_per_step": slab,
+               "api": "rc_formal_solve_host (pinned host buffers, chunked copy/compute overlap)"}
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+
+    # roofline of the march kernels (all cascade launches of a step)
+    cross = _load_crossings()
+    alg, rays = _algorithmic_bytes(cross, plan, N_LAMBDA)
+    march_ms = sum(per_launch.get(f"cascade {i}", 0.0) for i in range(N_CASC)) / args.steps
+    alg_total = sum(alg)
+    peak, peak_kind = _peaks()
+    achieved = alg_total / (march_ms / 1e3) / 1e9
+    khash = _kernel_hash()
+    traffic = _ncu_traffic(khash)
+    levels = []
+    for i in range(N_CASC):
+        ms = per_launch.get(f"cascade {i}", 0.0) / args.steps
+        levels.append({"cascade": i, "ms": round(ms, 4), "crossings_per_slice": cross["per_cascade"][i],
+                       "alg_GBps": round(alg[i] / (ms / 1e3) / 1e9, 1) if ms > 0 else None})
+    pack_ms = per_launch.get("pack", 0.0) / args.steps
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "traffic": traffic,
+                "kernel": "cascade march (level_kernel + level0_kernel), all 8 launches of a step",
+                "algorithmic_bytes_per_step": alg_total,
+                "bytes_model": "8 B (chi, S FP32) per voxel crossing + merged-interval write/read "
+                               "once + J write",
+                "peak_kind": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)",
+                "march_ms_per_step": round(march_ms, 3), "pack_ms_per_step": round(pack_ms, 3),
+                "per_cascade": levels, "kernel_source_sha256_16": khash}
+
+    # CPU baseline: the FP64 oracle on a bounded sample (one wavelength of this workload)
+    cpu = None
+    if not args.no_cpu_baseline:
+        cpu = _oracle_sample(chi_h[0], eta_h[0])
+
+    intervals = sum(rays)
+    line = {
+        "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n_side": N_SIDE, "n_lambda_per_gpu": N_LAMBDA,
+                   "n_cascades": N_CASC, "dirs0": 4, "branching": 4, "interval0": 1.0,
+                   "storage": "f32", "lambda_block": 4,
+                   "l2": "inputs (chi+eta 537 MB per GPU) larger than L2 (126 MB); no flush",
+                   "parallelism": f"wavelength batches, {world} GPU(s)"},
+        "probe_ray_intervals_per_s": round(value * intervals, 1),
+        "voxel_crossings_per_s": round(value * cross["total"], 1),
+        "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+        "gpu_launches": launches, "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def _oracle_sample(chi2d, eta2d):
+    import numpy as np
+
+    import oracle
+    oracle.build()
+    t0 = time.perf_counter()
+    oracle.rc_solve(chi2d.astype(np.float64), eta2d.astype(np.float64), N_CASC)
+    dt = time.perf_counter() - t0
+    return {"value": round(1.0 / dt, 5), "unit": UNIT, "cores": oracle.num_threads(),
+            "kind": "oracle",
+            "sample": "one wavelength slice (lambda 0) of the 1024^2, 8-cascade workload, FP64 "
+                      f"C oracle with OpenMP over probes, {dt:.2f} s"}
+
+
+def run_reference(args):
+    """The FP64 CPU oracle timed on this workload (rank 0 only; other ranks exit)."""
+    rank = _env_int("RANK", 0)
+    world = _env_int("WORLD_SIZE", 1)
+    if rank != 0:
+        return
+    import numpy as np
+
+    import oracle
+    from paper_2408_14425_b300 import workloads
+    oracle.build()
+    # warm-up steps: the oracle on the 64^2 disc case (loads the library, spins up threads)
+    chi0, eta0 = workloads.disc_field()
+    for _ in range(args.warmup):
+        oracle.rc_solve(chi0.astype(np.float64), eta0.astype(np.float64), 5)
+    times = []
+    for k in range(args.steps):
+        c, e = workloads.grf_fields(N_SIDE, 1, lambdas=[k % N_LAMBDA], dtype=np.float64)
+        t0 = time.perf_counter()
+        oracle.rc_solve(c[0], e[0], N_CASC)
+        times.append(time.perf_counter() - t0)
+    t = sum(times) / len(times)
+    value = 1.0 / t
+    cores = oracle.num_threads()
+    sample = (f"one wavelength slice per step (lambdas 0..{args.steps - 1}) of the 1024^2, "
+              "8-cascade workload, FP64 C oracle, OpenMP over probes")
+    line = {"metric": METRIC, "value": round(value, 5), "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(t * 1e3, 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "impl": "reference",
+            "config": {"workload": WORKLOAD, "n_side": N_SIDE, "n_cascades": N_CASC},
+            "cpu_baseline": {"value": round(value, 5), "unit": UNIT, "cores": cores,
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": round(value, 5), "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        print("note: fewer than 3 warm-up steps", file=sys.stderr)
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,108 @@
+// rcx_internal.h -- plan layout and kernel launch arguments shared by the host
+// side (rcx_plan.cu) and the kernels (rcx_fs_kernels.cu) of librcx.so.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/rcx.h"
+
+namespace rcx {
+
+// Opacities below this (per voxel) are raised to it; the cell's emission eta ds
+// survives through the source function eta / chi.
+constexpr float kChiFloor = 1e-30f;
+// Warps per CTA of the march kernels.
+constexpr int kWarpsPerCta = 8;
+// Merged-interval scale for 16-bit storage: values are stored as R / (S_max 2^-14),
+// which keeps every merged interval (R <= S_max in free space) below 2^14.
+constexpr float kF16Headroom = 16384.0f;
+
+struct LevelGeom {
+    int Px = 0, Pz = 0;      // probes per axis
+    long long W = 0;         // directions
+    double a = 0, b = 0;     // interval [a, b] in voxels (b = inf on the top cascade)
+    long long rays() const { return (long long)Px * Pz * W; }
+};
+
+// Arguments of one cascade-level launch (passed by value).
+struct LevelArgs {
+    const float2* field;     // packed (chi per voxel, S) [n_lblk][ncell][LB]
+    long long ncell;
+    int nx, nz;
+    int Px, Pz;              // this cascade's probes per axis
+    int W;                   // this cascade's directions
+    int Wshift;              // log2(W) if W is a power of two, else -1
+    float spacing;           // probe spacing 2^i (voxels)
+    float a, b;              // interval (b = +inf on the top cascade)
+    const float2* dirs;      // W unit vectors (cos, sin)
+    long long rays;          // Px * Pz * W
+    // upper cascade (merged), NULL on the top cascade
+    const void* R_up;
+    int Px_up, Pz_up;
+    long long R_up_lstride;  // elements per lambda block in R_up
+    // this cascade's merged output (levels >= 1)
+    void* R_out;
+    long long R_out_lstride;
+    const float* scale;      // per lambda block storage scale (16-bit storage), NULL = 1
+    // cascade 0 outputs
+    float* J;
+    float* alo;
+    int n_lambda;
+    int max_steps;           // upper bound on cells crossed by one ray (nx + nz + 2)
+};
+
+struct PackArgs {
+    const float* chi;
+    const float* eta;
+    int n_lambda;
+    long long ncell;
+    float voxel;
+    float2* out;
+    unsigned int* smax_bits;  // per lambda block, may be NULL
+};
+
+// Launchers (rcx_fs_kernels.cu).  Return the CUDA launch error.
+cudaError_t launch_pack(int LB, int n_lblk, const PackArgs& a, cudaStream_t s);
+cudaError_t launch_level(int LB, int precision, bool level0, bool has_up, int n_lblk,
+                         const LevelArgs& a, cudaStream_t s);
+cudaError_t launch_scales(int n_lblk, const unsigned int* smax_bits, float* scale,
+                          cudaStream_t s);
+
+}  // namespace rcx
+
+struct rc_plan_s {
+    int device = 0;
+    int nx = 0, nz = 0;
+    double voxel = 1.0;
+    int C = 0, W0 = 0, B = 0;
+    float L0 = 1.0f;
+    rc_options opt{};
+    int LB = 4;
+    std::vector<rcx::LevelGeom> lv;
+    std::vector<size_t> dir_off;     // offset of each cascade's table in d_dirs
+    float2* d_dirs = nullptr;
+    // scratch
+    float2* d_packed = nullptr;
+    size_t packed_bytes = 0;
+    void* d_R[2] = {nullptr, nullptr};
+    size_t R_bytes = 0;              // bytes of each of the two cascade buffers
+    unsigned int* d_smax = nullptr;  // per lambda block max source function (bits)
+    float* d_scale = nullptr;
+    size_t aux_count = 0;            // lambda blocks the smax/scale arrays hold
+    int cap_lambda = 0;              // largest n_lambda the scratch holds
+    // host-buffer pipeline
+    cudaStream_t s_io[2] = {nullptr, nullptr};
+    float* d_stage = nullptr;        // 2 chunks x (chi, eta, J, alo)
+    size_t stage_bytes = 0;
+    int last_launches = 0;
+    // tracing
+    bool timing = false;
+    std::vector<cudaEvent_t> ev;     // ev[0] before the first launch, ev[j+1] after launch j
+    std::vector<std::string> launch_names;
+    int timed_launches = 0;
+};

@@ -1,0 +1,483 @@
+// rcx_plan.cu -- host side of librcx.so: plans, scratch, argument checks and the
+// launch sequence of the formal solution (C ABI declared in include/rcx.h).
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "rcx_internal.h"
+
+namespace {
+
+thread_local std::string g_last_error;
+
+rc_status fail(rc_status s, const std::string& msg) {
+    g_last_error = msg;
+    return s;
+}
+
+rc_status cuda_fail(cudaError_t e, const char* what) {
+    g_last_error = std::string(what) + ": " + cudaGetErrorString(e);
+    return RC_ERR_CUDA;
+}
+
+// Makes the plan's device current for the scope and restores the caller's.
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = true;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) ok = cudaSetDevice(dev) == cudaSuccess;
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+bool is_pow2(long long v) { return v > 0 && (v & (v - 1)) == 0; }
+
+int ilog2(long long v) {
+    int s = 0;
+    while ((1LL << s) < v) ++s;
+    return s;
+}
+
+size_t storage_bytes(int precision) { return precision == RC_STORE_F32 ? 4 : 2; }
+
+void free_scratch(rc_plan_s* p) {
+    cudaFree(p->d_packed);
+    cudaFree(p->d_R[0]);
+    cudaFree(p->d_R[1]);
+    cudaFree(p->d_smax);
+    cudaFree(p->d_scale);
+    p->d_packed = nullptr;
+    p->d_R[0] = p->d_R[1] = nullptr;
+    p->d_smax = nullptr;
+    p->d_scale = nullptr;
+    p->packed_bytes = p->R_bytes = 0;
+    p->aux_count = 0;
+    p->cap_lambda = 0;
+}
+
+// Grows the solve scratch to hold n_lambda wavelengths.
+rc_status ensure_scratch(rc_plan_s* p, int n_lambda) {
+    if (n_lambda <= p->cap_lambda) return RC_OK;
+    const int LB = p->LB;
+    const size_t n_lblk = (size_t)((n_lambda + LB - 1) / LB);
+    const size_t ncell = (size_t)p->nx * p->nz;
+    long long max_rays = 0;
+    for (size_t i = 1; i < p->lv.size(); ++i) max_rays = std::max(max_rays, p->lv[i].rays());
+    const size_t packed = n_lblk * ncell * LB * sizeof(float2);
+    const size_t Rb = std::max<size_t>(1, n_lblk * (size_t)max_rays * LB *
+                                              storage_bytes(p->opt.precision));
+    cudaDeviceSynchronize();  // scratch may be in use by work still queued
+    free_scratch(p);
+    cudaError_t e;
+    if ((e = cudaMalloc(&p->d_packed, packed)) != cudaSuccess ||
+        (e = cudaMalloc(&p->d_R[0], Rb)) != cudaSuccess ||
+        (e = cudaMalloc(&p->d_R[1], Rb)) != cudaSuccess ||
+        (e = cudaMalloc(&p->d_smax, n_lblk * sizeof(unsigned))) != cudaSuccess ||
+        (e = cudaMalloc(&p->d_scale, n_lblk * sizeof(float))) != cudaSuccess) {
+        free_scratch(p);
+        cudaGetLastError();
+        return fail(e == cudaErrorMemoryAllocation ? RC_ERR_OOM : RC_ERR_CUDA,
+                    std::string("scratch allocation failed: ") + cudaGetErrorString(e));
+    }
+    p->packed_bytes = packed;
+    p->R_bytes = Rb;
+    p->aux_count = n_lblk;
+    p->cap_lambda = (int)(n_lblk * LB);
+    return RC_OK;
+}
+
+// The launch sequence of one solve on device buffers.
+rc_status solve_device(rc_plan_s* p, const float* chi, const float* eta, int n_lambda,
+                       float* J, float* alo, cudaStream_t s) {
+    if (n_lambda == 0) return RC_OK;
+    if ((n_lambda + p->LB - 1) / p->LB > 65535)
+        return fail(RC_ERR_ARG, "rc_formal_solve: too many wavelengths for one call (65535 blocks)");
+    rc_status st = ensure_scratch(p, n_lambda);
+    if (st != RC_OK) return st;
+    const int LB = p->LB;
+    const int n_lblk = (n_lambda + LB - 1) / LB;
+    const long long ncell = (long long)p->nx * p->nz;
+    const bool f16 = p->opt.precision != RC_STORE_F32;
+    int launches = 0;
+    cudaError_t e;
+    const bool timing = p->timing && p->ev.size() >= (size_t)(p->C + 3);
+    if (timing) {
+        p->launch_names.clear();
+        cudaEventRecord(p->ev[0], s);
+    }
+    auto mark = [&](const std::string& name) {
+        if (timing) {
+            p->launch_names.push_back(name);
+            cudaEventRecord(p->ev[launches], s);
+        }
+    };
+
+    if (f16) {
+        if ((e = cudaMemsetAsync(p->d_smax, 0, n_lblk * sizeof(unsigned), s)) != cudaSuccess)
+            return cuda_fail(e, "memset");
+    }
+    rcx::PackArgs pa{chi, eta, n_lambda, ncell, (float)p->voxel, p->d_packed,
+                     f16 ? p->d_smax : nullptr};
+    if ((e = rcx::launch_pack(LB, n_lblk, pa, s)) != cudaSuccess) return cuda_fail(e, "pack launch");
+    ++launches;
+    mark("pack");
+    if (f16) {
+        if ((e = rcx::launch_scales(n_lblk, p->d_smax, p->d_scale, s)) != cudaSuccess)
+            return cuda_fail(e, "scale launch");
+        ++launches;
+        mark("scale");
+    }
+
+    const int C = p->C;
+    for (int i = C - 1; i >= 0; --i) {
+        const rcx::LevelGeom& g = p->lv[i];
+        rcx::LevelArgs a{};
+        a.field = p->d_packed;
+        a.ncell = ncell;
+        a.nx = p->nx;
+        a.nz = p->nz;
+        a.Px = g.Px;
+        a.Pz = g.Pz;
+        a.W = (int)g.W;
+        a.Wshift = is_pow2(g.W) ? ilog2(g.W) : -1;
+        a.spacing = (float)(1 << i);
+        a.a = (float)g.a;
+        a.b = std::isinf(g.b) ? INFINITY : (float)g.b;
+        a.dirs = p->d_dirs + p->dir_off[i];
+        a.rays = g.rays();
+        const bool has_up = i < C - 1;
+        if (has_up) {
+            const rcx::LevelGeom& u = p->lv[i + 1];
+            a.R_up = p->d_R[(i + 1) & 1];
+            a.Px_up = u.Px;
+            a.Pz_up = u.Pz;
+            a.R_up_lstride = u.rays() * LB;
+        }
+        if (i > 0) {
+            a.R_out = p->d_R[i & 1];
+            a.R_out_lstride = g.rays() * LB;
+        }
+        a.scale = f16 ? p->d_scale : nullptr;
+        a.J = J;
+        a.alo = alo;
+        a.n_lambda = n_lambda;
+        a.max_steps = p->nx + p->nz + 2;
+        if ((e = rcx::launch_level(LB, p->opt.precision, i == 0, has_up, n_lblk, a, s)) !=
+            cudaSuccess)
+            return cuda_fail(e, "cascade launch");
+        ++launches;
+        mark("cascade " + std::to_string(i));
+    }
+    p->last_launches = launches;
+    p->timed_launches = timing ? launches : 0;
+    return RC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void rc_options_default(rc_options* opt) {
+    if (!opt) return;
+    std::memset(opt, 0, sizeof(*opt));
+    opt->precision = RC_STORE_F32;
+    opt->n_incl = 1;
+    opt->interval_rule = 0;
+    opt->lambda_block = 0;
+    opt->bilinear_fix = 0;
+}
+
+const char* rc_last_error(void) { return g_last_error.c_str(); }
+
+const char* rc_status_string(rc_status s) {
+    switch (s) {
+        case RC_OK: return "RC_OK";
+        case RC_ERR_ARG: return "RC_ERR_ARG";
+        case RC_ERR_OOM: return "RC_ERR_OOM";
+        case RC_ERR_CUDA: return "RC_ERR_CUDA";
+        case RC_ERR_TIMEOUT: return "RC_ERR_TIMEOUT";
+        case RC_ERR_NOT_CONVERGED: return "RC_ERR_NOT_CONVERGED";
+        case RC_ERR_UNSUPPORTED: return "RC_ERR_UNSUPPORTED";
+    }
+    return "RC_ERR_UNKNOWN";
+}
+
+rc_status rc_plan(const rc_grid* grid, int n_cascades, int dirs0, int branching,
+                  float interval0, const rc_options* opt, rc_plan_t* out) {
+    g_last_error.clear();
+    if (!out) return fail(RC_ERR_ARG, "rc_plan: out is NULL");
+    *out = nullptr;
+    if (!grid) return fail(RC_ERR_ARG, "rc_plan: grid is NULL");
+    if (grid->nx < 1 || grid->nz < 1 || grid->nx > (1 << 20) || grid->nz > (1 << 20))
+        return fail(RC_ERR_ARG, "rc_plan: nx, nz must be in [1, 2^20]");
+    if (!(grid->voxel_size > 0.0) || !std::isfinite(grid->voxel_size))
+        return fail(RC_ERR_ARG, "rc_plan: voxel_size must be positive and finite");
+    if (n_cascades < 1 || n_cascades > 16) return fail(RC_ERR_ARG, "rc_plan: n_cascades must be in [1, 16]");
+    if (dirs0 < 1 || dirs0 > 4096) return fail(RC_ERR_ARG, "rc_plan: dirs0 must be in [1, 4096]");
+    if (!(interval0 > 0.0f) || !std::isfinite(interval0))
+        return fail(RC_ERR_ARG, "rc_plan: interval0 must be positive and finite");
+    if (branching != 4)
+        return fail(RC_ERR_UNSUPPORTED, "rc_plan: only branching = 4 (alpha = 2) is implemented");
+    rc_options o;
+    rc_options_default(&o);
+    if (opt) o = *opt;
+    if (o.precision < RC_STORE_F32 || o.precision > RC_STORE_BF16)
+        return fail(RC_ERR_ARG, "rc_plan: precision must be RC_STORE_F32, _F16 or _BF16");
+    if (o.interval_rule != 0 && o.interval_rule != 1)
+        return fail(RC_ERR_ARG, "rc_plan: interval_rule must be 0 or 1");
+    if (o.n_incl != 1) return fail(RC_ERR_UNSUPPORTED, "rc_plan: n_incl != 1 is not implemented");
+    if (o.bilinear_fix != 0)
+        return fail(RC_ERR_UNSUPPORTED, "rc_plan: the bilinear fix is not implemented");
+    int LB = o.lambda_block == 0 ? 4 : o.lambda_block;
+    if (LB != 1 && LB != 2 && LB != 4 && LB != 8 && LB != 16 && LB != 32)
+        return fail(RC_ERR_ARG, "rc_plan: lambda_block must be 0, 1, 2, 4, 8, 16 or 32");
+    for (int r : o.reserved)
+        if (r != 0) return fail(RC_ERR_ARG, "rc_plan: reserved option fields must be zero");
+
+    rc_plan_s* p = new (std::nothrow) rc_plan_s();
+    if (!p) return fail(RC_ERR_OOM, "rc_plan: host allocation failed");
+    if (cudaGetDevice(&p->device) != cudaSuccess) {
+        delete p;
+        cudaGetLastError();
+        return fail(RC_ERR_CUDA, "rc_plan: no CUDA device");
+    }
+    p->nx = grid->nx;
+    p->nz = grid->nz;
+    p->voxel = grid->voxel_size;
+    p->C = n_cascades;
+    p->W0 = dirs0;
+    p->B = branching;
+    p->L0 = interval0;
+    p->opt = o;
+    p->LB = LB;
+
+    // geometry (Sec. 2.3, Eq. 12-13), FP64 on the host
+    const double g = std::pow(2.0, 0.5 * branching);
+    std::vector<float2> dirs;
+    double start = 0.0;
+    for (int i = 0; i < n_cascades; ++i) {
+        rcx::LevelGeom L;
+        L.Px = (p->nx + (1 << i) - 1) >> i;
+        L.Pz = (p->nz + (1 << i) - 1) >> i;
+        L.W = dirs0;
+        for (int j = 0; j < i; ++j) L.W *= branching;
+        const double len = (double)interval0 * std::pow(g, (double)i);
+        if (o.interval_rule == 0) {
+            L.a = start;
+            L.b = start + len;
+            start += len;
+        } else {
+            L.a = i == 0 ? 0.0 : (double)interval0 * std::pow(g, (double)(i - 1));
+            L.b = len;
+        }
+        if (i == n_cascades - 1) L.b = INFINITY;
+        if (L.W > (1LL << 26) || L.rays() > (1LL << 32)) {
+            delete p;
+            return fail(RC_ERR_ARG, "rc_plan: cascade too large (directions or rays)");
+        }
+        p->dir_off.push_back(dirs.size());
+        for (long long k = 0; k < L.W; ++k) {
+            const double th = 2.0 * M_PI * ((double)k + 0.5) / (double)L.W;
+            dirs.push_back(make_float2((float)std::cos(th), (float)std::sin(th)));
+        }
+        p->lv.push_back(L);
+    }
+    cudaError_t e = cudaMalloc(&p->d_dirs, dirs.size() * sizeof(float2));
+    if (e == cudaSuccess)
+        e = cudaMemcpy(p->d_dirs, dirs.data(), dirs.size() * sizeof(float2), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        cudaFree(p->d_dirs);
+        delete p;
+        cudaGetLastError();
+        return e == cudaErrorMemoryAllocation ? fail(RC_ERR_OOM, "rc_plan: direction table allocation failed")
+                                              : cuda_fail(e, "rc_plan: direction table upload");
+    }
+    *out = p;
+    return RC_OK;
+}
+
+void rc_plan_destroy(rc_plan_t p) {
+    if (!p) return;
+    DeviceGuard dg(p->device);
+    cudaDeviceSynchronize();
+    free_scratch(p);
+    cudaFree(p->d_dirs);
+    cudaFree(p->d_stage);
+    for (auto& s : p->s_io)
+        if (s) cudaStreamDestroy(s);
+    for (auto& e : p->ev) cudaEventDestroy(e);
+    delete p;
+}
+
+rc_status rc_plan_reserve(rc_plan_t p, int n_lambda) {
+    g_last_error.clear();
+    if (!p) return fail(RC_ERR_ARG, "rc_plan_reserve: plan is NULL");
+    if (n_lambda < 0) return fail(RC_ERR_ARG, "rc_plan_reserve: n_lambda < 0");
+    DeviceGuard dg(p->device);
+    if (!dg.ok) return fail(RC_ERR_CUDA, "rc_plan_reserve: cannot select the plan's device");
+    return ensure_scratch(p, n_lambda);
+}
+
+size_t rc_plan_scratch_bytes(rc_plan_t p) {
+    if (!p) return 0;
+    return p->packed_bytes + 2 * p->R_bytes + p->aux_count * (sizeof(unsigned) + sizeof(float)) +
+           p->stage_bytes;
+}
+
+rc_status rc_plan_cascade(rc_plan_t p, int i, int* px, int* pz, long long* dirs, double* a,
+                          double* b) {
+    if (!p) return fail(RC_ERR_ARG, "rc_plan_cascade: plan is NULL");
+    if (i < 0 || i >= p->C) return fail(RC_ERR_ARG, "rc_plan_cascade: cascade index out of range");
+    const rcx::LevelGeom& g = p->lv[i];
+    if (px) *px = g.Px;
+    if (pz) *pz = g.Pz;
+    if (dirs) *dirs = g.W;
+    if (a) *a = g.a;
+    if (b) *b = g.b;
+    return RC_OK;
+}
+
+int rc_plan_last_launch_count(rc_plan_t p) { return p ? p->last_launches : 0; }
+
+rc_status rc_plan_set_timing(rc_plan_t p, int enable) {
+    g_last_error.clear();
+    if (!p) return fail(RC_ERR_ARG, "rc_plan_set_timing: plan is NULL");
+    DeviceGuard dg(p->device);
+    const size_t need = (size_t)p->C + 3;  // pack, scale, C cascades, plus the start event
+    while (enable && p->ev.size() < need) {
+        cudaEvent_t e;
+        cudaError_t err = cudaEventCreate(&e);
+        if (err != cudaSuccess) return cuda_fail(err, "rc_plan_set_timing");
+        p->ev.push_back(e);
+    }
+    p->timing = enable != 0;
+    p->timed_launches = 0;
+    return RC_OK;
+}
+
+rc_status rc_plan_launch_times(rc_plan_t p, float* ms, int max_n, int* n_out) {
+    g_last_error.clear();
+    if (!p || !ms || !n_out) return fail(RC_ERR_ARG, "rc_plan_launch_times: NULL argument");
+    if (!p->timing || p->timed_launches == 0)
+        return fail(RC_ERR_ARG, "rc_plan_launch_times: no timed solve (enable timing first)");
+    DeviceGuard dg(p->device);
+    cudaError_t e = cudaEventSynchronize(p->ev[p->timed_launches]);
+    if (e != cudaSuccess) return cuda_fail(e, "rc_plan_launch_times");
+    const int n = std::min(max_n, p->timed_launches);
+    for (int j = 0; j < n; ++j) {
+        e = cudaEventElapsedTime(&ms[j], p->ev[j], p->ev[j + 1]);
+        if (e != cudaSuccess) return cuda_fail(e, "rc_plan_launch_times");
+    }
+    *n_out = n;
+    return RC_OK;
+}
+
+const char* rc_plan_launch_name(rc_plan_t p, int i) {
+    if (!p || i < 0 || i >= (int)p->launch_names.size()) return "";
+    return p->launch_names[i].c_str();
+}
+
+rc_status rc_formal_solve(rc_plan_t p, const float* chi, const float* eta, int n_lambda, float* J,
+                          float* alo, void* stream) {
+    g_last_error.clear();
+    if (!p) return fail(RC_ERR_ARG, "rc_formal_solve: plan is NULL");
+    if (n_lambda < 0) return fail(RC_ERR_ARG, "rc_formal_solve: n_lambda < 0");
+    if (n_lambda > 0 && (!chi || !eta || !J))
+        return fail(RC_ERR_ARG, "rc_formal_solve: chi, eta and J must be non-NULL");
+    DeviceGuard dg(p->device);
+    if (!dg.ok) return fail(RC_ERR_CUDA, "rc_formal_solve: cannot select the plan's device");
+    cudaError_t sticky = cudaGetLastError();
+    if (sticky != cudaSuccess) return cuda_fail(sticky, "rc_formal_solve: pending CUDA error");
+    return solve_device(p, chi, eta, n_lambda, J, alo, (cudaStream_t)stream);
+}
+
+rc_status rc_formal_solve_host(rc_plan_t p, const float* chi_h, const float* eta_h, int n_lambda,
+                               float* J_h, float* alo_h) {
+    g_last_error.clear();
+    if (!p) return fail(RC_ERR_ARG, "rc_formal_solve_host: plan is NULL");
+    if (n_lambda < 0) return fail(RC_ERR_ARG, "rc_formal_solve_host: n_lambda < 0");
+    if (n_lambda == 0) return RC_OK;
+    if (!chi_h || !eta_h || !J_h)
+        return fail(RC_ERR_ARG, "rc_formal_solve_host: chi, eta and J must be non-NULL");
+    DeviceGuard dg(p->device);
+    if (!dg.ok) return fail(RC_ERR_CUDA, "rc_formal_solve_host: cannot select the plan's device");
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "rc_formal_solve_host: pending CUDA error");
+
+    // Chunks of whole lambda blocks; chunk c's copies overlap chunk c-1's solve.
+    const size_t ncell = (size_t)p->nx * p->nz;
+    const int LB = p->LB;
+    int chunk = std::max(LB, ((16 + LB - 1) / LB) * LB);
+    if (chunk > n_lambda) chunk = n_lambda;
+    const int n_chunks = (n_lambda + chunk - 1) / chunk;
+    const size_t slab = (size_t)chunk * ncell;                 // floats per array per chunk
+    const size_t per_buf = slab * (alo_h ? 4 : 3);             // chi, eta, J (, alo)
+    const size_t need = 2 * per_buf * sizeof(float);
+    if (p->stage_bytes < need) {
+        cudaDeviceSynchronize();
+        cudaFree(p->d_stage);
+        p->d_stage = nullptr;
+        p->stage_bytes = 0;
+        if ((e = cudaMalloc(&p->d_stage, need)) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(RC_ERR_OOM, "rc_formal_solve_host: staging allocation failed");
+        }
+        p->stage_bytes = need;
+    }
+    for (auto& s : p->s_io)
+        if (!s && (e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking)) != cudaSuccess)
+            return cuda_fail(e, "rc_formal_solve_host: stream creation");
+    rc_status st = ensure_scratch(p, chunk);
+    if (st != RC_OK) return st;
+
+    // s_io[0] carries copies in, s_io[1] the solves and copies out.  Buffer b = c % 2 is
+    // reused two chunks later, after its J has left (event done[b]).
+    cudaEvent_t loaded[2], done[2];
+    for (int b = 0; b < 2; ++b) {
+        cudaEventCreateWithFlags(&loaded[b], cudaEventDisableTiming);
+        cudaEventCreateWithFlags(&done[b], cudaEventDisableTiming);
+    }
+    int launches = 0;
+    const bool timing_was = p->timing;
+    p->timing = false;
+    for (int c = 0; c < n_chunks && st == RC_OK; ++c) {
+        const int b = c & 1;
+        const int l0 = c * chunk;
+        const int nl = std::min(chunk, n_lambda - l0);
+        const size_t bytes = (size_t)nl * ncell * sizeof(float);
+        float* dchi = p->d_stage + b * per_buf;
+        float* deta = dchi + slab;
+        float* dJ = deta + slab;
+        float* dalo = alo_h ? dJ + slab : nullptr;
+        if (c >= 2) cudaStreamWaitEvent(p->s_io[0], done[b], 0);
+        cudaMemcpyAsync(dchi, chi_h + (size_t)l0 * ncell, bytes, cudaMemcpyHostToDevice, p->s_io[0]);
+        cudaMemcpyAsync(deta, eta_h + (size_t)l0 * ncell, bytes, cudaMemcpyHostToDevice, p->s_io[0]);
+        cudaEventRecord(loaded[b], p->s_io[0]);
+        cudaStreamWaitEvent(p->s_io[1], loaded[b], 0);
+        st = solve_device(p, dchi, deta, nl, dJ, dalo, p->s_io[1]);
+        launches += p->last_launches;
+        cudaMemcpyAsync(J_h + (size_t)l0 * ncell, dJ, bytes, cudaMemcpyDeviceToHost, p->s_io[1]);
+        if (alo_h)
+            cudaMemcpyAsync(alo_h + (size_t)l0 * ncell, dalo, bytes, cudaMemcpyDeviceToHost, p->s_io[1]);
+        cudaEventRecord(done[b], p->s_io[1]);
+    }
+    e = cudaStreamSynchronize(p->s_io[1]);
+    cudaStreamSynchronize(p->s_io[0]);
+    for (int b = 0; b < 2; ++b) {
+        cudaEventDestroy(loaded[b]);
+        cudaEventDestroy(done[b]);
+    }
+    p->last_launches = launches;
+    p->timing = timing_was;
+    if (st != RC_OK) return st;
+    if (e != cudaSuccess) return cuda_fail(e, "rc_formal_solve_host");
+    return RC_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,232 @@
+"""Thin ctypes binding of librcx.so (argument marshalling only).
+
+Every step of the formal solution runs in the library's CUDA kernels; this
+module checks tensor dtypes/devices/shapes, passes raw pointers and the
+current CUDA stream, and turns status codes into exceptions.  There is no
+fallback: if librcx.so is missing or fails to load, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "librcx.so")
+
+RC_OK = 0
+STATUS = {0: "RC_OK", -1: "RC_ERR_ARG", -2: "RC_ERR_OOM", -3: "RC_ERR_CUDA",
+          -4: "RC_ERR_TIMEOUT", -5: "RC_ERR_NOT_CONVERGED", -6: "RC_ERR_UNSUPPORTED"}
+PRECISION = {"f32": 0, "fp32": 0, "f16": 1, "fp16": 1, "bf16": 2}
+
+# every symbol include/rcx.h declares
+EXPORTS = [
+    "rc_options_default", "rc_plan", "rc_plan_destroy", "rc_plan_reserve",
+    "rc_plan_scratch_bytes", "rc_formal_solve", "rc_formal_solve_host", "rc_plan_cascade",
+    "rc_plan_last_launch_count", "rc_last_error", "rc_status_string", "rc_plan_set_timing",
+    "rc_plan_launch_times", "rc_plan_launch_name",
+]
+
+
+class RcError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        self.status = status
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+
+
+class rc_grid(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("nz", ctypes.c_int), ("voxel_size", ctypes.c_double)]
+
+
+class rc_options(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("n_incl", ctypes.c_int),
+                ("interval_rule", ctypes.c_int), ("lambda_block", ctypes.c_int),
+                ("bilinear_fix", ctypes.c_int), ("reserved", ctypes.c_int * 3)]
+
+
+_lib = None
+_vp = ctypes.c_void_p
+
+
+def load():
+    """Load librcx.so (raises if it is missing: there is no non-CUDA path)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"librcx.so not built at {LIB_PATH}; run paper_2408_14425_b300/build.py")
+    L = ctypes.CDLL(LIB_PATH)
+    L.rc_options_default.argtypes = [ctypes.POINTER(rc_options)]
+    L.rc_options_default.restype = None
+    L.rc_plan.argtypes = [ctypes.POINTER(rc_grid), ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                          ctypes.c_float, ctypes.POINTER(rc_options), ctypes.POINTER(_vp)]
+    L.rc_plan.restype = ctypes.c_int
+    L.rc_plan_destroy.argtypes = [_vp]
+    L.rc_plan_destroy.restype = None
+    L.rc_plan_reserve.argtypes = [_vp, ctypes.c_int]
+    L.rc_plan_reserve.restype = ctypes.c_int
+    L.rc_plan_scratch_bytes.argtypes = [_vp]
+    L.rc_plan_scratch_bytes.restype = ctypes.c_size_t
+    L.rc_formal_solve.argtypes = [_vp, _vp, _vp, ctypes.c_int, _vp, _vp, _vp]
+    L.rc_formal_solve.restype = ctypes.c_int
+    L.rc_formal_solve_host.argtypes = [_vp, _vp, _vp, ctypes.c_int, _vp, _vp]
+    L.rc_formal_solve_host.restype = ctypes.c_int
+    L.rc_plan_cascade.argtypes = [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                  ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_longlong),
+                                  ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
+    L.rc_plan_cascade.restype = ctypes.c_int
+    L.rc_plan_last_launch_count.argtypes = [_vp]
+    L.rc_plan_last_launch_count.restype = ctypes.c_int
+    L.rc_last_error.argtypes = []
+    L.rc_last_error.restype = ctypes.c_char_p
+    L.rc_status_string.argtypes = [ctypes.c_int]
+    L.rc_status_string.restype = ctypes.c_char_p
+    L.rc_plan_set_timing.argtypes = [_vp, ctypes.c_int]
+    L.rc_plan_set_timing.restype = ctypes.c_int
+    L.rc_plan_launch_times.argtypes = [_vp, ctypes.POINTER(ctypes.c_float), ctypes.c_int,
+                                       ctypes.POINTER(ctypes.c_int)]
+    L.rc_plan_launch_times.restype = ctypes.c_int
+    L.rc_plan_launch_name.argtypes = [_vp, ctypes.c_int]
+    L.rc_plan_launch_name.restype = ctypes.c_char_p
+    _lib = L
+    return L
+
+
+def check(status: int):
+    if status != RC_OK:
+        msg = load().rc_last_error().decode(errors="replace")
+        raise RcError(status, msg)
+
+
+def _stream_ptr(stream):
+    import torch
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _dev_ptr(t, name, shape, dtype_name="float32"):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != getattr(torch, dtype_name):
+        raise TypeError(f"{name} must be {dtype_name}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} has shape {tuple(t.shape)}, expected {tuple(shape)}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _host_ptr(a, name, shape):
+    if hasattr(a, "numpy") and not isinstance(a, np.ndarray):  # torch CPU tensor
+        if a.is_cuda:
+            raise TypeError(f"{name} must be in host memory")
+        if not a.is_contiguous() or str(a.dtype) != "torch.float32":
+            raise TypeError(f"{name} must be a contiguous float32 host tensor")
+        if tuple(a.shape) != tuple(shape):
+            raise ValueError(f"{name} has shape {tuple(a.shape)}, expected {tuple(shape)}")
+        return ctypes.c_void_p(a.data_ptr())
+    if not isinstance(a, np.ndarray) or a.dtype != np.float32 or not a.flags.c_contiguous:
+        raise TypeError(f"{name} must be a C-contiguous float32 array")
+    if a.shape != tuple(shape):
+        raise ValueError(f"{name} has shape {a.shape}, expected {tuple(shape)}")
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+class Plan:
+    """rc_plan: cascade geometry of an nx x nz grid (see include/rcx.h)."""
+
+    def __init__(self, nx: int, nz: int, n_cascades: int, dirs0: int = 4, branching: int = 4,
+                 interval0: float = 1.0, voxel_size: float = 1.0, precision: str = "f32",
+                 interval_rule: int = 0, lambda_block: int = 0, n_incl: int = 1,
+                 bilinear_fix: bool = False):
+        L = load()
+        self.nx, self.nz, self.n_cascades = nx, nz, n_cascades
+        g = rc_grid(nx, nz, voxel_size)
+        o = rc_options()
+        L.rc_options_default(ctypes.byref(o))
+        o.precision = PRECISION[precision]
+        o.interval_rule = interval_rule
+        o.lambda_block = lambda_block
+        o.n_incl = n_incl
+        o.bilinear_fix = int(bilinear_fix)
+        h = _vp()
+        check(L.rc_plan(ctypes.byref(g), n_cascades, dirs0, branching, interval0, ctypes.byref(o),
+                        ctypes.byref(h)))
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().rc_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def handle(self):
+        return self._h
+
+    def reserve(self, n_lambda: int):
+        check(load().rc_plan_reserve(self._h, n_lambda))
+
+    def scratch_bytes(self) -> int:
+        return int(load().rc_plan_scratch_bytes(self._h))
+
+    def last_launch_count(self) -> int:
+        return int(load().rc_plan_last_launch_count(self._h))
+
+    def set_timing(self, enable: bool = True):
+        check(load().rc_plan_set_timing(self._h, int(enable)))
+
+    def launch_times(self):
+        """[(kernel name, ms)] of the last timed solve (waits for it)."""
+        buf = (ctypes.c_float * 64)()
+        n = ctypes.c_int()
+        check(load().rc_plan_launch_times(self._h, buf, 64, ctypes.byref(n)))
+        return [(load().rc_plan_launch_name(self._h, j).decode(), float(buf[j]))
+                for j in range(n.value)]
+
+    def cascade(self, i: int):
+        px, pz = ctypes.c_int(), ctypes.c_int()
+        w = ctypes.c_longlong()
+        a, b = ctypes.c_double(), ctypes.c_double()
+        check(load().rc_plan_cascade(self._h, i, ctypes.byref(px), ctypes.byref(pz),
+                                     ctypes.byref(w), ctypes.byref(a), ctypes.byref(b)))
+        return dict(Px=px.value, Pz=pz.value, W=w.value, a=a.value, b=b.value)
+
+    def formal_solve(self, chi, eta, J=None, alo=None, want_alo: bool = False, stream=None):
+        """J (and the diagonal ALO) of device FP32 chi/eta [n_lambda][nz][nx]."""
+        import torch
+        if chi.dim() == 2:
+            chi = chi.unsqueeze(0)
+            eta = eta.unsqueeze(0)
+        nl = chi.shape[0]
+        shape = (nl, self.nz, self.nx)
+        pc = _dev_ptr(chi, "chi", shape)
+        pe = _dev_ptr(eta, "eta", shape)
+        if J is None:
+            J = torch.empty(shape, dtype=torch.float32, device=chi.device)
+        pj = _dev_ptr(J, "J", shape)
+        if want_alo and alo is None:
+            alo = torch.empty(shape, dtype=torch.float32, device=chi.device)
+        pa = _dev_ptr(alo, "alo", shape) if alo is not None else None
+        check(load().rc_formal_solve(self._h, pc, pe, nl, pj, pa, _stream_ptr(stream)))
+        return (J, alo) if alo is not None else J
+
+    def formal_solve_host(self, chi, eta, J=None, alo=None, want_alo: bool = False):
+        """Same on host FP32 arrays (numpy or CPU tensors); copies are inside the call."""
+        nl = chi.shape[0]
+        shape = (nl, self.nz, self.nx)
+        if J is None:
+            J = np.empty(shape, dtype=np.float32)
+        if want_alo and alo is None:
+            alo = np.empty(shape, dtype=np.float32)
+        check(load().rc_formal_solve_host(
+            self._h, _host_ptr(chi, "chi", shape), _host_ptr(eta, "eta", shape), nl,
+            _host_ptr(J, "J", shape), _host_ptr(alo, "alo", shape) if alo is not None else None))
+        return (J, alo) if alo is not None else J

@@ -22,7 +22,12 @@ fields stand in for it):
 """
 from __future__ import annotations
 
+import functools
+import os
+from concurrent.futures import ThreadPoolExecutor
+
 import numpy as np
+import scipy.fft as _fft
 
 
 def disc_field(n: int = 64, radius: float = 8.0, chi_bg: float = 1e-2,
@@ -66,18 +71,23 @@ def thin_disc_field(n: int, radius: float, chi_disc: float = 1e-9, eta_disc: flo
     return chi, eta
 
 
-def grf(nx: int, nz: int, seed: int, slope: float = -5.0 / 3.0) -> np.ndarray:
-    """Zero-mean 2D Gaussian random field with power spectrum ~ |k|^slope."""
-    rng = np.random.default_rng(seed)
-    w = rng.standard_normal((nz, nx))
-    F = np.fft.rfft2(w)
+@functools.lru_cache(maxsize=8)
+def _spectral_amplitude(nx: int, nz: int, slope: float) -> np.ndarray:
     kx = np.fft.rfftfreq(nx)
     kz = np.fft.fftfreq(nz)
     k = np.sqrt(kx[None, :] ** 2 + kz[:, None] ** 2)
     amp = np.zeros_like(k)
     nzk = k > 0
     amp[nzk] = k[nzk] ** (slope / 2.0)
-    return np.fft.irfft2(F * amp, s=(nz, nx))
+    return amp
+
+
+def grf(nx: int, nz: int, seed: int, slope: float = -5.0 / 3.0) -> np.ndarray:
+    """Zero-mean 2D Gaussian random field with power spectrum ~ |k|^slope."""
+    rng = np.random.default_rng(seed)
+    w = rng.standard_normal((nz, nx))
+    F = _fft.rfft2(w)
+    return _fft.irfft2(F * _spectral_amplitude(nx, nz, slope), s=(nz, nx))
 
 
 def _minmax(g: np.ndarray, lo: float, hi: float) -> np.ndarray:
@@ -104,10 +114,19 @@ def grf_fields(n: int, n_lambda: int, nz: int | None = None, seed_base: int = 0,
     lams = list(range(n_lambda)) if lambdas is None else list(lambdas)
     chi = np.empty((len(lams), nz, nx), dtype=dtype)
     eta = np.empty((len(lams), nz, nx), dtype=dtype)
-    for j, l in enumerate(lams):
-        c, e = grf_slab(nx, nz, l, seed_base)
+
+    def one(j):
+        c, e = grf_slab(nx, nz, lams[j], seed_base)
         chi[j] = c
         eta[j] = e
+
+    workers = max(1, min(len(lams), os.cpu_count() or 1, 16))
+    if workers == 1:
+        for j in range(len(lams)):
+            one(j)
+    else:
+        with ThreadPoolExecutor(workers) as ex:
+            list(ex.map(one, range(len(lams))))
     return chi, eta
 
 

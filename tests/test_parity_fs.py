@@ -1,0 +1,164 @@
+"""Parity of the CUDA formal solution (through the C ABI) with the FP64 oracle.
+
+Tolerance: J within 1e-3 relative in FP32 storage mode and 5e-3 with 16-bit
+interval storage, element by element, with an absolute floor of 1e-7 of the
+slab's largest J (cells darker than that carry no relative information in
+FP32 after ~1e3 accumulated crossings).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2408_14425_b300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+def _rcx():
+    from paper_2408_14425_b300 import build, rcx
+    build.build()
+    return rcx
+
+
+def _assert_close(J, J_ref, rtol, what=""):
+    J = np.asarray(J, dtype=np.float64)
+    J_ref = np.asarray(J_ref, dtype=np.float64)
+    assert J.shape == J_ref.shape
+    assert np.all(np.isfinite(J))
+    floor = 1e-7 * np.max(np.abs(J_ref), axis=(-2, -1), keepdims=True)
+    err = np.abs(J - J_ref)
+    bad = err > rtol * np.abs(J_ref) + floor
+    if bad.any():
+        idx = np.argwhere(bad)[0]
+        rel = (err / np.maximum(np.abs(J_ref), 1e-300)).max()
+        raise AssertionError(f"{what}: {bad.sum()} cells out of tolerance, first at {tuple(idx)}: "
+                             f"{J[tuple(idx)]} vs {J_ref[tuple(idx)]} (max rel {rel:.3e})")
+
+
+def _solve(chi, eta, C, want_alo=False, **plan_kw):
+    rcx = _rcx()
+    nl, nz, nx = chi.shape
+    p = rcx.Plan(nx, nz, C, **plan_kw)
+    dchi = torch.from_numpy(np.ascontiguousarray(chi, dtype=np.float32)).cuda()
+    deta = torch.from_numpy(np.ascontiguousarray(eta, dtype=np.float32)).cuda()
+    out = p.formal_solve(dchi, deta, want_alo=want_alo)
+    torch.cuda.synchronize()
+    if want_alo:
+        return out[0].cpu().numpy(), out[1].cpu().numpy()
+    return out.cpu().numpy()
+
+
+def _oracle(chi, eta, C, want_alo=False, **kw):
+    # the oracle sees the same FP32 inputs, widened to FP64
+    J, alo, _ = oracle.rc_solve(chi.astype(np.float64), eta.astype(np.float64), C,
+                                want_alo=want_alo, **kw)
+    return (J, alo) if want_alo else J
+
+
+def test_disc_64_five_cascades():
+    """64x64 disc, 1 wavelength, 5 cascades, W0 = 4, branching 4, interval 1 voxel."""
+    chi, eta = W.disc_field()
+    J, alo = _solve(chi, eta, 5, want_alo=True)
+    J_ref, alo_ref = _oracle(chi, eta, 5, want_alo=True)
+    _assert_close(J, J_ref, 1e-3, "J disc")
+    _assert_close(alo, alo_ref, 1e-5, "alo disc")
+
+
+@pytest.mark.parametrize("nx,nz,nl,C", [(96, 80, 7, 5), (130, 67, 5, 6), (33, 200, 3, 6)])
+def test_grf_ragged_shapes(nx, nz, nl, C):
+    """Non-square, non-power-of-two grids and a ragged last wavelength block."""
+    chi, eta = W.grf_fields(nx, nl, nz=nz)
+    J = _solve(chi, eta, C)
+    _assert_close(J, _oracle(chi, eta, C), 1e-3, f"J grf {nx}x{nz}")
+
+
+def test_grf_256_seven_cascades():
+    chi, eta = W.grf_fields(256, 6)
+    J, alo = _solve(chi, eta, 7, want_alo=True)
+    J_ref, alo_ref = _oracle(chi, eta, 7, want_alo=True)
+    _assert_close(J, J_ref, 1e-3, "J grf 256")
+    _assert_close(alo, alo_ref, 1e-5, "alo grf 256")
+
+
+@pytest.mark.parametrize("lb", [1, 2, 8, 16, 32])
+def test_lambda_block_layouts_agree(lb):
+    """Every lane-group width computes each (ray, wavelength) with the same arithmetic."""
+    chi, eta = W.grf_fields(72, 9)
+    J4 = _solve(chi, eta, 5, lambda_block=4)
+    Jb = _solve(chi, eta, 5, lambda_block=lb)
+    np.testing.assert_array_equal(J4, Jb)
+
+
+def test_interval_rule_alternative():
+    chi, eta = W.grf_fields(64, 2)
+    J = _solve(chi, eta, 5, interval_rule=1)
+    _assert_close(J, _oracle(chi, eta, 5, rule=1), 1e-3, "rule 1")
+
+
+@pytest.mark.parametrize("C,W0,L0,voxel", [(1, 4, 1.0, 1.0), (2, 8, 1.5, 1.0), (4, 4, 2.0, 0.25),
+                                           (6, 4, 1.0, 5.7e3)])
+def test_plan_parameters(C, W0, L0, voxel):
+    chi, eta = W.grf_fields(48, 2)
+    if voxel != 1.0:
+        chi = (chi / voxel).astype(np.float32)
+        eta = (eta / voxel).astype(np.float32)
+    J = _solve(chi, eta, C, dirs0=W0, interval0=L0, voxel_size=voxel)
+    J_ref = _oracle(chi, eta, C, dirs0=W0, interval0=L0, voxel=voxel)
+    _assert_close(J, J_ref, 1e-3, f"C={C} W0={W0} L0={L0} voxel={voxel}")
+
+
+@pytest.mark.parametrize("nx,nz", [(1, 1), (1, 17), (23, 1), (2, 2)])
+def test_degenerate_grids(nx, nz):
+    rng = np.random.default_rng(nx * 100 + nz)
+    chi = (10 ** rng.uniform(-3, 1, size=(2, nz, nx))).astype(np.float32)
+    eta = (chi * rng.uniform(0.1, 10, size=chi.shape)).astype(np.float32)
+    J = _solve(chi, eta, 4)
+    _assert_close(J, _oracle(chi, eta, 4), 1e-3, f"{nx}x{nz}")
+
+
+def test_zero_opacity_and_vacuum():
+    """chi = 0 cells keep their emission (eta ds); an empty domain gives J = 0."""
+    chi, eta = W.grf_fields(40, 2)
+    chi[0, 10:20, 5:30] = 0.0
+    J = _solve(chi, eta, 5)
+    _assert_close(J, _oracle(chi, eta, 5), 1e-3, "chi=0 patch")
+    z = np.zeros((1, 16, 16), np.float32)
+    assert np.all(_solve(z, z, 3) == 0.0)
+
+
+def test_zero_wavelengths_is_a_no_op():
+    rcx = _rcx()
+    p = rcx.Plan(16, 16, 3)
+    e = torch.empty((0, 16, 16), dtype=torch.float32, device="cuda")
+    J = p.formal_solve(e, e)
+    assert J.shape == (0, 16, 16)
+
+
+@pytest.mark.parametrize("prec,tol", [("f16", 5e-3), ("bf16", 5e-3)])
+def test_reduced_precision_storage(prec, tol):
+    chi, eta = W.grf_fields(128, 5)
+    J = _solve(chi, eta, 6, precision=prec)
+    _assert_close(J, _oracle(chi, eta, 6), tol, prec)
+
+
+def test_host_buffer_entry_matches_device_entry():
+    rcx = _rcx()
+    chi, eta = W.grf_fields(64, 37)
+    p = rcx.Plan(64, 64, 5)
+    J_host, alo_host = p.formal_solve_host(chi, eta, want_alo=True)
+    J_dev, alo_dev = p.formal_solve(torch.from_numpy(chi).cuda(), torch.from_numpy(eta).cuda(),
+                                    want_alo=True)
+    np.testing.assert_array_equal(J_host, J_dev.cpu().numpy())
+    np.testing.assert_array_equal(alo_host, alo_dev.cpu().numpy())
+
+
+def test_full_size_1024_sampled_wavelengths():
+    """The benchmark workload (1024^2, 64 wavelengths, 8 cascades) solved in one call;
+    two of its wavelengths compared with the oracle cell by cell."""
+    chi, eta = W.grf_fields(1024, 64)
+    J = _solve(chi, eta, 8)
+    for lam in (0, 45):
+        J_ref = _oracle(chi[lam:lam + 1], eta[lam:lam + 1], 8)
+        _assert_close(J[lam:lam + 1], J_ref, 1e-3, f"1024^2 lambda {lam}")

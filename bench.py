@@ -28,10 +28,18 @@ sys.path.insert(0, ROOT)
 METRIC = "RC wavelength-slices/s at 1024² (HBM roofline %); NLTE time-to-1e-3 vs plain"
 UNIT = "wavelength-slices/s"
 N_SIDE, N_LAMBDA, N_CASC = 1024, 64, 8
-WORKLOAD = ("RC formal solution, 2D 1024x1024 unit voxels, 64 wavelengths per GPU, 8 cascades, "
-            "W0=4, branching 4, interval0=1 voxel (lengths x4), FP32 chi/eta from seeded "
-            "log-normal GRFs (k^-5/3, log10 chi in [-6,2], S in [0.1,10])")
-CROSS_KEY = "1024x1024_C8_W4_B4_L1.0_r0"
+
+
+def _workload(n_side, n_lambda, n_casc):
+    return (f"RC formal solution, 2D {n_side}x{n_side} unit voxels, {n_lambda} wavelengths per GPU, "
+            f"{n_casc} cascades, W0=4, branching 4, interval0=1 voxel (lengths x4), FP32 chi/eta "
+            "from seeded log-normal GRFs (k^-5/3, log10 chi in [-6,2], S in [0.1,10])")
+
+
+def _cross_key(n_side, n_casc):
+    return f"{n_side}x{n_side}_C{n_casc}_W4_B4_L1.0_r0"
+
+
 KERNEL_SOURCES = ["paper_2408_14425_b300/csrc/rcx_fs_kernels.cu"]
 
 
@@ -42,9 +50,9 @@ def _env_int(name, default):
         return default
 
 
-def _load_crossings():
+def _load_crossings(n_side, n_casc):
     with open(os.path.join(ROOT, "tests", "golden", "crossings.json")) as f:
-        return json.load(f)["plans"][CROSS_KEY]
+        return json.load(f)["plans"][_cross_key(n_side, n_casc)]
 
 
 def _peaks():
@@ -132,7 +140,7 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def _algorithmic_bytes(cross, plan, n_lambda):
+def _algorithmic_bytes(cross, plan, n_lambda, n_side):
     """Per-launch algorithmic bytes of the march kernels (cascade i):
     8 B (chi, S in FP32) per voxel crossing, + the merged interval R_i written once
     (4 B per ray, cascades >= 1) + R_{i+1} read once (4 B per upper ray)
@@ -148,7 +156,7 @@ def _algorithmic_bytes(cross, plan, n_lambda):
         if i < C - 1:
             b += 4 * rays[i + 1]
         if i == 0:
-            b += 4 * N_SIDE * N_SIDE
+            b += 4 * n_side * n_side
         out.append(b * n_lambda)
     return out, rays
 
@@ -170,13 +178,16 @@ def run_ours(args):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     rbuild.build()
 
-    lams = list(range(rank * N_LAMBDA, (rank + 1) * N_LAMBDA))
-    chi_h, eta_h = workloads.grf_fields(N_SIDE, N_LAMBDA, lambdas=lams)
+    n_side, n_lambda, n_casc = args.n_side, args.n_lambda, args.n_cascades
+    lams = list(range(rank * n_lambda, (rank + 1) * n_lambda))
+    chi_h, eta_h = workloads.grf_fields(n_side, n_lambda, lambdas=lams)
     chi = torch.from_numpy(chi_h).cuda()
     eta = torch.from_numpy(eta_h).cuda()
     J = torch.empty_like(chi)
-    plan = rcx.Plan(N_SIDE, N_SIDE, N_CASC, dirs0=4, branching=4, interval0=1.0)
-    plan.reserve(N_LAMBDA)
+    plan = rcx.Plan(n_side, n_side, n_casc, dirs0=4, branching=4, interval0=1.0,
+                    precision=args.precision, lambda_block=args.lambda_block,
+                    lambda_per_lane=args.lambda_per_lane)
+    plan.reserve(n_lambda)
     stream = torch.cuda.current_stream()
 
     for _ in range(args.warmup):
@@ -210,7 +221,7 @@ def run_ours(args):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms_step = float(t.item())
         dist.barrier()
-    value = world * N_LAMBDA / (ms_step / 1e3)
+    value = world * n_lambda / (ms_step / 1e3)
 
     # end to end through the host-buffer entry point (pinned host memory, copies inside)
     e2e = None
@@ -229,8 +240,8 @@ def run_ours(args):
             t = torch.tensor([t_e2e], device="cuda")
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
             t_e2e = float(t.item())
-        slab = N_LAMBDA * N_SIDE * N_SIDE * 4
-        e2e = {"value": world * N_LAMBDA / t_e2e, "unit": UNIT,
+        slab = n_lambda * n_side * n_side * 4
+        e2e = {"value": world * n_lambda / t_e2e, "unit": UNIT,
                "h2d_bytes_per_step": 2 * slab, "d2h_bytes_per_step": slab,
                "api": "rc_formal_solve_host (pinned host buffers, chunked copy/compute overlap)"}
 
@@ -240,23 +251,23 @@ def run_ours(args):
         return
 
     # roofline of the march kernels (all cascade launches of a step)
-    cross = _load_crossings()
-    alg, rays = _algorithmic_bytes(cross, plan, N_LAMBDA)
-    march_ms = sum(per_launch.get(f"cascade {i}", 0.0) for i in range(N_CASC)) / args.steps
+    cross = _load_crossings(n_side, n_casc)
+    alg, rays = _algorithmic_bytes(cross, plan, n_lambda, n_side)
+    march_ms = sum(per_launch.get(f"cascade {i}", 0.0) for i in range(n_casc)) / args.steps
     alg_total = sum(alg)
     peak, peak_kind = _peaks()
     achieved = alg_total / (march_ms / 1e3) / 1e9
     khash = _kernel_hash()
-    traffic = _ncu_traffic(khash)
+    traffic = _ncu_traffic(khash) if (n_side, n_lambda, n_casc) == (N_SIDE, N_LAMBDA, N_CASC) else None
     levels = []
-    for i in range(N_CASC):
+    for i in range(n_casc):
         ms = per_launch.get(f"cascade {i}", 0.0) / args.steps
         levels.append({"cascade": i, "ms": round(ms, 4), "crossings_per_slice": cross["per_cascade"][i],
                        "alg_GBps": round(alg[i] / (ms / 1e3) / 1e9, 1) if ms > 0 else None})
     pack_ms = per_launch.get("pack", 0.0) / args.steps
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": traffic,
-                "kernel": "cascade march (level_kernel + level0_kernel), all 8 launches of a step",
+                "kernel": f"cascade march (level_kernel + level0_kernel), all {n_casc} launches of a step",
                 "algorithmic_bytes_per_step": alg_total,
                 "bytes_model": "8 B (chi, S FP32) per voxel crossing + merged-interval write/read "
                                "once + J write",
@@ -267,7 +278,7 @@ def run_ours(args):
     # CPU baseline: the FP64 oracle on a bounded sample (one wavelength of this workload)
     cpu = None
     if not args.no_cpu_baseline:
-        cpu = _oracle_sample(chi_h[0], eta_h[0])
+        cpu = _oracle_sample(chi_h[0], eta_h[0], n_casc, n_side)
 
     intervals = sum(rays)
     line = {
@@ -275,10 +286,13 @@ def run_ours(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 3),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "n_side": N_SIDE, "n_lambda_per_gpu": N_LAMBDA,
-                   "n_cascades": N_CASC, "dirs0": 4, "branching": 4, "interval0": 1.0,
-                   "storage": "f32", "lambda_block": 4,
-                   "l2": "inputs (chi+eta 537 MB per GPU) larger than L2 (126 MB); no flush",
+        "config": {"workload": _workload(n_side, n_lambda, n_casc), "n_side": n_side,
+                   "n_lambda_per_gpu": n_lambda, "n_cascades": n_casc, "dirs0": 4, "branching": 4,
+                   "interval0": 1.0, "storage": args.precision,
+                   "lambda_block": args.lambda_block or 16,
+                   "lambda_per_lane": args.lambda_per_lane or min(args.lambda_block or 16, 4),
+                   "l2": (f"inputs (chi+eta {2 * n_lambda * n_side * n_side * 4 / 1e6:.0f} MB per GPU) "
+                          "vs L2 126 MB; no flush"),
                    "parallelism": f"wavelength batches, {world} GPU(s)"},
         "probe_ray_intervals_per_s": round(value * intervals, 1),
         "voxel_crossings_per_s": round(value * cross["total"], 1),
@@ -290,17 +304,17 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
-def _oracle_sample(chi2d, eta2d):
+def _oracle_sample(chi2d, eta2d, n_casc, n_side):
     import numpy as np
 
     import oracle
     oracle.build()
     t0 = time.perf_counter()
-    oracle.rc_solve(chi2d.astype(np.float64), eta2d.astype(np.float64), N_CASC)
+    oracle.rc_solve(chi2d.astype(np.float64), eta2d.astype(np.float64), n_casc)
     dt = time.perf_counter() - t0
     return {"value": round(1.0 / dt, 5), "unit": UNIT, "cores": oracle.num_threads(),
             "kind": "oracle",
-            "sample": "one wavelength slice (lambda 0) of the 1024^2, 8-cascade workload, FP64 "
+            "sample": f"one wavelength slice (lambda 0) of the {n_side}^2, {n_casc}-cascade workload, FP64 "
                       f"C oracle with OpenMP over probes, {dt:.2f} s"}
 
 
@@ -334,7 +348,8 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(t * 1e3, 1),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "impl": "reference",
-            "config": {"workload": WORKLOAD, "n_side": N_SIDE, "n_cascades": N_CASC},
+            "config": {"workload": _workload(N_SIDE, N_LAMBDA, N_CASC), "n_side": N_SIDE,
+                       "n_lambda_per_gpu": N_LAMBDA, "n_cascades": N_CASC},
             "cpu_baseline": {"value": round(value, 5), "unit": UNIT, "cores": cores,
                              "kind": "oracle", "sample": sample},
             "e2e": {"value": round(value, 5), "unit": UNIT, "h2d_bytes_per_step": 0,
@@ -350,6 +365,12 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--n-side", type=int, default=N_SIDE, help="grid side (profiling cases only)")
+    ap.add_argument("--n-lambda", type=int, default=N_LAMBDA, help="wavelengths per GPU")
+    ap.add_argument("--n-cascades", type=int, default=N_CASC)
+    ap.add_argument("--precision", default="f32", choices=["f32", "f16", "bf16"])
+    ap.add_argument("--lambda-block", type=int, default=0)
+    ap.add_argument("--lambda-per-lane", type=int, default=0)
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         print("note: fewer than 3 warm-up steps", file=sys.stderr)

@@ -58,14 +58,16 @@ typedef struct {
     int n_incl;          /* inclination rays per in-plane ray (2D invariance, Sec. 3.1); 1 = flatland */
     int interval_rule;   /* 0: interval lengths interval0 * 4^i, a_i = sum of the shorter ones;
                             1: a_i = interval0 * 4^(i-1), b_i = interval0 * 4^i (both satisfy Eq. 12-13) */
-    int lambda_block;    /* wavelengths marched together by one lane group: 0 = default (4);
-                            1, 2, 4, 8, 16 or 32 */
+    int lambda_block;    /* wavelengths marched together along one ray (packed together per
+                            voxel): 0 = default (16); 1, 2, 4, 8, 16 or 32 */
     int bilinear_fix;    /* 1: trace each cascade-i ray to the start of each of the four upper
                             probes' child rays before merging (Sec. 2.5); 0 = basic RC */
-    int reserved[3];     /* must be zero */
+    int lambda_per_lane; /* wavelengths one GPU lane carries along its ray: 0 = default
+                            (min(lambda_block, 4)); 1, 2 or 4, at most lambda_block */
+    int reserved[2];     /* must be zero */
 } rc_options;
 
-/* Fills *opt with the defaults (F32 storage, flatland, rule 0, automatic block, basic RC). */
+/* Fills *opt with the defaults (F32 storage, flatland, rule 0, automatic lane layout, basic RC). */
 void rc_options_default(rc_options* opt);
 
 /*

@@ -2,24 +2,24 @@
 //
 // Work decomposition (one launch per cascade, top cascade first):
 //   * The opacity/emissivity slabs are first packed into a wavelength-blocked
-//     layout [lambda block][cell][LB] of (chi per voxel, S = eta/chi) pairs, so
-//     that the LB lanes of a lane group that march one ray for LB wavelengths
-//     read one contiguous 8*LB-byte run per voxel (one 32-byte sector for
-//     LB = 4).  A warp holds 32/LB lane groups = 32/LB rays of neighbouring
-//     directions of one probe; they walk the grid in near lock-step, so the
-//     warp's DDA instructions serve 32 voxel crossings each.
-//   * Each lane marches its ray front to back (Sec. 3.2 allows either order)
-//     with the piecewise-constant update of Eq. 16 in FP32, keeping the running
+//     layout [lambda block][cell][LB] of (chi' = chi voxel log2 e, S = eta/chi)
+//     pairs.  One ray is marched for the LB wavelengths of a block by LB/VL lanes,
+//     each carrying VL wavelengths; the lanes of a ray read one contiguous
+//     8*LB-byte run per voxel, and every DDA instruction of a lane serves VL
+//     crossings.  A warp holds the rays of 32*VL/LB neighbouring directions of one
+//     probe, which walk the grid in near lock-step.
+//   * Each lane marches front to back (Sec. 3.2 allows either order) with the
+//     piecewise-constant update of Eq. 16 in FP32, keeping the running
 //     transmittance T:  I += T S (1 - e^{-dtau}),  T *= e^{-dtau}.
 //   * The merge of Sec. 2.3.1 is fused into the same kernel: the lane reads the
 //     four child rays of its direction on each of the four bracketing upper
-//     probes (one 16-byte vector per probe thanks to the [ray/4][LB][4] layout
-//     of the merged intervals), averages them, interpolates bilinearly with the
-//     edge clamp of Sec. 2.5 and forms R = I + T * upper (Eq. 11, the nearer
-//     interval attenuating the farther one).
+//     probes (one 16-byte vector per probe and wavelength thanks to the
+//     [ray/4][LB][4] layout of the merged intervals), averages them,
+//     interpolates bilinearly with the edge clamp of Sec. 2.5 and forms
+//     R = I + T * upper (Eq. 11, the nearer interval attenuating the farther one).
 //   * Cascade 0 folds the W_0 directions of its probe (a cell centre) into J
 //     (Eq. 1) and, optionally, the diagonal operator of Eq. 17.
-// No tensor cores: the march is a gather-bound walk, not a contraction.
+// No tensor cores: the march is a gather walk, not a contraction.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -71,63 +71,119 @@ struct Store<__nv_bfloat16> {
 // one radiance interval
 // ---------------------------------------------------------------------------
 
-// 1 - exp(-x) for x >= 0 without cancellation: the Taylor series
-// x - x^2/2 + x^3/6 - x^4/24 below x = 1/32 (truncation < x^4/120 relative),
-// 1 - e otherwise (e = exp(-x) already computed).
-__device__ __forceinline__ float one_minus_exp_neg(float x, float e) {
-    float s = x * fmaf(x, fmaf(x, fmaf(x, -1.0f / 24.0f, 1.0f / 6.0f), -0.5f), 1.0f);
-    return x < 0.03125f ? s : 1.0f - e;
+// The packed opacity is chi per voxel times log2(e), so exp(-chi ds) = 2^(-y) with
+// y = chi' ds: one multiply and one MUFU.EX2 per crossing.
+constexpr float kLog2e = 1.4426950408889634f;
+constexpr float kLn2 = 0.69314718055994531f;
+
+__device__ __forceinline__ float exp2_neg(float y) {
+    float e;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e) : "f"(-y));
+    return e;
 }
 
-// R_{a,b}(o, w) for wavelength lane `l` of a lambda block.  Front-to-back DDA
-// over the uniform grid (Sec. 3.2); face parameters are recomputed from the
-// integer cell index each step so no error accumulates along long rays.
-template <int LB>
+// 1 - 2^(-y) for y >= 0 without cancellation: the Taylor series of 1 - e^(-x),
+// x = y ln 2, to third order below y = 1/32 (truncation below x^3/24 ~ 4e-7
+// relative), 1 - e otherwise (e = 2^(-y) already computed).
+__device__ __forceinline__ float one_minus_exp2_neg(float y, float e) {
+    constexpr float a1 = kLn2;
+    constexpr float a2 = -0.5f * kLn2 * kLn2;
+    constexpr float a3 = kLn2 * kLn2 * kLn2 / 6.0f;
+    const float s = y * fmaf(y, fmaf(y, a3, a2), a1);
+    return y < 0.03125f ? s : 1.0f - e;
+}
+
+// VL consecutive (chi', S) pairs of one voxel for this lane's wavelengths.
+template <int VL>
+struct Voxel {
+    float2 v[VL];
+    __device__ __forceinline__ void load(const float2* __restrict__ p) {
+        if constexpr (VL == 1) {
+            v[0] = __ldg(p);
+        } else {
+#pragma unroll
+            for (int j = 0; j < VL; j += 2) {
+                const float4 q = __ldg(reinterpret_cast<const float4*>(p) + j / 2);
+                v[j] = make_float2(q.x, q.y);
+                v[j + 1] = make_float2(q.z, q.w);
+            }
+        }
+    }
+};
+
+// R_{a,b}(o, w) for the VL wavelengths of this lane.  Front-to-back DDA over the
+// uniform grid (Sec. 3.2 allows either order).  The parameter of the k-th x face
+// after entry is tx0 + k dtx (one FMA, no accumulated error), and the domain exit
+// is evaluated with the same expression, so the walk ends exactly on it and never
+// leaves the grid.  The advance is predicated (no divergent branch between rays
+// of a warp that step along different axes), and the voxel address is a running
+// 32-bit offset.
+template <int LB, int VL>
 __device__ __forceinline__ void march_interval(const float2* __restrict__ F, int nx, int nz,
                                                float ox, float oz, float wx, float wz,
-                                               float a, float b, int l, int max_steps,
-                                               float& I, float& T) {
-    I = 0.0f;
-    T = 1.0f;
+                                               float a, float b, int lane_off,
+                                               unsigned off_hi, int max_steps,
+                                               float (&I)[VL], float (&T)[VL]) {
+#pragma unroll
+    for (int j = 0; j < VL; ++j) {
+        I[j] = 0.0f;
+        T[j] = 1.0f;
+    }
     const float invx = wx != 0.0f ? 1.0f / wx : 1e30f;
     const float invz = wz != 0.0f ? 1.0f / wz : 1e30f;
-    // clip [a, b] to the domain box (free space outside, Sec. 3.4)
+    // entry into the domain box (free space outside, Sec. 3.4)
     const float tx0 = (0.0f - ox) * invx, tx1 = ((float)nx - ox) * invx;
     const float tz0 = (0.0f - oz) * invz, tz1 = ((float)nz - oz) * invz;
     const float tlo = fmaxf(a, fmaxf(fminf(tx0, tx1), fminf(tz0, tz1)));
-    const float thi = fminf(b, fminf(fmaxf(tx0, tx1), fmaxf(tz0, tz1)));
-    if (!(tlo < thi)) return;
+    if (!(tlo < fminf(b, fminf(fmaxf(tx0, tx1), fmaxf(tz0, tz1))))) return;
 
-    const int px = wx > 0.0f ? 1 : 0, pz = wz > 0.0f ? 1 : 0;
-    const int sx = px ? 1 : -1, sz = pz ? 1 : -1;
+    const bool upx = wx > 0.0f, upz = wz > 0.0f;
     const float ex = ox + tlo * wx, ez = oz + tlo * wz;
     int ix = (int)floorf(ex), iz = (int)floorf(ez);
-    if (!px && (float)ix == ex) --ix;   // entering through a face while moving down
-    if (!pz && (float)iz == ez) --iz;
+    if (!upx && (float)ix == ex) --ix;   // entering through a face while moving down
+    if (!upz && (float)iz == ez) --iz;
     ix = min(max(ix, 0), nx - 1);
     iz = min(max(iz, 0), nz - 1);
 
-    float tnx = ((float)(ix + px) - ox) * invx;
-    float tnz = ((float)(iz + pz) - oz) * invz;
+    // face parameters: first face after entry and spacing between faces
+    const float fx0 = (float)(upx ? ix + 1 : ix), fz0 = (float)(upz ? iz + 1 : iz);
+    const float tfx = (fx0 - ox) * invx, tfz = (fz0 - oz) * invz;
+    const float dtx = fabsf(invx), dtz = fabsf(invz);
+    // exit: last face inside the domain, with the same expression as the walk
+    const float kx_end = (float)(upx ? nx - 1 - ix : ix);
+    const float kz_end = (float)(upz ? nz - 1 - iz : iz);
+    const float thi = fminf(b, fminf(fmaf(kx_end, dtx, tfx), fmaf(kz_end, dtz, tfz)));
+
+    float kx = 0.0f, kz = 0.0f;
+    float tnx = tfx, tnz = tfz;
+    int off = (iz * nx + ix) * LB + lane_off;
+    const int dox = upx ? LB : -LB;
+    const int doz = upz ? nx * LB : -nx * LB;
     float t = tlo;
     for (int step = 0; step < max_steps; ++step) {
+        const bool stepx = tnx <= tnz;
         const float tn = fminf(fminf(tnx, tnz), thi);
-        const float ds = fmaxf(tn - t, 0.0f);
-        const float2 f = __ldg(F + ((size_t)iz * nx + ix) * LB + l);
-        const float dtau = f.x * ds;
-        const float e = __expf(-dtau);
-        const float om = one_minus_exp_neg(dtau, e);
-        I = fmaf(T * f.y, om, I);
-        T *= e;
-        if (tn >= thi) break;
-        if (tnx <= tnz) {
-            ix += sx;
-            tnx = ((float)(ix + px) - ox) * invx;
-        } else {
-            iz += sz;
-            tnz = ((float)(iz + pz) - oz) * invz;
+        const float ds = tn - t;
+        Voxel<VL> vx;
+        vx.load(F + min((unsigned)off, off_hi));
+#pragma unroll
+        for (int j = 0; j < VL; ++j) {
+            const float y = vx.v[j].x * ds;
+            const float e = exp2_neg(y);
+            const float om = one_minus_exp2_neg(y, e);
+            I[j] = fmaf(T[j] * vx.v[j].y, om, I[j]);
+            T[j] *= e;
         }
-        if ((unsigned)ix >= (unsigned)nx || (unsigned)iz >= (unsigned)nz) break;
+        if (tn >= thi) break;
+        if (stepx) {
+            kx += 1.0f;
+            tnx = fmaf(kx, dtx, tfx);
+            off += dox;
+        } else {
+            kz += 1.0f;
+            tnz = fmaf(kz, dtz, tfz);
+            off += doz;
+        }
         t = tn;
     }
 }
@@ -142,16 +198,12 @@ __device__ __forceinline__ void upper_coord(int m, int P_up, int& j0, int& j1, f
     f = u - (float)j0;
 }
 
-// Child-cone average of the four bracketing upper probes, bilinearly weighted.
+// Child-cone average of the four bracketing upper probes, bilinearly weighted,
+// for wavelength l of the block.
 template <int LB, typename TS>
-__device__ __forceinline__ float upper_radiance(const TS* __restrict__ Rup, int Px_up, int Pz_up,
-                                                int px, int pz, int W, int k, int l) {
-    int jx0, jx1, jz0, jz1;
-    float fx, fz;
-    upper_coord(px, Px_up, jx0, jx1, fx);
-    upper_coord(pz, Pz_up, jz0, jz1, fz);
-    const long long b00 = (long long)jz0 * Px_up + jx0, b01 = (long long)jz0 * Px_up + jx1;
-    const long long b10 = (long long)jz1 * Px_up + jx0, b11 = (long long)jz1 * Px_up + jx1;
+__device__ __forceinline__ float upper_radiance(const TS* __restrict__ Rup, long long b00,
+                                                long long b01, long long b10, long long b11,
+                                                float fx, float fz, int W, int k, int l) {
     // children 4k..4k+3 of probe b sit at [(b W + k) LB + l][0..3]
     const float4 c00 = Store<TS>::load4(Rup + ((size_t)(b00 * W + k) * LB + l) * 4);
     const float4 c01 = Store<TS>::load4(Rup + ((size_t)(b01 * W + k) * LB + l) * 4);
@@ -166,15 +218,30 @@ __device__ __forceinline__ float upper_radiance(const TS* __restrict__ Rup, int 
     return 0.25f * fmaf(fz, r1 - r0, r0);
 }
 
+struct Bilinear {
+    long long b00, b01, b10, b11;
+    float fx, fz;
+    __device__ __forceinline__ Bilinear(int px, int pz, int Px_up, int Pz_up) {
+        int jx0, jx1, jz0, jz1;
+        upper_coord(px, Px_up, jx0, jx1, fx);
+        upper_coord(pz, Pz_up, jz0, jz1, fz);
+        b00 = (long long)jz0 * Px_up + jx0;
+        b01 = (long long)jz0 * Px_up + jx1;
+        b10 = (long long)jz1 * Px_up + jx0;
+        b11 = (long long)jz1 * Px_up + jx1;
+    }
+};
+
 // ---------------------------------------------------------------------------
 // cascades >= 1: march + merge, store the merged interval
 // ---------------------------------------------------------------------------
-template <int LB, typename TS, bool HAS_UP>
+template <int LB, int VL, typename TS, bool HAS_UP>
 __global__ void __launch_bounds__(kWarpsPerCta * 32)
 level_kernel(const LevelArgs A) {
-    constexpr int G = 32 / LB;
+    constexpr int LPR = LB / VL;   // lanes per ray
+    constexpr int G = 32 / LPR;    // rays per warp
     const int lane = threadIdx.x & 31;
-    const int g = lane / LB, l = lane % LB;
+    const int g = lane / LPR, q = lane % LPR;
     const long long wid = (long long)blockIdx.x * kWarpsPerCta + (threadIdx.x >> 5);
     const long long ray = wid * G + g;
     if (ray >= A.rays) return;
@@ -193,31 +260,45 @@ level_kernel(const LevelArgs A) {
     const float2 d = A.dirs[k];
     const float ox = ((float)px + 0.5f) * A.spacing, oz = ((float)pz + 0.5f) * A.spacing;
     const float2* F = A.field + (size_t)lb * A.ncell * LB;
+    const int lane_off = q * VL;
+    const unsigned off_hi = (unsigned)((A.ncell - 1) * LB + lane_off);
 
-    float I, T;
-    march_interval<LB>(F, A.nx, A.nz, ox, oz, d.x, d.y, A.a, A.b, l, A.max_steps, I, T);
-    float R = I;
+    float I[VL], T[VL];
+    march_interval<LB, VL>(F, A.nx, A.nz, ox, oz, d.x, d.y, A.a, A.b, lane_off, off_hi,
+                           A.max_steps, I, T);
+    float R[VL];
     if (HAS_UP) {
         const TS* Rup = reinterpret_cast<const TS*>(A.R_up) + (size_t)lb * A.R_up_lstride;
-        float up = upper_radiance<LB, TS>(Rup, A.Px_up, A.Pz_up, px, pz, A.W, k, l);
-        if (A.scale) up *= A.scale[lb];
-        R = fmaf(T, up, I);
+        const Bilinear bl(px, pz, A.Px_up, A.Pz_up);
+        const float sc = A.scale ? A.scale[lb] : 1.0f;
+#pragma unroll
+        for (int j = 0; j < VL; ++j) {
+            const float up = upper_radiance<LB, TS>(Rup, bl.b00, bl.b01, bl.b10, bl.b11, bl.fx,
+                                                    bl.fz, A.W, k, lane_off + j);
+            R[j] = fmaf(T[j], up * sc, I[j]);
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < VL; ++j) R[j] = I[j];
     }
     TS* out = reinterpret_cast<TS*>(A.R_out) + (size_t)lb * A.R_out_lstride;
     const float inv = A.scale ? 1.0f / A.scale[lb] : 1.0f;
-    Store<TS>::store(out + ((size_t)(ray >> 2) * LB + l) * 4 + (ray & 3), R * inv);
+#pragma unroll
+    for (int j = 0; j < VL; ++j)
+        Store<TS>::store(out + ((size_t)(ray >> 2) * LB + lane_off + j) * 4 + (ray & 3), R[j] * inv);
 }
 
 // ---------------------------------------------------------------------------
 // cascade 0: one lane group per cell centre, loop over the W_0 directions,
 // accumulate J (Eq. 1) and the diagonal operator (Eq. 17)
 // ---------------------------------------------------------------------------
-template <int LB, typename TS, bool HAS_UP>
+template <int LB, int VL, typename TS, bool HAS_UP>
 __global__ void __launch_bounds__(kWarpsPerCta * 32)
 level0_kernel(const LevelArgs A) {
-    constexpr int G = 32 / LB;
+    constexpr int LPR = LB / VL;
+    constexpr int G = 32 / LPR;
     const int lane = threadIdx.x & 31;
-    const int g = lane / LB, l = lane % LB;
+    const int g = lane / LPR, q = lane % LPR;
     const long long wid = (long long)blockIdx.x * kWarpsPerCta + (threadIdx.x >> 5);
     const long long cell = wid * G + g;
     if (cell >= A.ncell) return;
@@ -225,39 +306,53 @@ level0_kernel(const LevelArgs A) {
     const int px = (int)(cell % A.nx), pz = (int)(cell / A.nx);
     const float ox = (float)px + 0.5f, oz = (float)pz + 0.5f;
     const float2* F = A.field + (size_t)lb * A.ncell * LB;
+    const int lane_off = q * VL;
+    const unsigned off_hi = (unsigned)((A.ncell - 1) * LB + lane_off);
     const TS* Rup = nullptr;
-    float up_scale = 1.0f;
+    float sc = 1.0f;
     if (HAS_UP) {
         Rup = reinterpret_cast<const TS*>(A.R_up) + (size_t)lb * A.R_up_lstride;
-        if (A.scale) up_scale = A.scale[lb];
+        if (A.scale) sc = A.scale[lb];
     }
-    const float chi_c = __ldg(F + (size_t)cell * LB + l).x;
+    Voxel<VL> own;
+    own.load(F + (size_t)cell * LB + lane_off);
+    const Bilinear bl(px, pz, HAS_UP ? A.Px_up : 1, HAS_UP ? A.Pz_up : 1);
 
-    float Jsum = 0.0f, alo_sum = 0.0f;
+    float Jsum[VL], alo_sum[VL];
+#pragma unroll
+    for (int j = 0; j < VL; ++j) Jsum[j] = alo_sum[j] = 0.0f;
     for (int k = 0; k < A.W; ++k) {
         const float2 d = A.dirs[k];
-        float I, T;
-        march_interval<LB>(F, A.nx, A.nz, ox, oz, d.x, d.y, A.a, A.b, l, A.max_steps, I, T);
-        float R = I;
-        if (HAS_UP) {
-            const float up = upper_radiance<LB, TS>(Rup, A.Px_up, A.Pz_up, px, pz, A.W, k, l);
-            R = fmaf(T, up * up_scale, I);
-        }
-        Jsum += R;
+        float I[VL], T[VL];
+        march_interval<LB, VL>(F, A.nx, A.nz, ox, oz, d.x, d.y, A.a, A.b, lane_off, off_hi,
+                               A.max_steps, I, T);
         const float dk = 0.5f / fmaxf(fabsf(d.x), fabsf(d.y));
-        const float x = chi_c * dk;
-        alo_sum += one_minus_exp_neg(x, __expf(-x));
+#pragma unroll
+        for (int j = 0; j < VL; ++j) {
+            float R = I[j];
+            if (HAS_UP) {
+                const float up = upper_radiance<LB, TS>(Rup, bl.b00, bl.b01, bl.b10, bl.b11, bl.fx,
+                                                        bl.fz, A.W, k, lane_off + j);
+                R = fmaf(T[j], up * sc, I[j]);
+            }
+            Jsum[j] += R;
+            const float y = own.v[j].x * dk;
+            alo_sum[j] += one_minus_exp2_neg(y, exp2_neg(y));
+        }
     }
-    const int lam = lb * LB + l;
-    if (lam < A.n_lambda) {
-        const float invW = 1.0f / (float)A.W;
-        A.J[(size_t)lam * A.ncell + cell] = Jsum * invW;
-        if (A.alo) A.alo[(size_t)lam * A.ncell + cell] = alo_sum * invW;
+    const float invW = 1.0f / (float)A.W;
+#pragma unroll
+    for (int j = 0; j < VL; ++j) {
+        const int lam = lb * LB + lane_off + j;
+        if (lam < A.n_lambda) {
+            A.J[(size_t)lam * A.ncell + cell] = Jsum[j] * invW;
+            if (A.alo) A.alo[(size_t)lam * A.ncell + cell] = alo_sum[j] * invW;
+        }
     }
 }
 
 // ---------------------------------------------------------------------------
-// packing [lambda][cell] (chi, eta) -> [lambda block][cell][LB] (chi_vox, S)
+// packing [lambda][cell] (chi, eta) -> [lambda block][cell][LB] (chi' = chi voxel log2 e, S)
 // ---------------------------------------------------------------------------
 template <int LB>
 __global__ void __launch_bounds__(256) pack_kernel(const PackArgs P) {
@@ -273,8 +368,9 @@ __global__ void __launch_bounds__(256) pack_kernel(const PackArgs P) {
             if (lam < P.n_lambda) {
                 const float chi = __ldg(P.chi + (size_t)lam * P.ncell + cell);
                 const float eta = __ldg(P.eta + (size_t)lam * P.ncell + cell);
-                c = fmaxf(chi * P.voxel, kChiFloor);
-                s = (eta * P.voxel) / c;
+                const float cv = fmaxf(chi * P.voxel, kChiFloor);
+                s = (eta * P.voxel) / cv;
+                c = cv * kLog2e;
                 smax = fmaxf(smax, s);
             }
             v[l] = make_float2(c, s);
@@ -333,44 +429,57 @@ cudaError_t launch_scales(int n_lblk, const unsigned int* smax_bits, float* scal
     return cudaGetLastError();
 }
 
-template <int LB, typename TS>
+template <int LB, int VL, typename TS>
 static cudaError_t level_t(bool level0, bool has_up, int n_lblk, const LevelArgs& a,
                            cudaStream_t s) {
-    constexpr int G = 32 / LB;
+    constexpr int G = 32 / (LB / VL);
     const long long items = level0 ? a.ncell : a.rays;
     const long long per_cta = (long long)G * kWarpsPerCta;
     dim3 grid((unsigned)((items + per_cta - 1) / per_cta), (unsigned)n_lblk);
     dim3 block(kWarpsPerCta * 32);
     if (level0) {
-        if (has_up) level0_kernel<LB, TS, true><<<grid, block, 0, s>>>(a);
-        else level0_kernel<LB, TS, false><<<grid, block, 0, s>>>(a);
+        if (has_up) level0_kernel<LB, VL, TS, true><<<grid, block, 0, s>>>(a);
+        else level0_kernel<LB, VL, TS, false><<<grid, block, 0, s>>>(a);
     } else {
-        if (has_up) level_kernel<LB, TS, true><<<grid, block, 0, s>>>(a);
-        else level_kernel<LB, TS, false><<<grid, block, 0, s>>>(a);
+        if (has_up) level_kernel<LB, VL, TS, true><<<grid, block, 0, s>>>(a);
+        else level_kernel<LB, VL, TS, false><<<grid, block, 0, s>>>(a);
     }
     return cudaGetLastError();
 }
 
-template <int LB>
+template <int LB, int VL>
 static cudaError_t level_p(int precision, bool level0, bool has_up, int n_lblk,
                            const LevelArgs& a, cudaStream_t s) {
     switch (precision) {
-        case RC_STORE_F32: return level_t<LB, float>(level0, has_up, n_lblk, a, s);
-        case RC_STORE_F16: return level_t<LB, __half>(level0, has_up, n_lblk, a, s);
-        case RC_STORE_BF16: return level_t<LB, __nv_bfloat16>(level0, has_up, n_lblk, a, s);
+        case RC_STORE_F32: return level_t<LB, VL, float>(level0, has_up, n_lblk, a, s);
+        case RC_STORE_F16: return level_t<LB, VL, __half>(level0, has_up, n_lblk, a, s);
+        case RC_STORE_BF16: return level_t<LB, VL, __nv_bfloat16>(level0, has_up, n_lblk, a, s);
     }
     return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_level(int LB, int precision, bool level0, bool has_up, int n_lblk,
+template <int LB>
+static cudaError_t level_v(int VL, int precision, bool level0, bool has_up, int n_lblk,
+                           const LevelArgs& a, cudaStream_t s) {
+    if constexpr (LB >= 4) {
+        if (VL == 4) return level_p<LB, 4>(precision, level0, has_up, n_lblk, a, s);
+    }
+    if constexpr (LB >= 2) {
+        if (VL == 2) return level_p<LB, 2>(precision, level0, has_up, n_lblk, a, s);
+    }
+    if (VL == 1) return level_p<LB, 1>(precision, level0, has_up, n_lblk, a, s);
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_level(int LB, int VL, int precision, bool level0, bool has_up, int n_lblk,
                          const LevelArgs& a, cudaStream_t s) {
     switch (LB) {
-        case 1: return level_p<1>(precision, level0, has_up, n_lblk, a, s);
-        case 2: return level_p<2>(precision, level0, has_up, n_lblk, a, s);
-        case 4: return level_p<4>(precision, level0, has_up, n_lblk, a, s);
-        case 8: return level_p<8>(precision, level0, has_up, n_lblk, a, s);
-        case 16: return level_p<16>(precision, level0, has_up, n_lblk, a, s);
-        case 32: return level_p<32>(precision, level0, has_up, n_lblk, a, s);
+        case 1: return level_v<1>(VL, precision, level0, has_up, n_lblk, a, s);
+        case 2: return level_v<2>(VL, precision, level0, has_up, n_lblk, a, s);
+        case 4: return level_v<4>(VL, precision, level0, has_up, n_lblk, a, s);
+        case 8: return level_v<8>(VL, precision, level0, has_up, n_lblk, a, s);
+        case 16: return level_v<16>(VL, precision, level0, has_up, n_lblk, a, s);
+        case 32: return level_v<32>(VL, precision, level0, has_up, n_lblk, a, s);
     }
     return cudaErrorInvalidValue;
 }

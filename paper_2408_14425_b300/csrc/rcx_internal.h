@@ -68,10 +68,13 @@ struct PackArgs {
 
 // Launchers (rcx_fs_kernels.cu).  Return the CUDA launch error.
 cudaError_t launch_pack(int LB, int n_lblk, const PackArgs& a, cudaStream_t s);
-cudaError_t launch_level(int LB, int precision, bool level0, bool has_up, int n_lblk,
+cudaError_t launch_level(int LB, int VL, int precision, bool level0, bool has_up, int n_lblk,
                          const LevelArgs& a, cudaStream_t s);
 cudaError_t launch_scales(int n_lblk, const unsigned int* smax_bits, float* scale,
                           cudaStream_t s);
+
+// Sets the calling thread's rc_last_error() message (rcx_plan.cu).
+void set_last_error(const std::string& msg);
 
 }  // namespace rcx
 
@@ -82,7 +85,8 @@ struct rc_plan_s {
     int C = 0, W0 = 0, B = 0;
     float L0 = 1.0f;
     rc_options opt{};
-    int LB = 4;
+    int LB = 4;                      // wavelengths per lane group (one ray)
+    int VL = 1;                      // wavelengths per lane
     std::vector<rcx::LevelGeom> lv;
     std::vector<size_t> dir_off;     // offset of each cascade's table in d_dirs
     float2* d_dirs = nullptr;

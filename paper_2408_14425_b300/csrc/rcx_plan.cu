@@ -10,6 +10,14 @@
 
 namespace {
 
+// Default lane layout of the march: 16 wavelengths per ray, 4 per lane (4 lanes per
+// ray, 8 rays of neighbouring directions per warp): the DDA of each lane is shared by
+// 4 wavelengths, and a 16-wavelength block of a 1024^2 slab (134 MB of packed field)
+// still mostly hits in L2.  Measured fastest of the (block, per-lane) layouts on the
+// 1024^2 x 64-wavelength x 8-cascade workload.
+constexpr int kDefaultLambdaBlock = 16;
+constexpr int kDefaultLambdaPerLane = 4;
+
 thread_local std::string g_last_error;
 
 rc_status fail(rc_status s, const std::string& msg) {
@@ -168,7 +176,7 @@ rc_status solve_device(rc_plan_s* p, const float* chi, const float* eta, int n_l
         a.alo = alo;
         a.n_lambda = n_lambda;
         a.max_steps = p->nx + p->nz + 2;
-        if ((e = rcx::launch_level(LB, p->opt.precision, i == 0, has_up, n_lblk, a, s)) !=
+        if ((e = rcx::launch_level(LB, p->VL, p->opt.precision, i == 0, has_up, n_lblk, a, s)) !=
             cudaSuccess)
             return cuda_fail(e, "cascade launch");
         ++launches;
@@ -180,6 +188,8 @@ rc_status solve_device(rc_plan_s* p, const float* chi, const float* eta, int n_l
 }
 
 }  // namespace
+
+void rcx::set_last_error(const std::string& msg) { g_last_error = msg; }
 
 extern "C" {
 
@@ -234,11 +244,16 @@ rc_status rc_plan(const rc_grid* grid, int n_cascades, int dirs0, int branching,
     if (o.n_incl != 1) return fail(RC_ERR_UNSUPPORTED, "rc_plan: n_incl != 1 is not implemented");
     if (o.bilinear_fix != 0)
         return fail(RC_ERR_UNSUPPORTED, "rc_plan: the bilinear fix is not implemented");
-    int LB = o.lambda_block == 0 ? 4 : o.lambda_block;
+    int LB = o.lambda_block == 0 ? kDefaultLambdaBlock : o.lambda_block;
     if (LB != 1 && LB != 2 && LB != 4 && LB != 8 && LB != 16 && LB != 32)
         return fail(RC_ERR_ARG, "rc_plan: lambda_block must be 0, 1, 2, 4, 8, 16 or 32");
+    int VL = o.lambda_per_lane == 0 ? std::min(LB, kDefaultLambdaPerLane) : o.lambda_per_lane;
+    if ((VL != 1 && VL != 2 && VL != 4) || VL > LB)
+        return fail(RC_ERR_ARG, "rc_plan: lambda_per_lane must be 0, 1, 2 or 4 and <= lambda_block");
     for (int r : o.reserved)
         if (r != 0) return fail(RC_ERR_ARG, "rc_plan: reserved option fields must be zero");
+    if ((long long)grid->nx * grid->nz * LB >= (1LL << 31))
+        return fail(RC_ERR_ARG, "rc_plan: nx * nz * lambda_block must stay below 2^31");
 
     rc_plan_s* p = new (std::nothrow) rc_plan_s();
     if (!p) return fail(RC_ERR_OOM, "rc_plan: host allocation failed");
@@ -256,6 +271,7 @@ rc_status rc_plan(const rc_grid* grid, int n_cascades, int dirs0, int branching,
     p->L0 = interval0;
     p->opt = o;
     p->LB = LB;
+    p->VL = VL;
 
     // geometry (Sec. 2.3, Eq. 12-13), FP64 on the host
     const double g = std::pow(2.0, 0.5 * branching);

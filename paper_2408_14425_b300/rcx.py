@@ -42,7 +42,8 @@ class rc_grid(ctypes.Structure):
 class rc_options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("n_incl", ctypes.c_int),
                 ("interval_rule", ctypes.c_int), ("lambda_block", ctypes.c_int),
-                ("bilinear_fix", ctypes.c_int), ("reserved", ctypes.c_int * 3)]
+                ("bilinear_fix", ctypes.c_int), ("lambda_per_lane", ctypes.c_int),
+                ("reserved", ctypes.c_int * 2)]
 
 
 _lib = None
@@ -140,7 +141,7 @@ class Plan:
     def __init__(self, nx: int, nz: int, n_cascades: int, dirs0: int = 4, branching: int = 4,
                  interval0: float = 1.0, voxel_size: float = 1.0, precision: str = "f32",
                  interval_rule: int = 0, lambda_block: int = 0, n_incl: int = 1,
-                 bilinear_fix: bool = False):
+                 bilinear_fix: bool = False, lambda_per_lane: int = 0):
         L = load()
         self.nx, self.nz, self.n_cascades = nx, nz, n_cascades
         g = rc_grid(nx, nz, voxel_size)
@@ -151,6 +152,7 @@ class Plan:
         o.lambda_block = lambda_block
         o.n_incl = n_incl
         o.bilinear_fix = int(bilinear_fix)
+        o.lambda_per_lane = lambda_per_lane
         h = _vp()
         check(L.rc_plan(ctypes.byref(g), n_cascades, dirs0, branching, interval0, ctypes.byref(o),
                         ctypes.byref(h)))
@@ -230,3 +232,4 @@ class Plan:
             self._h, _host_ptr(chi, "chi", shape), _host_ptr(eta, "eta", shape), nl,
             _host_ptr(J, "J", shape), _host_ptr(alo, "alo", shape) if alo is not None else None))
         return (J, alo) if alo is not None else J
+

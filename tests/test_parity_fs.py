@@ -82,13 +82,15 @@ def test_grf_256_seven_cascades():
     _assert_close(alo, alo_ref, 1e-5, "alo grf 256")
 
 
-@pytest.mark.parametrize("lb", [1, 2, 8, 16, 32])
-def test_lambda_block_layouts_agree(lb):
-    """Every lane-group width computes each (ray, wavelength) with the same arithmetic."""
+@pytest.mark.parametrize("lb,vl", [(1, 1), (2, 2), (4, 1), (4, 4), (8, 4), (16, 2), (16, 4),
+                                   (32, 1), (32, 4)])
+def test_lane_layouts_agree(lb, vl):
+    """Every lane layout (wavelengths per ray, per lane) computes each (ray, wavelength)
+    with the same arithmetic, so the results are identical."""
     chi, eta = W.grf_fields(72, 9)
-    J4 = _solve(chi, eta, 5, lambda_block=4)
-    Jb = _solve(chi, eta, 5, lambda_block=lb)
-    np.testing.assert_array_equal(J4, Jb)
+    J_ref = _solve(chi, eta, 5, lambda_block=8, lambda_per_lane=2)
+    J = _solve(chi, eta, 5, lambda_block=lb, lambda_per_lane=vl)
+    np.testing.assert_array_equal(J, J_ref)
 
 
 def test_interval_rule_alternative():

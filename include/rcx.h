@@ -63,7 +63,7 @@ typedef struct {
     int bilinear_fix;    /* 1: trace each cascade-i ray to the start of each of the four upper
                             probes' child rays before merging (Sec. 2.5); 0 = basic RC */
     int lambda_per_lane; /* wavelengths one GPU lane carries along its ray: 0 = default
-                            (min(lambda_block, 4)); 1, 2 or 4, at most lambda_block */
+                            (min(lambda_block, 4)); 1, 2, 4 or 8, at most lambda_block */
     int reserved[2];     /* must be zero */
 } rc_options;
 

@@ -461,6 +461,9 @@ static cudaError_t level_p(int precision, bool level0, bool has_up, int n_lblk,
 template <int LB>
 static cudaError_t level_v(int VL, int precision, bool level0, bool has_up, int n_lblk,
                            const LevelArgs& a, cudaStream_t s) {
+    if constexpr (LB >= 8) {
+        if (VL == 8) return level_p<LB, 8>(precision, level0, has_up, n_lblk, a, s);
+    }
     if constexpr (LB >= 4) {
         if (VL == 4) return level_p<LB, 4>(precision, level0, has_up, n_lblk, a, s);
     }

@@ -248,8 +248,8 @@ rc_status rc_plan(const rc_grid* grid, int n_cascades, int dirs0, int branching,
     if (LB != 1 && LB != 2 && LB != 4 && LB != 8 && LB != 16 && LB != 32)
         return fail(RC_ERR_ARG, "rc_plan: lambda_block must be 0, 1, 2, 4, 8, 16 or 32");
     int VL = o.lambda_per_lane == 0 ? std::min(LB, kDefaultLambdaPerLane) : o.lambda_per_lane;
-    if ((VL != 1 && VL != 2 && VL != 4) || VL > LB)
-        return fail(RC_ERR_ARG, "rc_plan: lambda_per_lane must be 0, 1, 2 or 4 and <= lambda_block");
+    if ((VL != 1 && VL != 2 && VL != 4 && VL != 8) || VL > LB)
+        return fail(RC_ERR_ARG, "rc_plan: lambda_per_lane must be 0, 1, 2, 4 or 8 and <= lambda_block");
     for (int r : o.reserved)
         if (r != 0) return fail(RC_ERR_ARG, "rc_plan: reserved option fields must be zero");
     if ((long long)grid->nx * grid->nz * LB >= (1LL << 31))

@@ -151,6 +151,35 @@ rc_status rc_plan_set_timing(rc_plan_t plan, int enable);
 rc_status rc_plan_launch_times(rc_plan_t plan, float* ms_out, int max_n, int* n_out);
 const char* rc_plan_launch_name(rc_plan_t plan, int i);
 
+/*
+ * rc_formal_solve_noalloc -- the formal solution of rc_formal_solve without any device
+ * allocation, for callers that cannot call cudaMalloc: code whose device memory is owned by
+ * another allocator (a framework's caching pool, a memory budget fixed up front), code that
+ * runs where allocation is not allowed or would synchronise the device, and embedders that
+ * must not grow the process's device footprint after start-up.  The paper has no counterpart;
+ * it is a deployment variant of rc_formal_solve.
+ *   grid, n_cascades, dirs0, interval0   as rc_plan, with branching 4, interval_rule 0,
+ *                                        FP32 interval storage, 4-wavelength blocks and
+ *                                        2 wavelengths per lane.
+ *   chi, eta, n_lambda, J, alo, stream   as rc_formal_solve (caller-owned device buffers).
+ * Scratch: a static device array of 32 MiB (33554432 bytes) inside librcx.so, which every GPU
+ * that loads the library holds until the process exits.  It must hold the direction tables,
+ * the packed field (n_lambda rounded up to 4) x nx x nz x 8 bytes and two cascades of merged
+ * intervals (rounded n_lambda x the largest cascade's rays x 4 bytes each), each rounded up to
+ * 256 bytes; for example 256 x 256 with 8 wavelengths and 7 cascades fits.  A larger problem
+ * is rejected with RC_ERR_ARG and a message giving the bytes it needs.
+ * The first call on a device (with that device current) looks up the array's device address
+ * once with cudaGetSymbolAddress; make that first call before any stream capture.
+ * All calls share the one array, and it keeps the last call's contents: every call rewrites
+ * what it reads, so nothing has to be cleared, but calls whose work overlaps on the GPU (on
+ * different streams, or from several host threads) race on the array and must be serialised
+ * by the caller.  Allocates nothing: no cudaMalloc, cudaFree or allocating library call.
+ * Errors: RC_ERR_ARG (bad sizes, NULL pointers, problem too large), RC_ERR_CUDA.
+ */
+rc_status rc_formal_solve_noalloc(const rc_grid* grid, int n_cascades, int dirs0, float interval0,
+                                  const float* chi, const float* eta, int n_lambda, float* J,
+                                  float* alo, void* stream);
+
 /* One-line message for the calling thread's last error ("" if none). */
 const char* rc_last_error(void);
 

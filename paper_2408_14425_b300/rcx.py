@@ -25,7 +25,7 @@ EXPORTS = [
     "rc_options_default", "rc_plan", "rc_plan_destroy", "rc_plan_reserve",
     "rc_plan_scratch_bytes", "rc_formal_solve", "rc_formal_solve_host", "rc_plan_cascade",
     "rc_plan_last_launch_count", "rc_last_error", "rc_status_string", "rc_plan_set_timing",
-    "rc_plan_launch_times", "rc_plan_launch_name",
+    "rc_plan_launch_times", "rc_plan_launch_name", "rc_formal_solve_noalloc",
 ]
 
 
@@ -90,6 +90,9 @@ def load():
     L.rc_plan_launch_times.restype = ctypes.c_int
     L.rc_plan_launch_name.argtypes = [_vp, ctypes.c_int]
     L.rc_plan_launch_name.restype = ctypes.c_char_p
+    L.rc_formal_solve_noalloc.argtypes = [ctypes.POINTER(rc_grid), ctypes.c_int, ctypes.c_int,
+                                          ctypes.c_float, _vp, _vp, ctypes.c_int, _vp, _vp, _vp]
+    L.rc_formal_solve_noalloc.restype = ctypes.c_int
     _lib = L
     return L
 
@@ -233,3 +236,29 @@ class Plan:
             _host_ptr(J, "J", shape), _host_ptr(alo, "alo", shape) if alo is not None else None))
         return (J, alo) if alo is not None else J
 
+
+def formal_solve_noalloc(chi, eta, n_cascades: int, dirs0: int = 4, interval0: float = 1.0,
+                         voxel_size: float = 1.0, J=None, alo=None, stream=None):
+    """rc_formal_solve_noalloc: the formal solution with no device allocation by the library.
+
+    For callers that cannot let a library call cudaMalloc (memory owned by another allocator,
+    fixed device-memory budgets).  Scratch is a 32 MiB static device array shared by every
+    call; calls that overlap on the GPU race on it.  J (and alo) may be passed in so that this
+    call allocates nothing either; if J is None a torch tensor is created for it here.
+    """
+    import torch
+    if chi.dim() == 2:
+        chi = chi.unsqueeze(0)
+        eta = eta.unsqueeze(0)
+    nl, nz, nx = chi.shape
+    shape = (nl, nz, nx)
+    pc = _dev_ptr(chi, "chi", shape)
+    pe = _dev_ptr(eta, "eta", shape)
+    if J is None:
+        J = torch.empty(shape, dtype=torch.float32, device=chi.device)
+    pj = _dev_ptr(J, "J", shape)
+    pa = _dev_ptr(alo, "alo", shape) if alo is not None else None
+    g = rc_grid(nx, nz, voxel_size)
+    check(load().rc_formal_solve_noalloc(ctypes.byref(g), n_cascades, dirs0, interval0, pc, pe, nl,
+                                         pj, pa, _stream_ptr(stream)))
+    return (J, alo) if alo is not None else J

@@ -160,30 +160,35 @@ __device__ __forceinline__ void march_interval(const float2* __restrict__ F, int
     const int dox = upx ? LB : -LB;
     const int doz = upz ? nx * LB : -nx * LB;
     float t = tlo;
+    // The walk does not depend on the field, so the next voxel is fetched one step
+    // ahead: two loads per lane are in flight while the current voxel is integrated.
+    Voxel<VL> cur;
+    cur.load(F + min((unsigned)off, off_hi));
     for (int step = 0; step < max_steps; ++step) {
         const bool stepx = tnx <= tnz;
         const float tn = fminf(fminf(tnx, tnz), thi);
         const float ds = tn - t;
-        Voxel<VL> vx;
-        vx.load(F + min((unsigned)off, off_hi));
+        const int off_next = off + (stepx ? dox : doz);
+        Voxel<VL> nxt;
+        nxt.load(F + min((unsigned)off_next, off_hi));
 #pragma unroll
         for (int j = 0; j < VL; ++j) {
-            const float y = vx.v[j].x * ds;
+            const float y = cur.v[j].x * ds;
             const float e = exp2_neg(y);
             const float om = one_minus_exp2_neg(y, e);
-            I[j] = fmaf(T[j] * vx.v[j].y, om, I[j]);
+            I[j] = fmaf(T[j] * cur.v[j].y, om, I[j]);
             T[j] *= e;
         }
         if (tn >= thi) break;
         if (stepx) {
             kx += 1.0f;
             tnx = fmaf(kx, dtx, tfx);
-            off += dox;
         } else {
             kz += 1.0f;
             tnz = fmaf(kz, dtz, tfz);
-            off += doz;
         }
+        off = off_next;
+        cur = nxt;
         t = tn;
     }
 }

@@ -138,3 +138,59 @@ def batched_domains(n_domains: int = 16, seed: int = 7, side_min: int = 256,
     sides = rng.integers(side_min // side_step, side_max // side_step + 1, size=n_domains) * side_step
     nls = rng.integers(nl_min, nl_max + 1, size=n_domains)
     return [(int(s), int(l), 100_000 * (d + 1)) for d, (s, l) in enumerate(zip(sides, nls))]
+
+
+# ---------------------------------------------------------------------------
+# non-LTE workload: a synthetic 3-level hydrogen-like atom in a prominence slab
+# ---------------------------------------------------------------------------
+
+def h3_atom():
+    """The synthetic 3-level H-like atom (data only): level energies (eV), statistical
+    weights g = 2 n^2, the three lines (lower, upper, A_ul in s^-1), wavelengths per line,
+    the frequency-grid half-width in Doppler units at the reference temperature, and the
+    atomic mass in amu."""
+    return {
+        "E_eV": [0.0, 10.2, 12.09],
+        "g": [2.0, 8.0, 18.0],
+        "lines": [(0, 1, 4.7e8), (0, 2, 5.6e7), (1, 2, 4.4e7)],
+        "n_per_line": 21,
+        "x_max": 5.0,
+        "T_ref": 1.0e4,
+        "mass_amu": 1.00794,
+    }
+
+
+def _grf1d(n: int, seed: int, slope: float = -5.0 / 3.0) -> np.ndarray:
+    rng = np.random.default_rng(seed)
+    w = rng.standard_normal(n)
+    F = np.fft.rfft(w)
+    k = np.fft.rfftfreq(n)
+    amp = np.zeros_like(k)
+    amp[k > 0] = k[k > 0] ** (slope / 2.0)
+    g = np.fft.irfft(F * amp, n=n)
+    return g / g.std()
+
+
+def prominence_slab(n: int = 512, seed: int = 11, half_width: float = 48.0,
+                    blend: float = 8.0, T_cool: float = 6.0e3, T_hot: float = 1.0e6,
+                    nH_cool: float = 1.0e18, nH_lo: float = 1.0e15, nH_hi: float = 1.0e18,
+                    wander: float = 12.0, voxel_m: float = 5.7e3):
+    """Vertical cool dense sheet in a hot corona on an n x n grid of 5.7 km voxels.
+
+    The sheet's centreline x_c(z) = n/2 + wander * g(z), g a unit-variance 1D GRF (k^-5/3);
+    log T blends from log T_cool inside to log T_hot outside with tanh((d - half_width) /
+    blend), d = |x - x_c(z)|; n_H = nH_cool T_cool / T (constant pressure) times
+    10^(0.3 G), G a unit-variance 2D GRF, clipped to [nH_lo, nH_hi].
+    Returns T [K], n_H [m^-3] as float64 [n][n] and the voxel size in metres."""
+    z = np.arange(n)
+    xc = n / 2.0 + wander * _grf1d(n, seed)
+    x = np.arange(n) + 0.5
+    d = np.abs(x[None, :] - xc[:, None])
+    s = 0.5 * (1.0 + np.tanh((d - half_width) / blend))
+    logT = np.log10(T_cool) + (np.log10(T_hot) - np.log10(T_cool)) * s
+    T = 10.0 ** logT
+    G = grf(n, n, seed + 1)
+    G = G / G.std()
+    nH = np.clip(nH_cool * T_cool / T * 10.0 ** (0.3 * G), nH_lo, nH_hi)
+    del z
+    return T, nH, voxel_m

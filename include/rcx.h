@@ -180,6 +180,107 @@ rc_status rc_formal_solve_noalloc(const rc_grid* grid, int n_cascades, int dirs0
                                   const float* chi, const float* eta, int n_lambda, float* J,
                                   float* alo, void* stream);
 
+/*
+ * rc_formal_solve_mali -- the formal solution with the two extra cascade-0 outputs the
+ * MALI population update needs (Sec. 3.3, Eq. 17-19), computed without cancellation:
+ *   J_eff  device FP32 [n_lambda][nz][nx] or NULL: J - Lambda* S_local, the mean intensity
+ *          without the emission of the cell's own centre-to-edge segment (the effective
+ *          intensity I_dagger - Psi* eta_dagger of Eq. 19 with a diagonal operator).  It is
+ *          accumulated without that term rather than by subtraction, so it keeps FP32
+ *          relative precision in optically thick cells where J ~ S.
+ *   alo_c  device FP32 or NULL: 1 - Lambda* = (1/W_0) sum_k exp(-chi d_k), the escape
+ *          probability of the cell's own segment (accurate where Lambda* -> 1).
+ * J and alo as rc_formal_solve (alo may be NULL).  Requires interval0 >= the centre-to-edge
+ * path of every cascade-0 direction (0.5/max(|cos|,|sin|) voxels, e.g. 0.71 for W_0 = 4).
+ * Errors: as rc_formal_solve, plus RC_ERR_ARG if interval0 is too short for J_eff.
+ */
+rc_status rc_formal_solve_mali(rc_plan_t plan, const float* chi, const float* eta, int n_lambda,
+                               float* J, float* alo, float* J_eff, float* alo_c, void* stream);
+
+/* ---------------------------------------------------------------------------------------
+ * Non-LTE population update (Sec. 3.3): model atom, LTE start, opacity/emissivity from
+ * populations, statistical equilibrium with MALI rates, and the iteration driver.
+ * Populations and thermodynamic inputs are FP64 (populations span many decades); the
+ * formal solution in between is FP32.
+ * ------------------------------------------------------------------------------------- */
+
+/* Atom with non-overlapping Gaussian lines in complete redistribution.  Host pointers,
+ * copied by rc_atom_create. */
+typedef struct {
+    int n_levels;          /* 2..8 */
+    const double* E_eV;    /* level energies in eV (n_levels), ascending from the ground level */
+    const double* g;       /* statistical weights (n_levels) */
+    int n_lines;           /* 1..16 */
+    const int* lower;      /* lower level of each line */
+    const int* upper;      /* upper level of each line (> lower) */
+    const double* A_ul;    /* Einstein A of each line, s^-1 */
+    int n_per_line;        /* frequencies per line, 2..64 */
+    double x_max;          /* grid half-width in Doppler widths at T_ref (uniform in frequency) */
+    double T_ref;          /* K */
+    double mass_amu;       /* atomic mass */
+} rc_atom_desc;
+
+typedef struct rc_atom_s* rc_atom_t;
+
+/* Derives the line constants (nu0, B_ul = A c^2/(2 h nu0^3), B_lu = g_u/g_l B_ul, f_lu, the
+ * frequency grid and trapezoid weights) and uploads them to the current device.
+ * Errors: RC_ERR_ARG, RC_ERR_OOM, RC_ERR_CUDA. */
+rc_status rc_atom_create(const rc_atom_desc* desc, rc_atom_t* out);
+void rc_atom_destroy(rc_atom_t atom);
+/* Number of line wavelengths (n_lines * n_per_line); the wavelength index is
+ * line * n_per_line + k. */
+int rc_atom_n_lambda(rc_atom_t atom);
+
+/*
+ * rc_lte -- LTE start (Sec. 3.3): pure-hydrogen Saha ionisation at (T, n_H) gives n_e and
+ * the neutral density n_atom; the levels follow Boltzmann over the model's levels.
+ * Device FP64 arrays of ncell cells; pops is [n_levels][ncell].  Asynchronous.
+ * Errors: RC_ERR_ARG, RC_ERR_CUDA.
+ */
+rc_status rc_lte(rc_atom_t atom, const double* T, const double* nH, long long ncell, double* ne,
+                 double* n_atom, double* pops, void* stream);
+
+/*
+ * rc_emis_opac -- line opacity and emissivity at every grid frequency (the inputs of the RTE,
+ * Sec. 3.2): chi = (h nu0/4 pi)(n_l B_lu - n_u B_ul) phi, eta = (h nu0/4 pi) n_u A_ul phi,
+ * phi the Gaussian profile at the local Doppler width renormalised so that sum_k w_k phi_k = 1.
+ * T, pops device FP64; chi [m^-1] and eta [W m^-3 Hz^-1 sr^-1] device FP32
+ * [n_lambda][ncell].  Asynchronous.  Errors: RC_ERR_ARG, RC_ERR_CUDA.
+ */
+rc_status rc_emis_opac(rc_atom_t atom, const double* T, const double* pops, long long ncell,
+                       float* chi, float* eta, void* stream);
+
+/*
+ * rc_stat_eq -- statistical equilibrium Gamma n = 0 per cell (Sec. 3.3, Eq. 20) with the
+ * same-preconditioning MALI rates of a diagonal operator (Eq. 18-19):
+ *   R_lu = B_lu Jeff_bar,  R_ul = A_ul (1 - Lambda*)_bar + B_ul Jeff_bar,
+ * bars = sum_k w_k phi_k (.), plus van Regemorter collisions (C_ul from detailed balance).
+ * Only off-diagonal rates are accumulated; the diagonal is minus the column sum; the row of
+ * the most populated level is replaced by sum n = n_atom; the system is solved in FP64.
+ *   J_eff, alo_c   device FP32 [n_lambda][ncell] from rc_formal_solve_mali.  alo_c = NULL
+ *                  means Lambda* = 0 (plain Lambda iteration; pass J as J_eff).
+ *   pops           device FP64 [n_levels][ncell], in: previous iterate, out: new populations.
+ *   max_rel_change host FP64 out (may be NULL): max over cells and levels of
+ *                  |n_new - n_old| / n_new.  If non-NULL the call synchronises the stream.
+ * Errors: RC_ERR_ARG, RC_ERR_CUDA.
+ */
+rc_status rc_stat_eq(rc_atom_t atom, const double* T, const double* ne, const double* n_atom,
+                     const float* J_eff, const float* alo_c, long long ncell, double* pops,
+                     double* max_rel_change, void* stream);
+
+/*
+ * rc_nlte_solve -- the non-LTE iteration (Sec. 3.3): repeat {rc_emis_opac, rc_formal_solve_mali,
+ * rc_stat_eq} from the populations in `pops` until the maximum relative change drops below
+ * tol (Sec. 4.2 uses 1e-3) or max_iter iterations ran.  The plan's grid must have
+ * nx * nz = ncell cells and its voxel_size in metres.  history (host, max_iter entries, may be
+ * NULL) receives the change of every iteration.  Synchronises once per iteration (one 8-byte
+ * copy).  Returns RC_OK on convergence, RC_ERR_NOT_CONVERGED after max_iter iterations
+ * (pops then holds the last iterate).
+ */
+rc_status rc_nlte_solve(rc_plan_t plan, rc_atom_t atom, const double* T, const double* ne,
+                        const double* n_atom, double* pops, double tol, int max_iter,
+                        int* iterations, double* final_change, double* history, void* stream);
+
 /* One-line message for the calling thread's last error ("" if none). */
 const char* rc_last_error(void);
 

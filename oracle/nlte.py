@@ -196,34 +196,56 @@ def collision_rates(atom, T, ne):
 # statistical equilibrium (Sec. 3.3, Eq. 18-20)
 # ---------------------------------------------------------------------------
 
-def rate_matrix(atom, T, ne, J, alo, pops_old):
-    """Gamma [cell][i][j]: rate j -> i per atom in j (off-diagonal), diagonal from
-    conservation.  J, alo: [line*n_per_line][cell]; pops_old: [level][cell]."""
+def effective_inputs(atom, J, alo, pops_old):
+    """(J_eff, 1 - Lambda*) per wavelength: J_eff = J - Lambda* S_dagger (Eq. 19 with a
+    diagonal operator; Psi* eta_dagger = Lambda* S_dagger)."""
+    npl = atom["n_per_line"]
+    J = np.asarray(J, dtype=np.float64)
+    alo = np.zeros_like(J) if alo is None else np.asarray(alo, dtype=np.float64).reshape(J.shape)
+    S_old = line_source_function(atom, pops_old)
+    Jeff = np.empty_like(J)
+    for li, S in enumerate(S_old):
+        sl = slice(li * npl, (li + 1) * npl)
+        Jeff[sl] = J[sl] - S[None, :] * alo[sl]
+    return Jeff, 1.0 - alo
+
+
+def rate_matrix_eff(atom, T, ne, J_eff, alo_c):
+    """Gamma [cell][i][j] from the effective intensity: rate j -> i per atom in j
+    (off-diagonal), diagonal from conservation.  J_eff, alo_c: [line*n_per_line][cell];
+    alo_c = None means Lambda* = 0."""
     T = np.asarray(T, dtype=np.float64).ravel()
     ncell = T.size
     nlev = len(atom["E_eV"])
     npl = atom["n_per_line"]
-    J = np.asarray(J, dtype=np.float64).reshape(-1, ncell)
-    alo = np.zeros_like(J) if alo is None else np.asarray(alo, dtype=np.float64).reshape(-1, ncell)
+    J_eff = np.asarray(J_eff, dtype=np.float64).reshape(-1, ncell)
+    alo_c = np.ones_like(J_eff) if alo_c is None else \
+        np.asarray(alo_c, dtype=np.float64).reshape(-1, ncell)
     phis = profiles(atom, T)
     grids = frequency_grid(atom)
-    S_old = line_source_function(atom, pops_old)
     coll = collision_rates(atom, T, ne)
     G = np.zeros((ncell, nlev, nlev))
-    for li, (L, phi, (nu, w), S, (Clu, Cul)) in enumerate(zip(line_constants(atom), phis, grids,
-                                                              S_old, coll)):
+    for li, (L, phi, (nu, w), (Clu, Cul)) in enumerate(zip(line_constants(atom), phis, grids,
+                                                           coll)):
         sl = slice(li * npl, (li + 1) * npl)
         wphi = w[:, None] * phi
-        Jbar = np.sum(wphi * J[sl], axis=0)
-        Lbar = np.sum(wphi * alo[sl], axis=0)
-        Jeff = Jbar - S * Lbar
-        Rlu = L["Blu"] * Jeff
-        Rul = L["A"] * (1.0 - Lbar) + L["Bul"] * Jeff
+        Jb = np.sum(wphi * J_eff[sl], axis=0)          # sum_k w phi (J - Lambda* S_dagger)
+        Lc = np.sum(wphi * alo_c[sl], axis=0)          # sum_k w phi (1 - Lambda*)
+        Rlu = L["Blu"] * Jb
+        Rul = L["A"] * Lc + L["Bul"] * Jb
         G[:, L["up"], L["lo"]] += Rlu + Clu
         G[:, L["lo"], L["up"]] += Rul + Cul
     for i in range(nlev):
         G[:, i, i] = -np.sum(G[:, :, i], axis=1)
     return G
+
+
+def rate_matrix(atom, T, ne, J, alo, pops_old):
+    """Gamma from J and Lambda* (MALI, same preconditioning, diagonal operator)."""
+    ncell = np.asarray(T).size
+    J = np.asarray(J, dtype=np.float64).reshape(-1, ncell)
+    Jeff, aloc = effective_inputs(atom, J, alo, pops_old)
+    return rate_matrix_eff(atom, T, ne, Jeff, aloc)
 
 
 def solve_populations(G, n_atom, pops_old):
@@ -241,6 +263,15 @@ def solve_populations(G, n_atom, pops_old):
 def stat_eq(atom, T, ne, n_atom, J, alo, pops_old):
     """New populations and the maximum relative change max |n_new - n_old| / n_new."""
     G = rate_matrix(atom, T, ne, J, alo, pops_old)
+    new = solve_populations(G, n_atom, pops_old)
+    old = np.asarray(pops_old, dtype=np.float64).reshape(new.shape)
+    rel = np.abs(new - old) / np.abs(new)
+    return new, float(np.max(rel))
+
+
+def stat_eq_eff(atom, T, ne, n_atom, J_eff, alo_c, pops_old):
+    """stat_eq from (J_eff, 1 - Lambda*) directly."""
+    G = rate_matrix_eff(atom, T, ne, J_eff, alo_c)
     new = solve_populations(G, n_atom, pops_old)
     old = np.asarray(pops_old, dtype=np.float64).reshape(new.shape)
     rel = np.abs(new - old) / np.abs(new)

@@ -118,16 +118,19 @@ struct Voxel {
 // leaves the grid.  The advance is predicated (no divergent branch between rays
 // of a warp that step along different axes), and the voxel address is a running
 // 32-bit offset.
-template <int LB, int VL>
+// With SPLIT_FIRST the emission of the first piece (for a cascade-0 ray: the probe's
+// own cell from its centre to its edge) goes to I0 instead of I.
+template <int LB, int VL, bool SPLIT_FIRST = false>
 __device__ __forceinline__ void march_interval(const float2* __restrict__ F, int nx, int nz,
                                                float ox, float oz, float wx, float wz,
                                                float a, float b, int lane_off,
                                                unsigned off_hi, int max_steps,
-                                               float (&I)[VL], float (&T)[VL]) {
+                                               float (&I)[VL], float (&T)[VL], float (&I0)[VL]) {
 #pragma unroll
     for (int j = 0; j < VL; ++j) {
         I[j] = 0.0f;
         T[j] = 1.0f;
+        I0[j] = 0.0f;
     }
     const float invx = wx != 0.0f ? 1.0f / wx : 1e30f;
     const float invz = wz != 0.0f ? 1.0f / wz : 1e30f;
@@ -176,7 +179,10 @@ __device__ __forceinline__ void march_interval(const float2* __restrict__ F, int
             const float y = cur.v[j].x * ds;
             const float e = exp2_neg(y);
             const float om = one_minus_exp2_neg(y, e);
-            I[j] = fmaf(T[j] * cur.v[j].y, om, I[j]);
+            if (SPLIT_FIRST && step == 0)
+                I0[j] = cur.v[j].y * om;
+            else
+                I[j] = fmaf(T[j] * cur.v[j].y, om, I[j]);
             T[j] *= e;
         }
         if (tn >= thi) break;
@@ -268,9 +274,9 @@ level_kernel(const LevelArgs A) {
     const int lane_off = q * VL;
     const unsigned off_hi = (unsigned)((A.ncell - 1) * LB + lane_off);
 
-    float I[VL], T[VL];
+    float I[VL], T[VL], I0[VL];
     march_interval<LB, VL>(F, A.nx, A.nz, ox, oz, d.x, d.y, A.a, A.b, lane_off, off_hi,
-                           A.max_steps, I, T);
+                           A.max_steps, I, T, I0);
     float R[VL];
     if (HAS_UP) {
         const TS* Rup = reinterpret_cast<const TS*>(A.R_up) + (size_t)lb * A.R_up_lstride;
@@ -323,26 +329,32 @@ level0_kernel(const LevelArgs A) {
     own.load(F + (size_t)cell * LB + lane_off);
     const Bilinear bl(px, pz, HAS_UP ? A.Px_up : 1, HAS_UP ? A.Pz_up : 1);
 
-    float Jsum[VL], alo_sum[VL];
+    // J = mean of the merged rays; J_eff leaves out the emission of the cell's own
+    // centre-to-edge piece (Eq. 19 with a diagonal operator) and is summed without it, so
+    // no cancellation; alo = mean(1 - e^{-chi d_k}) (Eq. 17), alo_c = mean(e^{-chi d_k}).
+    float Jsum[VL], Jeff[VL], alo_sum[VL], aloc_sum[VL];
 #pragma unroll
-    for (int j = 0; j < VL; ++j) Jsum[j] = alo_sum[j] = 0.0f;
+    for (int j = 0; j < VL; ++j) Jsum[j] = Jeff[j] = alo_sum[j] = aloc_sum[j] = 0.0f;
     for (int k = 0; k < A.W; ++k) {
         const float2 d = A.dirs[k];
-        float I[VL], T[VL];
-        march_interval<LB, VL>(F, A.nx, A.nz, ox, oz, d.x, d.y, A.a, A.b, lane_off, off_hi,
-                               A.max_steps, I, T);
+        float I[VL], T[VL], I0[VL];
+        march_interval<LB, VL, true>(F, A.nx, A.nz, ox, oz, d.x, d.y, A.a, A.b, lane_off,
+                                     off_hi, A.max_steps, I, T, I0);
         const float dk = 0.5f / fmaxf(fabsf(d.x), fabsf(d.y));
 #pragma unroll
         for (int j = 0; j < VL; ++j) {
-            float R = I[j];
+            float Rnl = I[j];
             if (HAS_UP) {
                 const float up = upper_radiance<LB, TS>(Rup, bl.b00, bl.b01, bl.b10, bl.b11, bl.fx,
                                                         bl.fz, A.W, k, lane_off + j);
-                R = fmaf(T[j], up * sc, I[j]);
+                Rnl = fmaf(T[j], up * sc, I[j]);
             }
-            Jsum[j] += R;
+            Jsum[j] += Rnl + I0[j];
+            Jeff[j] += Rnl;
             const float y = own.v[j].x * dk;
-            alo_sum[j] += one_minus_exp2_neg(y, exp2_neg(y));
+            const float e = exp2_neg(y);
+            alo_sum[j] += one_minus_exp2_neg(y, e);
+            aloc_sum[j] += e;
         }
     }
     const float invW = 1.0f / (float)A.W;
@@ -350,8 +362,11 @@ level0_kernel(const LevelArgs A) {
     for (int j = 0; j < VL; ++j) {
         const int lam = lb * LB + lane_off + j;
         if (lam < A.n_lambda) {
-            A.J[(size_t)lam * A.ncell + cell] = Jsum[j] * invW;
-            if (A.alo) A.alo[(size_t)lam * A.ncell + cell] = alo_sum[j] * invW;
+            const size_t o = (size_t)lam * A.ncell + cell;
+            A.J[o] = Jsum[j] * invW;
+            if (A.alo) A.alo[o] = alo_sum[j] * invW;
+            if (A.J_eff) A.J_eff[o] = Jeff[j] * invW;
+            if (A.alo_c) A.alo_c[o] = aloc_sum[j] * invW;
         }
     }
 }

@@ -52,6 +52,8 @@ struct LevelArgs {
     // cascade 0 outputs
     float* J;
     float* alo;
+    float* J_eff;            // J without the cell's own segment emission (MALI), may be NULL
+    float* alo_c;            // 1 - alo, may be NULL
     int n_lambda;
     int max_steps;           // upper bound on cells crossed by one ray (nx + nz + 2)
 };

@@ -1,0 +1,462 @@
+// rcx_nlte.cu -- the non-LTE population update around the formal solution (Sec. 3.3):
+// model atom tables, LTE start, line opacity/emissivity from populations, statistical
+// equilibrium with MALI rates of a diagonal operator, and the iteration driver.
+//
+// Precision: populations, temperatures and densities are FP64; the profile sums, the
+// rates, the rate matrix and its solve are FP64 as well (one thread per cell, a few
+// hundred FP64 operations -- negligible next to the formal solution); chi/eta handed to
+// the FP32 formal solution and the J_eff / (1 - Lambda*) it returns are FP32.
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "rcx_internal.h"
+
+namespace {
+
+// CODATA 2018
+constexpr double kH = 6.62607015e-34;
+constexpr double kC = 2.99792458e8;
+constexpr double kK = 1.380649e-23;
+constexpr double kEV = 1.602176634e-19;
+constexpr double kMe = 9.1093837015e-31;
+constexpr double kAmu = 1.66053906660e-27;
+constexpr double kQe = 1.602176634e-19;
+constexpr double kEps0 = 8.8541878128e-12;
+constexpr double kRydbergE = 13.605693122994 * kEV;   // van Regemorter's E_H
+constexpr double kChiH = 13.598434599702 * kEV;       // hydrogen ionisation energy
+constexpr double kPi = 3.14159265358979323846;
+constexpr double kEulerGamma = 0.57721566490153286061;
+
+constexpr int kMaxLevels = 8;
+constexpr int kMaxLines = 16;
+constexpr int kMaxPerLine = 64;
+
+struct LineConst {
+    int lo, up, lam0;
+    double A, Blu, Bul;
+    double hnu_4pi;      // h nu0 / 4 pi
+    double dop;          // Doppler width / sqrt(T): nu0/c sqrt(2 k / m)
+    double coll;         // n_e-independent van Regemorter factor: beta Omega/(g_l P) = beta (8pi/sqrt3)(E_Ryd/dE) f_lu
+    double y_T;          // dE / k: y = y_T / T
+    double glo_gup;      // g_l / g_u
+};
+
+struct AtomDev {
+    int n_levels, n_lines, n_per_line;
+    double E_k[kMaxLevels];   // E / k  (K)
+    double g[kMaxLevels];
+    LineConst line[kMaxLines];
+    const double* dnu;        // [n_lines][n_per_line]: nu_k - nu0
+    const double* w;          // [n_lines][n_per_line]: trapezoid weights (Hz)
+};
+
+rc_status nfail(rc_status s, const std::string& m) {
+    rcx::set_last_error(m);
+    return s;
+}
+rc_status ncuda(cudaError_t e, const char* what) {
+    cudaGetLastError();
+    rcx::set_last_error(std::string(what) + ": " + cudaGetErrorString(e));
+    return RC_ERR_CUDA;
+}
+
+// ---------------------------------------------------------------------------
+// device helpers
+// ---------------------------------------------------------------------------
+
+// e^y E1(y) through the power series of E1 (Abramowitz & Stegun 5.1.11) for y < 1.
+__device__ double exp_e1_small(double y) {
+    double term = 1.0, sum = 0.0;
+    for (int k = 1; k <= 30; ++k) {
+        term *= -y / (double)k;            // (-y)^k / k!
+        sum += term / (double)k;
+    }
+    return exp(y) * (-kEulerGamma - log(y) - sum);
+}
+
+// van Regemorter's effective Gaunt factor P(y) = max(0.2, 0.276 e^y E1(y)); for y >= 1,
+// e^y E1(y) <= 0.597 so the floor 0.2 applies.
+__device__ double van_regemorter_p(double y) {
+    if (y >= 1.0) return 0.2;
+    return fmax(0.2, 0.276 * exp_e1_small(y));
+}
+
+// Gaussian profile value at offset dnu for Doppler width dD (not yet renormalised).
+__device__ __forceinline__ double gauss(double dnu, double dD) {
+    const double u = dnu / dD;
+    return exp(-u * u);
+}
+
+__global__ void lte_kernel(AtomDev A, const double* __restrict__ T, const double* __restrict__ nH,
+                           long long ncell, double saha_c, double chi_k, double* __restrict__ ne,
+                           double* __restrict__ n_atom, double* __restrict__ pops) {
+    const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= ncell) return;
+    const double t = T[c], n = nH[c];
+    // x^2 n / (1 - x) = phi with phi = (2 pi m_e k T / h^2)^1.5 exp(-chi_H / kT)
+    const double phi = saha_c * t * sqrt(t) * exp(-chi_k / t);
+    const double s = sqrt(phi * phi + 4.0 * n * phi);
+    const double x = 2.0 * phi / (phi + s);
+    const double na = n * (4.0 * n * phi / ((phi + s) * (phi + s)));  // n (1 - x)
+    ne[c] = x * n;
+    n_atom[c] = na;
+    double b[kMaxLevels], sum = 0.0;
+    for (int i = 0; i < A.n_levels; ++i) {
+        b[i] = A.g[i] * exp(-A.E_k[i] / t);
+        sum += b[i];
+    }
+    for (int i = 0; i < A.n_levels; ++i) pops[(size_t)i * ncell + c] = na * b[i] / sum;
+}
+
+__global__ void emis_opac_kernel(AtomDev A, const double* __restrict__ T,
+                                 const double* __restrict__ pops, long long ncell,
+                                 float* __restrict__ chi, float* __restrict__ eta) {
+    const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= ncell) return;
+    const double sqT = sqrt(T[c]);
+    for (int li = 0; li < A.n_lines; ++li) {
+        const LineConst& L = A.line[li];
+        const double dD = L.dop * sqT;
+        const double* dnu = A.dnu + (size_t)li * A.n_per_line;
+        const double* w = A.w + (size_t)li * A.n_per_line;
+        double norm = 0.0;
+        for (int k = 0; k < A.n_per_line; ++k) norm += w[k] * gauss(dnu[k], dD);
+        const double nl = pops[(size_t)L.lo * ncell + c], nu = pops[(size_t)L.up * ncell + c];
+        // phi_k = gauss / (sqrt(pi) dD) renormalised: the sqrt(pi) dD cancels
+        const double kchi = L.hnu_4pi * (nl * L.Blu - nu * L.Bul) / norm;
+        const double keta = L.hnu_4pi * nu * L.A / norm;
+        for (int k = 0; k < A.n_per_line; ++k) {
+            const double ph = gauss(dnu[k], dD);
+            const size_t o = (size_t)(L.lam0 + k) * ncell + c;
+            chi[o] = (float)(kchi * ph);
+            eta[o] = (float)(keta * ph);
+        }
+    }
+}
+
+// Gamma n = 0 per cell (Eq. 20) with MALI rates; FP64 throughout.
+__global__ void stat_eq_kernel(AtomDev A, const double* __restrict__ T,
+                               const double* __restrict__ ne, const double* __restrict__ n_atom,
+                               const float* __restrict__ Jeff, const float* __restrict__ aloc,
+                               long long ncell, double* __restrict__ pops,
+                               unsigned long long* __restrict__ dmax_bits) {
+    const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    double rel = 0.0;
+    if (c < ncell) {
+        const int n = A.n_levels;
+        const double t = T[c], sqT = sqrt(t), nec = ne[c];
+        double G[kMaxLevels][kMaxLevels];
+        for (int i = 0; i < n; ++i)
+            for (int j = 0; j < n; ++j) G[i][j] = 0.0;
+        for (int li = 0; li < A.n_lines; ++li) {
+            const LineConst& L = A.line[li];
+            const double dD = L.dop * sqT;
+            const double* dnu = A.dnu + (size_t)li * A.n_per_line;
+            const double* w = A.w + (size_t)li * A.n_per_line;
+            double norm = 0.0, sj = 0.0, sl = 0.0;
+            for (int k = 0; k < A.n_per_line; ++k) {
+                const double wp = w[k] * gauss(dnu[k], dD);
+                const size_t o = (size_t)(L.lam0 + k) * ncell + c;
+                norm += wp;
+                sj += wp * (double)Jeff[o];
+                if (aloc) sl += wp * (double)aloc[o];
+            }
+            const double Jb = sj / norm;                 // sum_k w phi J_eff
+            const double Lc = aloc ? sl / norm : 1.0;    // sum_k w phi (1 - Lambda*)
+            const double Rlu = L.Blu * Jb;
+            const double Rul = L.A * Lc + L.Bul * Jb;
+            const double y = L.y_T / t;
+            const double Clu = nec * L.coll * van_regemorter_p(y) / sqT * exp(-y);
+            const double Cul = Clu * L.glo_gup * exp(y);
+            G[L.up][L.lo] += Rlu + Clu;                  // lo -> up, per atom in lo
+            G[L.lo][L.up] += Rul + Cul;                  // up -> lo, per atom in up
+        }
+        double old[kMaxLevels];
+        int r = 0;
+        for (int i = 0; i < n; ++i) {
+            old[i] = pops[(size_t)i * ncell + c];
+            if (old[i] > old[r]) r = i;
+        }
+        for (int j = 0; j < n; ++j) {
+            double s = 0.0;
+            for (int i = 0; i < n; ++i)
+                if (i != j) s += G[i][j];
+            G[j][j] = -s;
+        }
+        double b[kMaxLevels];
+        for (int i = 0; i < n; ++i) b[i] = 0.0;
+        for (int j = 0; j < n; ++j) G[r][j] = 1.0;       // particle conservation
+        b[r] = n_atom[c];
+        // Gaussian elimination with partial pivoting
+        for (int col = 0; col < n; ++col) {
+            int p = col;
+            for (int i = col + 1; i < n; ++i)
+                if (fabs(G[i][col]) > fabs(G[p][col])) p = i;
+            if (p != col) {
+                for (int j = 0; j < n; ++j) {
+                    const double tmp = G[col][j];
+                    G[col][j] = G[p][j];
+                    G[p][j] = tmp;
+                }
+                const double tb = b[col];
+                b[col] = b[p];
+                b[p] = tb;
+            }
+            const double inv = 1.0 / G[col][col];
+            for (int i = col + 1; i < n; ++i) {
+                const double f = G[i][col] * inv;
+                if (f == 0.0) continue;
+                for (int j = col; j < n; ++j) G[i][j] -= f * G[col][j];
+                b[i] -= f * b[col];
+            }
+        }
+        double x[kMaxLevels];
+        for (int i = n - 1; i >= 0; --i) {
+            double s = b[i];
+            for (int j = i + 1; j < n; ++j) s -= G[i][j] * x[j];
+            x[i] = s / G[i][i];
+        }
+        for (int i = 0; i < n; ++i) {
+            pops[(size_t)i * ncell + c] = x[i];
+            const double d = fabs(x[i] - old[i]) / fabs(x[i]);
+            rel = (d == d) ? fmax(rel, d) : INFINITY;    // NaN -> infinite change
+        }
+    }
+    // block max -> one atomic per block (non-negative doubles order like their bits)
+    __shared__ double red[256];
+    red[threadIdx.x] = rel;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if ((int)threadIdx.x < s) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + s]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0 && dmax_bits)
+        atomicMax(dmax_bits, (unsigned long long)__double_as_longlong(red[0]));
+}
+
+}  // namespace
+
+struct rc_atom_s {
+    int device = 0;
+    AtomDev dev{};
+    int n_lambda = 0;
+    double* d_grid = nullptr;     // dnu then w
+    // driver workspace
+    float* d_ws = nullptr;
+    size_t ws_floats = 0;
+    unsigned long long* d_dmax = nullptr;
+    double* h_dmax = nullptr;     // pinned
+};
+
+namespace {
+
+rc_status launch_stat_eq(rc_atom_t a, const double* T, const double* ne, const double* n_atom,
+                         const float* J_eff, const float* alo_c, long long ncell, double* pops,
+                         cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(a->d_dmax, 0, sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return ncuda(e, "rc_stat_eq");
+    stat_eq_kernel<<<(unsigned)((ncell + 255) / 256), 256, 0, s>>>(a->dev, T, ne, n_atom, J_eff,
+                                                                   alo_c, ncell, pops, a->d_dmax);
+    if ((e = cudaGetLastError()) != cudaSuccess) return ncuda(e, "rc_stat_eq launch");
+    return RC_OK;
+}
+
+rc_status read_dmax(rc_atom_t a, cudaStream_t s, double* out) {
+    cudaError_t e = cudaMemcpyAsync(a->h_dmax, a->d_dmax, sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return ncuda(e, "rc_stat_eq: reading the maximum change");
+    *out = *a->h_dmax;
+    return RC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+rc_status rc_atom_create(const rc_atom_desc* d, rc_atom_t* out) {
+    rcx::set_last_error("");
+    if (!out) return nfail(RC_ERR_ARG, "rc_atom_create: out is NULL");
+    *out = nullptr;
+    if (!d || !d->E_eV || !d->g || !d->lower || !d->upper || !d->A_ul)
+        return nfail(RC_ERR_ARG, "rc_atom_create: NULL description or array");
+    if (d->n_levels < 2 || d->n_levels > kMaxLevels)
+        return nfail(RC_ERR_ARG, "rc_atom_create: n_levels must be in [2, 8]");
+    if (d->n_lines < 1 || d->n_lines > kMaxLines)
+        return nfail(RC_ERR_ARG, "rc_atom_create: n_lines must be in [1, 16]");
+    if (d->n_per_line < 2 || d->n_per_line > kMaxPerLine)
+        return nfail(RC_ERR_ARG, "rc_atom_create: n_per_line must be in [2, 64]");
+    if (!(d->x_max > 0) || !(d->T_ref > 0) || !(d->mass_amu > 0))
+        return nfail(RC_ERR_ARG, "rc_atom_create: x_max, T_ref and mass_amu must be positive");
+    for (int i = 0; i < d->n_levels; ++i)
+        if (!(d->g[i] > 0) || (i > 0 && !(d->E_eV[i] > d->E_eV[i - 1])))
+            return nfail(RC_ERR_ARG, "rc_atom_create: weights must be positive, energies ascending");
+    rc_atom_s* a = new (std::nothrow) rc_atom_s();
+    if (!a) return nfail(RC_ERR_OOM, "rc_atom_create: host allocation");
+    cudaGetDevice(&a->device);
+    AtomDev& A = a->dev;
+    A.n_levels = d->n_levels;
+    A.n_lines = d->n_lines;
+    A.n_per_line = d->n_per_line;
+    for (int i = 0; i < d->n_levels; ++i) {
+        A.E_k[i] = d->E_eV[i] * kEV / kK;
+        A.g[i] = d->g[i];
+    }
+    const double m = d->mass_amu * kAmu;
+    const double beta = kH * kH / (std::pow(2.0 * kPi * kMe, 1.5) * std::sqrt(kK));
+    std::vector<double> grid(2 * (size_t)d->n_lines * d->n_per_line);
+    double* hdnu = grid.data();
+    double* hw = grid.data() + (size_t)d->n_lines * d->n_per_line;
+    for (int li = 0; li < d->n_lines; ++li) {
+        const int lo = d->lower[li], up = d->upper[li];
+        if (lo < 0 || up >= d->n_levels || !(lo < up) || !(d->A_ul[li] > 0)) {
+            delete a;
+            return nfail(RC_ERR_ARG, "rc_atom_create: bad line levels or A_ul");
+        }
+        LineConst& L = A.line[li];
+        const double dE = (d->E_eV[up] - d->E_eV[lo]) * kEV;
+        const double nu0 = dE / kH;
+        L.lo = lo;
+        L.up = up;
+        L.lam0 = li * d->n_per_line;
+        L.A = d->A_ul[li];
+        L.Bul = L.A * kC * kC / (2.0 * kH * nu0 * nu0 * nu0);
+        L.Blu = d->g[up] / d->g[lo] * L.Bul;
+        L.hnu_4pi = kH * nu0 / (4.0 * kPi);
+        L.dop = nu0 / kC * std::sqrt(2.0 * kK / m);
+        const double f_lu = L.A * kEps0 * kMe * kC * kC * kC * d->g[up] /
+                            (2.0 * kPi * kQe * kQe * nu0 * nu0 * d->g[lo]);
+        // C_lu = n_e beta Omega_lu / (g_l sqrt T) e^-y,  Omega_lu = (8 pi/sqrt 3)(E_Ryd/dE) g_l f_lu P(y)
+        L.coll = beta * (8.0 * kPi / std::sqrt(3.0)) * (kRydbergE / dE) * f_lu;
+        L.y_T = dE / kK;
+        L.glo_gup = d->g[lo] / d->g[up];
+        const double dref = nu0 / kC * std::sqrt(2.0 * kK * d->T_ref / m);
+        const double step = 2.0 * d->x_max / (double)(d->n_per_line - 1) * dref;
+        for (int k = 0; k < d->n_per_line; ++k) {
+            hdnu[(size_t)li * d->n_per_line + k] = (-d->x_max + 2.0 * d->x_max * k / (d->n_per_line - 1)) * dref;
+            hw[(size_t)li * d->n_per_line + k] = (k == 0 || k == d->n_per_line - 1) ? 0.5 * step : step;
+        }
+    }
+    cudaError_t e = cudaMalloc(&a->d_grid, grid.size() * sizeof(double));
+    if (e == cudaSuccess)
+        e = cudaMemcpy(a->d_grid, grid.data(), grid.size() * sizeof(double), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMalloc(&a->d_dmax, sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMallocHost(&a->h_dmax, sizeof(double));
+    if (e != cudaSuccess) {
+        cudaFree(a->d_grid);
+        cudaFree(a->d_dmax);
+        delete a;
+        return ncuda(e, "rc_atom_create: device tables");
+    }
+    A.dnu = a->d_grid;
+    A.w = a->d_grid + (size_t)d->n_lines * d->n_per_line;
+    a->n_lambda = d->n_lines * d->n_per_line;
+    *out = a;
+    return RC_OK;
+}
+
+void rc_atom_destroy(rc_atom_t a) {
+    if (!a) return;
+    cudaDeviceSynchronize();
+    cudaFree(a->d_grid);
+    cudaFree(a->d_dmax);
+    cudaFree(a->d_ws);
+    cudaFreeHost(a->h_dmax);
+    delete a;
+}
+
+int rc_atom_n_lambda(rc_atom_t a) { return a ? a->n_lambda : 0; }
+
+rc_status rc_lte(rc_atom_t a, const double* T, const double* nH, long long ncell, double* ne,
+                 double* n_atom, double* pops, void* stream) {
+    rcx::set_last_error("");
+    if (!a || !T || !nH || !ne || !n_atom || !pops || ncell < 0)
+        return nfail(RC_ERR_ARG, "rc_lte: NULL argument or negative ncell");
+    if (ncell == 0) return RC_OK;
+    const double saha_c = std::pow(2.0 * kPi * kMe * kK / (kH * kH), 1.5);
+    lte_kernel<<<(unsigned)((ncell + 255) / 256), 256, 0, (cudaStream_t)stream>>>(
+        a->dev, T, nH, ncell, saha_c, kChiH / kK, ne, n_atom, pops);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? RC_OK : ncuda(e, "rc_lte launch");
+}
+
+rc_status rc_emis_opac(rc_atom_t a, const double* T, const double* pops, long long ncell,
+                       float* chi, float* eta, void* stream) {
+    rcx::set_last_error("");
+    if (!a || !T || !pops || !chi || !eta || ncell < 0)
+        return nfail(RC_ERR_ARG, "rc_emis_opac: NULL argument or negative ncell");
+    if (ncell == 0) return RC_OK;
+    emis_opac_kernel<<<(unsigned)((ncell + 127) / 128), 128, 0, (cudaStream_t)stream>>>(
+        a->dev, T, pops, ncell, chi, eta);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? RC_OK : ncuda(e, "rc_emis_opac launch");
+}
+
+rc_status rc_stat_eq(rc_atom_t a, const double* T, const double* ne, const double* n_atom,
+                     const float* J_eff, const float* alo_c, long long ncell, double* pops,
+                     double* max_rel_change, void* stream) {
+    rcx::set_last_error("");
+    if (!a || !T || !ne || !n_atom || !J_eff || !pops || ncell < 0)
+        return nfail(RC_ERR_ARG, "rc_stat_eq: NULL argument or negative ncell");
+    if (ncell == 0) {
+        if (max_rel_change) *max_rel_change = 0.0;
+        return RC_OK;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    rc_status st = launch_stat_eq(a, T, ne, n_atom, J_eff, alo_c, ncell, pops, s);
+    if (st != RC_OK || !max_rel_change) return st;
+    return read_dmax(a, s, max_rel_change);
+}
+
+rc_status rc_nlte_solve(rc_plan_t plan, rc_atom_t a, const double* T, const double* ne,
+                        const double* n_atom, double* pops, double tol, int max_iter,
+                        int* iterations, double* final_change, double* history, void* stream) {
+    rcx::set_last_error("");
+    if (!plan || !a || !T || !ne || !n_atom || !pops || max_iter < 1 || !(tol > 0))
+        return nfail(RC_ERR_ARG, "rc_nlte_solve: NULL argument, max_iter < 1 or tol <= 0");
+    const long long ncell = (long long)plan->nx * plan->nz;
+    const int nl = a->n_lambda;
+    const size_t need = (size_t)5 * nl * ncell;   // chi, eta, J, J_eff, alo_c
+    if (a->ws_floats < need) {
+        cudaDeviceSynchronize();
+        cudaFree(a->d_ws);
+        a->d_ws = nullptr;
+        a->ws_floats = 0;
+        if (cudaMalloc(&a->d_ws, need * sizeof(float)) != cudaSuccess) {
+            cudaGetLastError();
+            return nfail(RC_ERR_OOM, "rc_nlte_solve: workspace allocation");
+        }
+        a->ws_floats = need;
+    }
+    float* chi = a->d_ws;
+    float* eta = chi + (size_t)nl * ncell;
+    float* J = eta + (size_t)nl * ncell;
+    float* Jeff = J + (size_t)nl * ncell;
+    float* aloc = Jeff + (size_t)nl * ncell;
+    cudaStream_t s = (cudaStream_t)stream;
+    double change = INFINITY;
+    int it = 0;
+    for (; it < max_iter; ++it) {
+        rc_status st = rc_emis_opac(a, T, pops, ncell, chi, eta, stream);
+        if (st != RC_OK) return st;
+        st = rc_formal_solve_mali(plan, chi, eta, nl, J, nullptr, Jeff, aloc, stream);
+        if (st != RC_OK) return st;
+        st = launch_stat_eq(a, T, ne, n_atom, Jeff, aloc, ncell, pops, s);
+        if (st != RC_OK) return st;
+        st = read_dmax(a, s, &change);
+        if (st != RC_OK) return st;
+        if (history) history[it] = change;
+        if (change < tol) {
+            ++it;
+            break;
+        }
+    }
+    if (iterations) *iterations = it;
+    if (final_change) *final_change = change;
+    if (change < tol) return RC_OK;
+    return nfail(RC_ERR_NOT_CONVERGED, "rc_nlte_solve: max_iter reached before tol");
+}
+
+}  // extern "C"

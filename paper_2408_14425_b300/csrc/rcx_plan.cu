@@ -102,7 +102,8 @@ rc_status ensure_scratch(rc_plan_s* p, int n_lambda) {
 
 // The launch sequence of one solve on device buffers.
 rc_status solve_device(rc_plan_s* p, const float* chi, const float* eta, int n_lambda,
-                       float* J, float* alo, cudaStream_t s) {
+                       float* J, float* alo, cudaStream_t s, float* J_eff = nullptr,
+                       float* alo_c = nullptr) {
     if (n_lambda == 0) return RC_OK;
     if ((n_lambda + p->LB - 1) / p->LB > 65535)
         return fail(RC_ERR_ARG, "rc_formal_solve: too many wavelengths for one call (65535 blocks)");
@@ -174,6 +175,8 @@ rc_status solve_device(rc_plan_s* p, const float* chi, const float* eta, int n_l
         a.scale = f16 ? p->d_scale : nullptr;
         a.J = J;
         a.alo = alo;
+        a.J_eff = J_eff;
+        a.alo_c = alo_c;
         a.n_lambda = n_lambda;
         a.max_steps = p->nx + p->nz + 2;
         if ((e = rcx::launch_level(LB, p->VL, p->opt.precision, i == 0, has_up, n_lblk, a, s)) !=
@@ -411,6 +414,31 @@ rc_status rc_formal_solve(rc_plan_t p, const float* chi, const float* eta, int n
     cudaError_t sticky = cudaGetLastError();
     if (sticky != cudaSuccess) return cuda_fail(sticky, "rc_formal_solve: pending CUDA error");
     return solve_device(p, chi, eta, n_lambda, J, alo, (cudaStream_t)stream);
+}
+
+rc_status rc_formal_solve_mali(rc_plan_t p, const float* chi, const float* eta, int n_lambda,
+                               float* J, float* alo, float* J_eff, float* alo_c, void* stream) {
+    g_last_error.clear();
+    if (!p) return fail(RC_ERR_ARG, "rc_formal_solve_mali: plan is NULL");
+    if (n_lambda < 0) return fail(RC_ERR_ARG, "rc_formal_solve_mali: n_lambda < 0");
+    if (n_lambda > 0 && (!chi || !eta || !J))
+        return fail(RC_ERR_ARG, "rc_formal_solve_mali: chi, eta and J must be non-NULL");
+    if (J_eff || alo_c) {
+        // the first piece of every cascade-0 ray must be the whole centre-to-edge segment
+        double dmax = 0.0;
+        for (int k = 0; k < p->W0; ++k) {
+            const double th = 2.0 * M_PI * ((double)k + 0.5) / (double)p->W0;
+            dmax = std::max(dmax, 0.5 / std::max(std::fabs(std::cos(th)), std::fabs(std::sin(th))));
+        }
+        if (p->lv[0].b < dmax)
+            return fail(RC_ERR_ARG, "rc_formal_solve_mali: the cascade-0 interval is shorter than "
+                                    "the centre-to-edge path of a cell");
+    }
+    DeviceGuard dg(p->device);
+    if (!dg.ok) return fail(RC_ERR_CUDA, "rc_formal_solve_mali: cannot select the plan's device");
+    cudaError_t sticky = cudaGetLastError();
+    if (sticky != cudaSuccess) return cuda_fail(sticky, "rc_formal_solve_mali: pending CUDA error");
+    return solve_device(p, chi, eta, n_lambda, J, alo, (cudaStream_t)stream, J_eff, alo_c);
 }
 
 rc_status rc_formal_solve_host(rc_plan_t p, const float* chi_h, const float* eta_h, int n_lambda,

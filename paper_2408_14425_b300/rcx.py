@@ -26,6 +26,8 @@ EXPORTS = [
     "rc_plan_scratch_bytes", "rc_formal_solve", "rc_formal_solve_host", "rc_plan_cascade",
     "rc_plan_last_launch_count", "rc_last_error", "rc_status_string", "rc_plan_set_timing",
     "rc_plan_launch_times", "rc_plan_launch_name", "rc_formal_solve_noalloc",
+    "rc_formal_solve_mali", "rc_atom_create", "rc_atom_destroy", "rc_atom_n_lambda", "rc_lte",
+    "rc_emis_opac", "rc_stat_eq", "rc_nlte_solve",
 ]
 
 
@@ -44,6 +46,15 @@ class rc_options(ctypes.Structure):
                 ("interval_rule", ctypes.c_int), ("lambda_block", ctypes.c_int),
                 ("bilinear_fix", ctypes.c_int), ("lambda_per_lane", ctypes.c_int),
                 ("reserved", ctypes.c_int * 2)]
+
+
+class rc_atom_desc(ctypes.Structure):
+    _fields_ = [("n_levels", ctypes.c_int), ("E_eV", ctypes.POINTER(ctypes.c_double)),
+                ("g", ctypes.POINTER(ctypes.c_double)), ("n_lines", ctypes.c_int),
+                ("lower", ctypes.POINTER(ctypes.c_int)), ("upper", ctypes.POINTER(ctypes.c_int)),
+                ("A_ul", ctypes.POINTER(ctypes.c_double)), ("n_per_line", ctypes.c_int),
+                ("x_max", ctypes.c_double), ("T_ref", ctypes.c_double),
+                ("mass_amu", ctypes.c_double)]
 
 
 _lib = None
@@ -93,6 +104,25 @@ def load():
     L.rc_formal_solve_noalloc.argtypes = [ctypes.POINTER(rc_grid), ctypes.c_int, ctypes.c_int,
                                           ctypes.c_float, _vp, _vp, ctypes.c_int, _vp, _vp, _vp]
     L.rc_formal_solve_noalloc.restype = ctypes.c_int
+    L.rc_formal_solve_mali.argtypes = [_vp, _vp, _vp, ctypes.c_int, _vp, _vp, _vp, _vp, _vp]
+    L.rc_formal_solve_mali.restype = ctypes.c_int
+    L.rc_atom_create.argtypes = [ctypes.POINTER(rc_atom_desc), ctypes.POINTER(_vp)]
+    L.rc_atom_create.restype = ctypes.c_int
+    L.rc_atom_destroy.argtypes = [_vp]
+    L.rc_atom_destroy.restype = None
+    L.rc_atom_n_lambda.argtypes = [_vp]
+    L.rc_atom_n_lambda.restype = ctypes.c_int
+    L.rc_lte.argtypes = [_vp, _vp, _vp, ctypes.c_longlong, _vp, _vp, _vp, _vp]
+    L.rc_lte.restype = ctypes.c_int
+    L.rc_emis_opac.argtypes = [_vp, _vp, _vp, ctypes.c_longlong, _vp, _vp, _vp]
+    L.rc_emis_opac.restype = ctypes.c_int
+    L.rc_stat_eq.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp, ctypes.c_longlong, _vp,
+                             ctypes.POINTER(ctypes.c_double), _vp]
+    L.rc_stat_eq.restype = ctypes.c_int
+    L.rc_nlte_solve.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp, ctypes.c_double, ctypes.c_int,
+                                ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double),
+                                ctypes.POINTER(ctypes.c_double), _vp]
+    L.rc_nlte_solve.restype = ctypes.c_int
     _lib = L
     return L
 
@@ -223,6 +253,21 @@ class Plan:
         check(load().rc_formal_solve(self._h, pc, pe, nl, pj, pa, _stream_ptr(stream)))
         return (J, alo) if alo is not None else J
 
+    def formal_solve_mali(self, chi, eta, J=None, J_eff=None, alo_c=None, alo=None, stream=None):
+        """J, J_eff = J - Lambda* S_local (no cancellation) and 1 - Lambda* (rc_formal_solve_mali)."""
+        import torch
+        nl = chi.shape[0]
+        shape = (nl, self.nz, self.nx)
+
+        def out(t):
+            return torch.empty(shape, dtype=torch.float32, device=chi.device) if t is None else t
+        J, J_eff, alo_c = out(J), out(J_eff), out(alo_c)
+        check(load().rc_formal_solve_mali(
+            self._h, _dev_ptr(chi, "chi", shape), _dev_ptr(eta, "eta", shape), nl,
+            _dev_ptr(J, "J", shape), _dev_ptr(alo, "alo", shape) if alo is not None else None,
+            _dev_ptr(J_eff, "J_eff", shape), _dev_ptr(alo_c, "alo_c", shape), _stream_ptr(stream)))
+        return J, J_eff, alo_c
+
     def formal_solve_host(self, chi, eta, J=None, alo=None, want_alo: bool = False):
         """Same on host FP32 arrays (numpy or CPU tensors); copies are inside the call."""
         nl = chi.shape[0]
@@ -262,3 +307,92 @@ def formal_solve_noalloc(chi, eta, n_cascades: int, dirs0: int = 4, interval0: f
     check(load().rc_formal_solve_noalloc(ctypes.byref(g), n_cascades, dirs0, interval0, pc, pe, nl,
                                          pj, pa, _stream_ptr(stream)))
     return (J, alo) if alo is not None else J
+
+
+class Atom:
+    """rc_atom_create: a model atom with non-overlapping Gaussian lines (include/rcx.h)."""
+
+    def __init__(self, desc: dict):
+        L = load()
+        E = (ctypes.c_double * len(desc["E_eV"]))(*desc["E_eV"])
+        g = (ctypes.c_double * len(desc["g"]))(*desc["g"])
+        lines = desc["lines"]
+        lo = (ctypes.c_int * len(lines))(*[int(x[0]) for x in lines])
+        up = (ctypes.c_int * len(lines))(*[int(x[1]) for x in lines])
+        A = (ctypes.c_double * len(lines))(*[float(x[2]) for x in lines])
+        d = rc_atom_desc(len(desc["E_eV"]), E, g, len(lines), lo, up, A, int(desc["n_per_line"]),
+                         float(desc["x_max"]), float(desc["T_ref"]), float(desc["mass_amu"]))
+        h = _vp()
+        check(L.rc_atom_create(ctypes.byref(d), ctypes.byref(h)))
+        self._h = h
+        self.n_levels = len(desc["E_eV"])
+        self.n_lambda = L.rc_atom_n_lambda(h)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().rc_atom_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def lte(self, T, nH, stream=None):
+        """(n_e, n_atom, pops[n_levels][ncell]) from device FP64 T, n_H (flattened cells)."""
+        import torch
+        n = T.numel()
+        ne = torch.empty(n, dtype=torch.float64, device=T.device)
+        na = torch.empty_like(ne)
+        pops = torch.empty((self.n_levels, n), dtype=torch.float64, device=T.device)
+        check(load().rc_lte(self._h, _dev_ptr(T.reshape(-1), "T", (n,), "float64"),
+                            _dev_ptr(nH.reshape(-1), "nH", (n,), "float64"), n,
+                            _dev_ptr(ne, "ne", (n,), "float64"), _dev_ptr(na, "n_atom", (n,), "float64"),
+                            _dev_ptr(pops, "pops", (self.n_levels, n), "float64"), _stream_ptr(stream)))
+        return ne, na, pops
+
+    def emis_opac(self, T, pops, stream=None):
+        import torch
+        n = T.numel()
+        chi = torch.empty((self.n_lambda, n), dtype=torch.float32, device=T.device)
+        eta = torch.empty_like(chi)
+        check(load().rc_emis_opac(self._h, _dev_ptr(T.reshape(-1), "T", (n,), "float64"),
+                                  _dev_ptr(pops, "pops", (self.n_levels, n), "float64"), n,
+                                  _dev_ptr(chi, "chi", chi.shape), _dev_ptr(eta, "eta", eta.shape),
+                                  _stream_ptr(stream)))
+        return chi, eta
+
+    def stat_eq(self, T, ne, n_atom, J_eff, alo_c, pops, stream=None):
+        """Updates pops (device FP64 [n_levels][ncell]) in place; returns the max relative change."""
+        n = T.numel()
+        ch = ctypes.c_double()
+        shp = (self.n_lambda, n)
+        check(load().rc_stat_eq(
+            self._h, _dev_ptr(T.reshape(-1), "T", (n,), "float64"),
+            _dev_ptr(ne.reshape(-1), "ne", (n,), "float64"),
+            _dev_ptr(n_atom.reshape(-1), "n_atom", (n,), "float64"),
+            _dev_ptr(J_eff.reshape(shp), "J_eff", shp),
+            _dev_ptr(alo_c.reshape(shp), "alo_c", shp) if alo_c is not None else None, n,
+            _dev_ptr(pops, "pops", (self.n_levels, n), "float64"), ctypes.byref(ch),
+            _stream_ptr(stream)))
+        return ch.value
+
+
+def nlte_solve(plan: Plan, atom: Atom, T, ne, n_atom, pops, tol: float = 1e-3,
+               max_iter: int = 500, stream=None):
+    """rc_nlte_solve: iterate pops (device FP64, in place) to max relative change < tol.
+    Returns (converged, iterations, history)."""
+    n = T.numel()
+    it = ctypes.c_int()
+    fin = ctypes.c_double()
+    hist = (ctypes.c_double * max_iter)()
+    st = load().rc_nlte_solve(
+        plan.handle, atom._h, _dev_ptr(T.reshape(-1), "T", (n,), "float64"),
+        _dev_ptr(ne.reshape(-1), "ne", (n,), "float64"),
+        _dev_ptr(n_atom.reshape(-1), "n_atom", (n,), "float64"),
+        _dev_ptr(pops, "pops", (atom.n_levels, n), "float64"), tol, max_iter, ctypes.byref(it),
+        ctypes.byref(fin), hist, _stream_ptr(stream))
+    if st not in (RC_OK, -5):
+        check(st)
+    return st == RC_OK, it.value, [hist[i] for i in range(it.value)]

@@ -1,0 +1,142 @@
+"""Parity of the CUDA non-LTE pieces (through the C ABI) with the FP64 oracle.
+
+FP64 kernels (LTE start, statistical equilibrium) must match the oracle to 1e-10;
+FP32 outputs (chi, eta) to 1e-6; the MALI cascade-0 outputs (J_eff, 1 - Lambda*) to the
+formal-solution tolerance 1e-3; populations after whole iterations (FP32 formal solution
+inside) to the population tolerance 1e-4 relative.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import nlte
+from paper_2408_14425_b300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+ATOM = W.h3_atom()
+
+
+def _rcx():
+    from paper_2408_14425_b300 import build, rcx
+    build.build()
+    return rcx
+
+
+def _slab(n=48, seed=11):
+    return W.prominence_slab(n=n, seed=seed, half_width=n / 5, blend=3, wander=3)
+
+
+def _dev(a, dtype=torch.float64):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(dtype).cuda()
+
+
+def test_lte_start_matches_oracle():
+    rcx = _rcx()
+    atom = rcx.Atom(ATOM)
+    T, nH, _ = _slab(64)
+    ne, na, pops = atom.lte(_dev(T), _dev(nH))
+    ne_r, na_r = nlte.saha_hydrogen(T.ravel(), nH.ravel())
+    pops_r = nlte.lte_populations(ATOM, T, na_r)
+    np.testing.assert_allclose(ne.cpu().numpy(), ne_r, rtol=1e-12)
+    np.testing.assert_allclose(na.cpu().numpy(), na_r, rtol=1e-12)
+    np.testing.assert_allclose(pops.cpu().numpy(), pops_r, rtol=1e-12)
+
+
+def test_emis_opac_matches_oracle():
+    rcx = _rcx()
+    atom = rcx.Atom(ATOM)
+    T, nH, _ = _slab(64)
+    ne_r, na_r = nlte.saha_hydrogen(T.ravel(), nH.ravel())
+    rng = np.random.default_rng(2)
+    pops = nlte.lte_populations(ATOM, T, na_r) * rng.uniform(0.5, 2.0, (3, T.size))
+    chi, eta = atom.emis_opac(_dev(T), _dev(pops))
+    chi_r, eta_r = nlte.emis_opac(ATOM, T, pops)
+    np.testing.assert_allclose(chi.cpu().numpy(), chi_r.astype(np.float32), rtol=2e-6)
+    np.testing.assert_allclose(eta.cpu().numpy(), eta_r.astype(np.float32), rtol=2e-6)
+
+
+def test_stat_eq_matches_oracle_on_the_same_inputs():
+    """Same FP32 (J_eff, 1 - Lambda*) into both: the rates and the FP64 solve agree."""
+    rcx = _rcx()
+    atom = rcx.Atom(ATOM)
+    T, nH, vox = _slab(40)
+    ne_r, na_r = nlte.saha_hydrogen(T.ravel(), nH.ravel())
+    pops0 = nlte.lte_populations(ATOM, T, na_r)
+    chi_r, eta_r = nlte.emis_opac(ATOM, T, pops0)
+    J_r, alo_r, _ = oracle.rc_solve(chi_r.reshape(-1, *T.shape), eta_r.reshape(-1, *T.shape), 5,
+                                    voxel=vox, want_alo=True)
+    Jeff, aloc = nlte.effective_inputs(ATOM, J_r.reshape(chi_r.shape), alo_r.reshape(chi_r.shape),
+                                       pops0)
+    Jeff32 = Jeff.astype(np.float32)
+    aloc32 = aloc.astype(np.float32)
+    new_r, dmax_r = nlte.stat_eq_eff(ATOM, T, ne_r, na_r, Jeff32.astype(np.float64),
+                                     aloc32.astype(np.float64), pops0)
+    pops = _dev(pops0)
+    dmax = atom.stat_eq(_dev(T), _dev(ne_r), _dev(na_r), _dev(Jeff32, torch.float32),
+                        _dev(aloc32, torch.float32), pops)
+    np.testing.assert_allclose(pops.cpu().numpy(), new_r, rtol=1e-10)
+    assert dmax == pytest.approx(dmax_r, rel=1e-8)
+    # plain Lambda iteration (no operator): J as J_eff, alo_c = NULL
+    new_l, _ = nlte.stat_eq(ATOM, T, ne_r, na_r, J_r.reshape(chi_r.shape).astype(np.float32)
+                            .astype(np.float64), None, pops0)
+    pops = _dev(pops0)
+    atom.stat_eq(_dev(T), _dev(ne_r), _dev(na_r),
+                 _dev(J_r.reshape(chi_r.shape), torch.float32), None, pops)
+    np.testing.assert_allclose(pops.cpu().numpy(), new_l, rtol=1e-10)
+
+
+def test_mali_outputs_match_oracle():
+    """J_eff = J - Lambda* S_local and 1 - Lambda* from the cascade-0 kernel."""
+    rcx = _rcx()
+    T, nH, vox = _slab(48)
+    ne_r, na_r = nlte.saha_hydrogen(T.ravel(), nH.ravel())
+    pops0 = nlte.lte_populations(ATOM, T, na_r)
+    chi_r, eta_r = nlte.emis_opac(ATOM, T, pops0)
+    chi32 = chi_r.astype(np.float32).reshape(-1, *T.shape)
+    eta32 = eta_r.astype(np.float32).reshape(-1, *T.shape)
+    J_r, alo_r, _ = oracle.rc_solve(chi32.astype(np.float64), eta32.astype(np.float64), 5,
+                                    voxel=vox, want_alo=True)
+    S_loc = np.where(chi32 > 0, eta32.astype(np.float64) / chi32.astype(np.float64), 0.0)
+    Jeff_r = J_r - alo_r * S_loc
+    plan = rcx.Plan(T.shape[1], T.shape[0], 5, voxel_size=vox)
+    J, Jeff, aloc = plan.formal_solve_mali(_dev(chi32, torch.float32), _dev(eta32, torch.float32))
+    J, Jeff, aloc = J.cpu().numpy(), Jeff.cpu().numpy(), aloc.cpu().numpy()
+    for name, a, b in [("J", J, J_r), ("J_eff", Jeff, Jeff_r), ("1-alo", aloc, 1.0 - alo_r)]:
+        floor = 1e-7 * np.abs(b).max(axis=(1, 2), keepdims=True)
+        bad = np.abs(a - b) > 1e-3 * np.abs(b) + floor
+        assert not bad.any(), f"{name}: {bad.sum()} cells off, max rel " \
+                              f"{(np.abs(a - b) / np.maximum(np.abs(b), 1e-300)).max():.2e}"
+
+
+@pytest.mark.parametrize("n_iter", [1, 6])
+def test_whole_iterations_match_oracle(n_iter):
+    """n_iter iterations of the whole loop (emissivity, FP32 formal solution, FP64 update)
+    from LTE on a 32^2 slab: populations within 1e-4 of the FP64 oracle's iterates."""
+    rcx = _rcx()
+    T, nH, vox = _slab(32)
+    atom = rcx.Atom(ATOM)
+    ne, na, pops = atom.lte(_dev(T), _dev(nH))
+    plan = rcx.Plan(32, 32, 4, voxel_size=vox)
+    conv, it, hist = rcx.nlte_solve(plan, atom, _dev(T), ne, na, pops, tol=1e-30,
+                                    max_iter=n_iter)
+    assert not conv and it == n_iter
+    pops_r, hist_r = nlte.nlte_iterate(ATOM, T, nH, vox, 4, max_iter=n_iter, tol=1e-30)
+    g = pops.cpu().numpy()
+    rel = np.abs(g - pops_r) / np.abs(pops_r)
+    assert rel.max() < 1e-4, f"max rel population difference {rel.max():.3e}"
+    np.testing.assert_allclose(hist, hist_r, rtol=1e-2)
+
+
+def test_nlte_converges_on_a_slab():
+    rcx = _rcx()
+    T, nH, vox = _slab(64)
+    atom = rcx.Atom(ATOM)
+    ne, na, pops = atom.lte(_dev(T), _dev(nH))
+    plan = rcx.Plan(64, 64, 5, voxel_size=vox)
+    conv, it, hist = rcx.nlte_solve(plan, atom, _dev(T), ne, na, pops, tol=1e-3, max_iter=200)
+    assert conv and hist[-1] < 1e-3
+    p = pops.cpu().numpy()
+    np.testing.assert_allclose(p.sum(axis=0), na.cpu().numpy(), rtol=1e-12)
+    assert np.all(p > 0)

@@ -180,6 +180,50 @@ rc_status rc_formal_solve_noalloc(const rc_grid* grid, int n_cascades, int dirs0
                                   const float* chi, const float* eta, int n_lambda, float* J,
                                   float* alo, void* stream);
 
+/* Lane layout of a plan's march: wavelengths per ray (packed together per voxel) and per GPU
+ * lane; see rc_options.  Changing lambda_block re-allocates the plan's scratch (synchronous).
+ * Errors: RC_ERR_ARG, RC_ERR_OOM, RC_ERR_CUDA. */
+rc_status rc_plan_set_lane_layout(rc_plan_t plan, int lambda_block, int lambda_per_lane);
+rc_status rc_plan_get_lane_layout(rc_plan_t plan, int* lambda_block, int* lambda_per_lane);
+
+/*
+ * rc_plan_autotune -- times the formal solution of these inputs (device buffers as
+ * rc_formal_solve; J is overwritten) with each candidate lane layout (16/4, 8/4, 32/4, 8/2,
+ * 4/4, 4/2, 4/1, 2/2, 1/1 wavelengths per ray / per lane; blocks wider than twice n_lambda
+ * skipped), keeps the fastest on the plan and reports it.  Synchronous.
+ * Errors: RC_ERR_ARG, RC_ERR_OOM, RC_ERR_CUDA.
+ */
+rc_status rc_plan_autotune(rc_plan_t plan, const float* chi, const float* eta, int n_lambda,
+                           float* J, void* stream, int* lambda_block, int* lambda_per_lane);
+
+/*
+ * Batched formal solutions (independent problems solved together, Sec. 3.6: wavelengths and
+ * domains are independent).  A batch binds n plans (same n_cascades, storage precision and
+ * device; every plan is switched to the first plan's lane layout) to fixed device buffers
+ * chi[d], eta[d], J[d] ([n_lambda[d]][nz_d][nx_d]).  Each cascade is ONE persistent launch over
+ * a work list of CTA-sized chunks of every (domain, wavelength block), sorted by estimated
+ * cost (interval length a ray can march, longest first); packing is one launch for all
+ * domains.  The whole sequence is captured once into a CUDA graph; rc_batch_run replays it on
+ * `stream` (asynchronous).  With autotune != 0 creation times graph replays of the candidate
+ * lane layouts (16/4, 8/4, 32/4, 8/2, 4/4) on the bound inputs and keeps the fastest.
+ * Scratch is reserved at creation, so runs allocate nothing.  The buffers must outlive the
+ * batch; a batch must not run concurrently with another use of its plans.
+ * Errors: RC_ERR_ARG (mismatched plans, NULL buffers), RC_ERR_OOM, RC_ERR_CUDA.
+ */
+typedef struct rc_batch_s* rc_batch_t;
+rc_status rc_batch_create(int n, const rc_plan_t* plans, const float* const* chi,
+                          const float* const* eta, const int* n_lambda, float* const* J,
+                          int autotune, rc_batch_t* out);
+rc_status rc_batch_run(rc_batch_t batch, void* stream);
+rc_status rc_batch_info(rc_batch_t batch, int* launches_per_run, int* lambda_block,
+                        int* lambda_per_lane);
+void rc_batch_destroy(rc_batch_t batch);
+
+/* One-shot batched solve: rc_batch_create + rc_batch_run + synchronise + rc_batch_destroy. */
+rc_status rc_formal_solve_batched(int n, const rc_plan_t* plans, const float* const* chi,
+                                  const float* const* eta, const int* n_lambda, float* const* J,
+                                  void* stream);
+
 /*
  * rc_formal_solve_mali -- the formal solution with the two extra cascade-0 outputs the
  * MALI population update needs (Sec. 3.3, Eq. 17-19), computed without cancellation:

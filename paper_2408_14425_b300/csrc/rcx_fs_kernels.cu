@@ -246,17 +246,16 @@ struct Bilinear {
 // ---------------------------------------------------------------------------
 // cascades >= 1: march + merge, store the merged interval
 // ---------------------------------------------------------------------------
+// One CTA-sized chunk `cta` of the rays of lambda block `lb` of one cascade.
 template <int LB, int VL, typename TS, bool HAS_UP>
-__global__ void __launch_bounds__(kWarpsPerCta * 32)
-level_kernel(const LevelArgs A) {
+__device__ __forceinline__ void level_body(const LevelArgs& A, int lb, long long cta) {
     constexpr int LPR = LB / VL;   // lanes per ray
     constexpr int G = 32 / LPR;    // rays per warp
     const int lane = threadIdx.x & 31;
     const int g = lane / LPR, q = lane % LPR;
-    const long long wid = (long long)blockIdx.x * kWarpsPerCta + (threadIdx.x >> 5);
+    const long long wid = cta * kWarpsPerCta + (threadIdx.x >> 5);
     const long long ray = wid * G + g;
     if (ray >= A.rays) return;
-    const int lb = blockIdx.y;
 
     int k;
     long long probe;
@@ -299,21 +298,25 @@ level_kernel(const LevelArgs A) {
         Store<TS>::store(out + ((size_t)(ray >> 2) * LB + lane_off + j) * 4 + (ray & 3), R[j] * inv);
 }
 
+template <int LB, int VL, typename TS, bool HAS_UP>
+__global__ void __launch_bounds__(kWarpsPerCta * 32)
+level_kernel(const LevelArgs A) {
+    level_body<LB, VL, TS, HAS_UP>(A, blockIdx.y, blockIdx.x);
+}
+
 // ---------------------------------------------------------------------------
 // cascade 0: one lane group per cell centre, loop over the W_0 directions,
 // accumulate J (Eq. 1) and the diagonal operator (Eq. 17)
 // ---------------------------------------------------------------------------
 template <int LB, int VL, typename TS, bool HAS_UP>
-__global__ void __launch_bounds__(kWarpsPerCta * 32)
-level0_kernel(const LevelArgs A) {
+__device__ __forceinline__ void level0_body(const LevelArgs& A, int lb, long long cta) {
     constexpr int LPR = LB / VL;
     constexpr int G = 32 / LPR;
     const int lane = threadIdx.x & 31;
     const int g = lane / LPR, q = lane % LPR;
-    const long long wid = (long long)blockIdx.x * kWarpsPerCta + (threadIdx.x >> 5);
+    const long long wid = cta * kWarpsPerCta + (threadIdx.x >> 5);
     const long long cell = wid * G + g;
     if (cell >= A.ncell) return;
-    const int lb = blockIdx.y;
     const int px = (int)(cell % A.nx), pz = (int)(cell / A.nx);
     const float ox = (float)px + 0.5f, oz = (float)pz + 0.5f;
     const float2* F = A.field + (size_t)lb * A.ncell * LB;
@@ -371,6 +374,34 @@ level0_kernel(const LevelArgs A) {
     }
 }
 
+template <int LB, int VL, typename TS, bool HAS_UP>
+__global__ void __launch_bounds__(kWarpsPerCta * 32)
+level0_kernel(const LevelArgs A) {
+    level0_body<LB, VL, TS, HAS_UP>(A, blockIdx.y, blockIdx.x);
+}
+
+// ---------------------------------------------------------------------------
+// batched: one persistent launch per cascade over the CTA-sized chunks of every
+// (domain, lambda block) segment of a batch, segments sorted by estimated cost
+// (most expensive first) so the tail of the launch is made of cheap chunks.
+// Chunk t belongs to the last segment whose prefix is <= t.
+// ---------------------------------------------------------------------------
+template <bool LEVEL0, int LB, int VL, typename TS, bool HAS_UP>
+__global__ void __launch_bounds__(kWarpsPerCta * 32)
+batched_level_kernel(const BatchLevelArgs B) {
+    for (long long t = blockIdx.x; t < B.total; t += gridDim.x) {
+        int lo = 0, hi = B.n_seg - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (B.prefix[mid] <= t) lo = mid;
+            else hi = mid - 1;
+        }
+        const LevelArgs& A = B.args[B.seg_domain[lo]];
+        if (LEVEL0) level0_body<LB, VL, TS, HAS_UP>(A, B.seg_lblk[lo], t - B.prefix[lo]);
+        else level_body<LB, VL, TS, HAS_UP>(A, B.seg_lblk[lo], t - B.prefix[lo]);
+    }
+}
+
 // ---------------------------------------------------------------------------
 // packing [lambda][cell] (chi, eta) -> [lambda block][cell][LB] (chi' = chi voxel log2 e, S)
 // ---------------------------------------------------------------------------
@@ -411,6 +442,56 @@ __global__ void __launch_bounds__(256) pack_kernel(const PackArgs P) {
             smax = fmaxf(smax, __shfl_xor_sync(0xffffffffu, smax, off));
         if ((threadIdx.x & 31) == 0 && smax > 0.0f)
             atomicMax(P.smax_bits + lb, __float_as_uint(smax));  // S >= 0: bit order = value order
+    }
+}
+
+// Batched packing: chunk t (256 cells of one (domain, lambda block) segment).
+template <int LB>
+__global__ void __launch_bounds__(256) batched_pack_kernel(const BatchPackArgs B) {
+    for (long long t = blockIdx.x; t < B.total; t += gridDim.x) {
+        int lo = 0, hi = B.n_seg - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (B.prefix[mid] <= t) lo = mid;
+            else hi = mid - 1;
+        }
+        const PackArgs& P = B.args[B.seg_domain[lo]];
+        const int lb = B.seg_lblk[lo];
+        const long long cell = (t - B.prefix[lo]) * 256 + threadIdx.x;
+        float smax = 0.0f;
+        if (cell < P.ncell) {
+#pragma unroll
+            for (int l = 0; l < LB; l += 2) {
+                float4 q;
+                float* qq = reinterpret_cast<float*>(&q);
+#pragma unroll
+                for (int h = 0; h < 2 && l + h < LB; ++h) {
+                    const int lam = lb * LB + l + h;
+                    float c = 0.0f, sv = 0.0f;
+                    if (lam < P.n_lambda) {
+                        const float chi = __ldg(P.chi + (size_t)lam * P.ncell + cell);
+                        const float eta = __ldg(P.eta + (size_t)lam * P.ncell + cell);
+                        const float cv = fmaxf(chi * P.voxel, kChiFloor);
+                        sv = (eta * P.voxel) / cv;
+                        c = cv * kLog2e;
+                        smax = fmaxf(smax, sv);
+                    }
+                    qq[2 * h] = c;
+                    qq[2 * h + 1] = sv;
+                }
+                float2* o = P.out + ((size_t)lb * P.ncell + cell) * LB;
+                if (LB >= 2) reinterpret_cast<float4*>(o)[l / 2] = q;
+                else o[0] = make_float2(qq[0], qq[1]);
+            }
+        }
+        if (P.smax_bits) {
+            // the 256 cells of a chunk share one segment: warp max, one atomic per warp
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1)
+                smax = fmaxf(smax, __shfl_xor_sync(0xffffffffu, smax, off));
+            if ((threadIdx.x & 31) == 0 && smax > 0.0f)
+                atomicMax(P.smax_bits + lb, __float_as_uint(smax));
+        }
     }
 }
 
@@ -492,6 +573,67 @@ static cudaError_t level_v(int VL, int precision, bool level0, bool has_up, int 
     }
     if (VL == 1) return level_p<LB, 1>(precision, level0, has_up, n_lblk, a, s);
     return cudaErrorInvalidValue;
+}
+
+template <bool L0, int LB, int VL, typename TS>
+static cudaError_t batched_t(bool has_up, const BatchLevelArgs& b, int grid, cudaStream_t s) {
+    if (has_up) batched_level_kernel<L0, LB, VL, TS, true><<<grid, kWarpsPerCta * 32, 0, s>>>(b);
+    else batched_level_kernel<L0, LB, VL, TS, false><<<grid, kWarpsPerCta * 32, 0, s>>>(b);
+    return cudaGetLastError();
+}
+
+template <int LB, int VL, typename TS>
+static int batched_occ(bool level0, bool has_up) {
+    int n = 0;
+    const void* f = level0 ? (has_up ? (const void*)batched_level_kernel<true, LB, VL, TS, true>
+                                     : (const void*)batched_level_kernel<true, LB, VL, TS, false>)
+                           : (has_up ? (const void*)batched_level_kernel<false, LB, VL, TS, true>
+                                     : (const void*)batched_level_kernel<false, LB, VL, TS, false>);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, f, kWarpsPerCta * 32, 0);
+    return n;
+}
+
+template <int LB, int VL>
+static cudaError_t batched_p(int precision, bool level0, bool has_up, const BatchLevelArgs& b,
+                             int grid, cudaStream_t s, int* occ) {
+    switch (precision) {
+        case RC_STORE_F32:
+            if (occ) { *occ = batched_occ<LB, VL, float>(level0, has_up); return cudaSuccess; }
+            return level0 ? batched_t<true, LB, VL, float>(has_up, b, grid, s)
+                          : batched_t<false, LB, VL, float>(has_up, b, grid, s);
+        case RC_STORE_F16:
+            if (occ) { *occ = batched_occ<LB, VL, __half>(level0, has_up); return cudaSuccess; }
+            return level0 ? batched_t<true, LB, VL, __half>(has_up, b, grid, s)
+                          : batched_t<false, LB, VL, __half>(has_up, b, grid, s);
+        case RC_STORE_BF16:
+            if (occ) { *occ = batched_occ<LB, VL, __nv_bfloat16>(level0, has_up); return cudaSuccess; }
+            return level0 ? batched_t<true, LB, VL, __nv_bfloat16>(has_up, b, grid, s)
+                          : batched_t<false, LB, VL, __nv_bfloat16>(has_up, b, grid, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+// The batched path instantiates the lane layouts the autotuner picks from.
+cudaError_t launch_batched_level(int LB, int VL, int precision, bool level0, bool has_up,
+                                 const BatchLevelArgs& b, int grid, cudaStream_t s, int* occ) {
+    if (LB == 16 && VL == 4) return batched_p<16, 4>(precision, level0, has_up, b, grid, s, occ);
+    if (LB == 8 && VL == 4) return batched_p<8, 4>(precision, level0, has_up, b, grid, s, occ);
+    if (LB == 8 && VL == 2) return batched_p<8, 2>(precision, level0, has_up, b, grid, s, occ);
+    if (LB == 32 && VL == 4) return batched_p<32, 4>(precision, level0, has_up, b, grid, s, occ);
+    if (LB == 4 && VL == 4) return batched_p<4, 4>(precision, level0, has_up, b, grid, s, occ);
+    if (LB == 4 && VL == 2) return batched_p<4, 2>(precision, level0, has_up, b, grid, s, occ);
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_batched_pack(int LB, const BatchPackArgs& b, int grid, cudaStream_t s) {
+    switch (LB) {
+        case 4: batched_pack_kernel<4><<<grid, 256, 0, s>>>(b); break;
+        case 8: batched_pack_kernel<8><<<grid, 256, 0, s>>>(b); break;
+        case 16: batched_pack_kernel<16><<<grid, 256, 0, s>>>(b); break;
+        case 32: batched_pack_kernel<32><<<grid, 256, 0, s>>>(b); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
 }
 
 cudaError_t launch_level(int LB, int VL, int precision, bool level0, bool has_up, int n_lblk,

@@ -68,7 +68,30 @@ struct PackArgs {
     unsigned int* smax_bits;  // per lambda block, may be NULL
 };
 
+// A batch launch: CTA-sized chunks of all (domain, lambda block) segments of one cascade.
+struct BatchLevelArgs {
+    const LevelArgs* args;        // per domain (device)
+    const long long* prefix;      // first chunk of each segment (device), ascending
+    const int* seg_domain;        // domain of each segment (device)
+    const int* seg_lblk;          // lambda block of each segment (device)
+    int n_seg;
+    long long total;              // chunks in all segments
+};
+
+struct BatchPackArgs {
+    const PackArgs* args;
+    const long long* prefix;
+    const int* seg_domain;
+    const int* seg_lblk;
+    int n_seg;
+    long long total;
+};
+
 // Launchers (rcx_fs_kernels.cu).  Return the CUDA launch error.
+// With occ != NULL the batched launcher only reports the kernel's resident CTAs per SM.
+cudaError_t launch_batched_level(int LB, int VL, int precision, bool level0, bool has_up,
+                                 const BatchLevelArgs& b, int grid, cudaStream_t s, int* occ);
+cudaError_t launch_batched_pack(int LB, const BatchPackArgs& b, int grid, cudaStream_t s);
 cudaError_t launch_pack(int LB, int n_lblk, const PackArgs& a, cudaStream_t s);
 cudaError_t launch_level(int LB, int VL, int precision, bool level0, bool has_up, int n_lblk,
                          const LevelArgs& a, cudaStream_t s);
@@ -78,6 +101,15 @@ cudaError_t launch_scales(int n_lblk, const unsigned int* smax_bits, float* scal
 // Sets the calling thread's rc_last_error() message (rcx_plan.cu).
 void set_last_error(const std::string& msg);
 
+}  // namespace rcx
+
+struct rc_plan_s;
+namespace rcx {
+// Launch arguments of cascade i of a plan whose scratch holds n_lambda (rcx_plan.cu).
+LevelArgs level_args(const rc_plan_s* p, int i, int n_lambda, float* J, float* alo,
+                     float* J_eff, float* alo_c);
+rc_status plan_reserve(rc_plan_s* p, int n_lambda);
+rc_status plan_set_layout(rc_plan_s* p, int LB, int VL);
 }  // namespace rcx
 
 struct rc_plan_s {

@@ -145,40 +145,8 @@ rc_status solve_device(rc_plan_s* p, const float* chi, const float* eta, int n_l
 
     const int C = p->C;
     for (int i = C - 1; i >= 0; --i) {
-        const rcx::LevelGeom& g = p->lv[i];
-        rcx::LevelArgs a{};
-        a.field = p->d_packed;
-        a.ncell = ncell;
-        a.nx = p->nx;
-        a.nz = p->nz;
-        a.Px = g.Px;
-        a.Pz = g.Pz;
-        a.W = (int)g.W;
-        a.Wshift = is_pow2(g.W) ? ilog2(g.W) : -1;
-        a.spacing = (float)(1 << i);
-        a.a = (float)g.a;
-        a.b = std::isinf(g.b) ? INFINITY : (float)g.b;
-        a.dirs = p->d_dirs + p->dir_off[i];
-        a.rays = g.rays();
+        const rcx::LevelArgs a = rcx::level_args(p, i, n_lambda, J, alo, J_eff, alo_c);
         const bool has_up = i < C - 1;
-        if (has_up) {
-            const rcx::LevelGeom& u = p->lv[i + 1];
-            a.R_up = p->d_R[(i + 1) & 1];
-            a.Px_up = u.Px;
-            a.Pz_up = u.Pz;
-            a.R_up_lstride = u.rays() * LB;
-        }
-        if (i > 0) {
-            a.R_out = p->d_R[i & 1];
-            a.R_out_lstride = g.rays() * LB;
-        }
-        a.scale = f16 ? p->d_scale : nullptr;
-        a.J = J;
-        a.alo = alo;
-        a.J_eff = J_eff;
-        a.alo_c = alo_c;
-        a.n_lambda = n_lambda;
-        a.max_steps = p->nx + p->nz + 2;
         if ((e = rcx::launch_level(LB, p->VL, p->opt.precision, i == 0, has_up, n_lblk, a, s)) !=
             cudaSuccess)
             return cuda_fail(e, "cascade launch");
@@ -191,6 +159,61 @@ rc_status solve_device(rc_plan_s* p, const float* chi, const float* eta, int n_l
 }
 
 }  // namespace
+
+rcx::LevelArgs rcx::level_args(const rc_plan_s* p, int i, int n_lambda, float* J, float* alo,
+                               float* J_eff, float* alo_c) {
+    const rcx::LevelGeom& g = p->lv[i];
+    const int LB = p->LB;
+    rcx::LevelArgs a{};
+    a.field = p->d_packed;
+    a.ncell = (long long)p->nx * p->nz;
+    a.nx = p->nx;
+    a.nz = p->nz;
+    a.Px = g.Px;
+    a.Pz = g.Pz;
+    a.W = (int)g.W;
+    a.Wshift = is_pow2(g.W) ? ilog2(g.W) : -1;
+    a.spacing = (float)(1 << i);
+    a.a = (float)g.a;
+    a.b = std::isinf(g.b) ? INFINITY : (float)g.b;
+    a.dirs = p->d_dirs + p->dir_off[i];
+    a.rays = g.rays();
+    if (i < p->C - 1) {
+        const rcx::LevelGeom& u = p->lv[i + 1];
+        a.R_up = p->d_R[(i + 1) & 1];
+        a.Px_up = u.Px;
+        a.Pz_up = u.Pz;
+        a.R_up_lstride = u.rays() * LB;
+    }
+    if (i > 0) {
+        a.R_out = p->d_R[i & 1];
+        a.R_out_lstride = g.rays() * LB;
+    }
+    a.scale = p->opt.precision != RC_STORE_F32 ? p->d_scale : nullptr;
+    a.J = J;
+    a.alo = alo;
+    a.J_eff = J_eff;
+    a.alo_c = alo_c;
+    a.n_lambda = n_lambda;
+    a.max_steps = p->nx + p->nz + 2;
+    return a;
+}
+
+rc_status rcx::plan_reserve(rc_plan_s* p, int n_lambda) { return ensure_scratch(p, n_lambda); }
+
+rc_status rcx::plan_set_layout(rc_plan_s* p, int LB, int VL) {
+    if (LB == p->LB && VL == p->VL) return RC_OK;
+    if (LB != p->LB) {
+        const int cap = p->cap_lambda;
+        cudaDeviceSynchronize();
+        free_scratch(p);
+        p->LB = LB;
+        p->VL = VL;
+        return cap > 0 ? ensure_scratch(p, cap) : RC_OK;
+    }
+    p->VL = VL;
+    return RC_OK;
+}
 
 void rcx::set_last_error(const std::string& msg) { g_last_error = msg; }
 
@@ -363,6 +386,79 @@ rc_status rc_plan_cascade(rc_plan_t p, int i, int* px, int* pz, long long* dirs,
 }
 
 int rc_plan_last_launch_count(rc_plan_t p) { return p ? p->last_launches : 0; }
+
+rc_status rc_plan_set_lane_layout(rc_plan_t p, int lambda_block, int lambda_per_lane) {
+    g_last_error.clear();
+    if (!p) return fail(RC_ERR_ARG, "rc_plan_set_lane_layout: plan is NULL");
+    const int LB = lambda_block, VL = lambda_per_lane;
+    if ((LB != 1 && LB != 2 && LB != 4 && LB != 8 && LB != 16 && LB != 32) ||
+        (VL != 1 && VL != 2 && VL != 4 && VL != 8) || VL > LB)
+        return fail(RC_ERR_ARG, "rc_plan_set_lane_layout: unsupported layout");
+    if ((long long)p->nx * p->nz * LB >= (1LL << 31))
+        return fail(RC_ERR_ARG, "rc_plan_set_lane_layout: nx * nz * lambda_block too large");
+    DeviceGuard dg(p->device);
+    return rcx::plan_set_layout(p, LB, VL);
+}
+
+rc_status rc_plan_get_lane_layout(rc_plan_t p, int* lambda_block, int* lambda_per_lane) {
+    if (!p) return fail(RC_ERR_ARG, "rc_plan_get_lane_layout: plan is NULL");
+    if (lambda_block) *lambda_block = p->LB;
+    if (lambda_per_lane) *lambda_per_lane = p->VL;
+    return RC_OK;
+}
+
+rc_status rc_plan_autotune(rc_plan_t p, const float* chi, const float* eta, int n_lambda,
+                           float* J, void* stream, int* lambda_block, int* lambda_per_lane) {
+    g_last_error.clear();
+    if (!p || !chi || !eta || !J || n_lambda < 1)
+        return fail(RC_ERR_ARG, "rc_plan_autotune: NULL argument or n_lambda < 1");
+    DeviceGuard dg(p->device);
+    static const int cand[][2] = {{16, 4}, {8, 4}, {32, 4}, {8, 2}, {4, 4}, {4, 2}, {4, 1},
+                                  {2, 2}, {1, 1}};
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    const bool timing_was = p->timing;
+    p->timing = false;
+    float best = INFINITY;
+    int bLB = p->LB, bVL = p->VL;
+    for (const auto& c : cand) {
+        // blocks much wider than the wavelength count only pad with empty lanes
+        if (c[0] > 4 && c[0] > 2 * n_lambda) continue;
+        if ((long long)p->nx * p->nz * c[0] >= (1LL << 31)) continue;
+        rc_status st = rcx::plan_set_layout(p, c[0], c[1]);
+        if (st == RC_OK) st = ensure_scratch(p, n_lambda);
+        if (st == RC_OK) st = solve_device(p, chi, eta, n_lambda, J, nullptr, s);  // warm-up
+        if (st != RC_OK) {
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            p->timing = timing_was;
+            return st;
+        }
+        cudaEventRecord(e0, s);
+        for (int r = 0; r < 2; ++r) solve_device(p, chi, eta, n_lambda, J, nullptr, s);
+        cudaEventRecord(e1, s);
+        cudaEventSynchronize(e1);
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best) {
+            best = ms;
+            bLB = c[0];
+            bVL = c[1];
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    p->timing = timing_was;
+    rc_status st = rcx::plan_set_layout(p, bLB, bVL);
+    if (st == RC_OK) st = ensure_scratch(p, n_lambda);
+    if (lambda_block) *lambda_block = bLB;
+    if (lambda_per_lane) *lambda_per_lane = bVL;
+    cudaError_t err = cudaGetLastError();
+    if (st == RC_OK && err != cudaSuccess) return cuda_fail(err, "rc_plan_autotune");
+    return st;
+}
 
 rc_status rc_plan_set_timing(rc_plan_t p, int enable) {
     g_last_error.clear();

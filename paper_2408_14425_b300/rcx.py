@@ -27,7 +27,9 @@ EXPORTS = [
     "rc_plan_last_launch_count", "rc_last_error", "rc_status_string", "rc_plan_set_timing",
     "rc_plan_launch_times", "rc_plan_launch_name", "rc_formal_solve_noalloc",
     "rc_formal_solve_mali", "rc_atom_create", "rc_atom_destroy", "rc_atom_n_lambda", "rc_lte",
-    "rc_emis_opac", "rc_stat_eq", "rc_nlte_solve",
+    "rc_emis_opac", "rc_stat_eq", "rc_nlte_solve", "rc_plan_set_lane_layout",
+    "rc_plan_get_lane_layout", "rc_plan_autotune", "rc_batch_create", "rc_batch_run",
+    "rc_batch_info", "rc_batch_destroy", "rc_formal_solve_batched",
 ]
 
 
@@ -123,6 +125,25 @@ def load():
                                 ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double),
                                 ctypes.POINTER(ctypes.c_double), _vp]
     L.rc_nlte_solve.restype = ctypes.c_int
+    _ip = ctypes.POINTER(ctypes.c_int)
+    L.rc_plan_set_lane_layout.argtypes = [_vp, ctypes.c_int, ctypes.c_int]
+    L.rc_plan_set_lane_layout.restype = ctypes.c_int
+    L.rc_plan_get_lane_layout.argtypes = [_vp, _ip, _ip]
+    L.rc_plan_get_lane_layout.restype = ctypes.c_int
+    L.rc_plan_autotune.argtypes = [_vp, _vp, _vp, ctypes.c_int, _vp, _vp, _ip, _ip]
+    L.rc_plan_autotune.restype = ctypes.c_int
+    _pp = ctypes.POINTER(_vp)
+    L.rc_batch_create.argtypes = [ctypes.c_int, _pp, _pp, _pp, _ip, _pp, ctypes.c_int,
+                                  ctypes.POINTER(_vp)]
+    L.rc_batch_create.restype = ctypes.c_int
+    L.rc_batch_run.argtypes = [_vp, _vp]
+    L.rc_batch_run.restype = ctypes.c_int
+    L.rc_batch_info.argtypes = [_vp, _ip, _ip, _ip]
+    L.rc_batch_info.restype = ctypes.c_int
+    L.rc_batch_destroy.argtypes = [_vp]
+    L.rc_batch_destroy.restype = None
+    L.rc_formal_solve_batched.argtypes = [ctypes.c_int, _pp, _pp, _pp, _ip, _pp, _vp]
+    L.rc_formal_solve_batched.restype = ctypes.c_int
     _lib = L
     return L
 
@@ -225,6 +246,24 @@ class Plan:
         check(load().rc_plan_launch_times(self._h, buf, 64, ctypes.byref(n)))
         return [(load().rc_plan_launch_name(self._h, j).decode(), float(buf[j]))
                 for j in range(n.value)]
+
+    def set_lane_layout(self, lambda_block: int, lambda_per_lane: int):
+        check(load().rc_plan_set_lane_layout(self._h, lambda_block, lambda_per_lane))
+
+    def lane_layout(self):
+        a, b = ctypes.c_int(), ctypes.c_int()
+        check(load().rc_plan_get_lane_layout(self._h, ctypes.byref(a), ctypes.byref(b)))
+        return a.value, b.value
+
+    def autotune(self, chi, eta, J, stream=None):
+        """rc_plan_autotune: keep the fastest lane layout for these inputs; returns it."""
+        nl = chi.shape[0]
+        shape = (nl, self.nz, self.nx)
+        a, b = ctypes.c_int(), ctypes.c_int()
+        check(load().rc_plan_autotune(self._h, _dev_ptr(chi, "chi", shape), _dev_ptr(eta, "eta", shape),
+                                      nl, _dev_ptr(J, "J", shape), _stream_ptr(stream),
+                                      ctypes.byref(a), ctypes.byref(b)))
+        return a.value, b.value
 
     def cascade(self, i: int):
         px, pz = ctypes.c_int(), ctypes.c_int()
@@ -396,3 +435,43 @@ def nlte_solve(plan: Plan, atom: Atom, T, ne, n_atom, pops, tol: float = 1e-3,
     if st not in (RC_OK, -5):
         check(st)
     return st == RC_OK, it.value, [hist[i] for i in range(it.value)]
+
+
+class Batch:
+    """rc_batch_create: fixed batch of domains, one persistent launch per cascade, CUDA graph."""
+
+    def __init__(self, plans, chis, etas, Js, autotune: bool = False):
+        L = load()
+        n = len(plans)
+        arr = lambda xs: (_vp * n)(*[_vp(x) for x in xs])  # noqa: E731
+        self._keep = (plans, chis, etas, Js)
+        for p, c, e, j in zip(plans, chis, etas, Js):
+            shape = (c.shape[0], p.nz, p.nx)
+            _dev_ptr(c, "chi", shape)
+            _dev_ptr(e, "eta", shape)
+            _dev_ptr(j, "J", shape)
+        nl = (ctypes.c_int * n)(*[int(c.shape[0]) for c in chis])
+        h = _vp()
+        check(L.rc_batch_create(n, arr([p.handle.value for p in plans]),
+                                arr([c.data_ptr() for c in chis]), arr([e.data_ptr() for e in etas]),
+                                nl, arr([j.data_ptr() for j in Js]), int(autotune), ctypes.byref(h)))
+        self._h = h
+
+    def run(self, stream=None):
+        check(load().rc_batch_run(self._h, _stream_ptr(stream)))
+
+    def info(self):
+        a, b, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        check(load().rc_batch_info(self._h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+        return dict(launches=a.value, lambda_block=b.value, lambda_per_lane=c.value)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().rc_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -357,12 +357,97 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def run_nlte(args):
+    """Second half of the metric: non-LTE time-to-1e-3, LTE-started vs surrogate-seeded.
+
+    * the 512^2 prominence slab (seed 11, 6 cascades): LTE-started iterations and wall time;
+    * the surrogate: training pairs from 200 seeded 256^2 slabs (seeds 100..299, 5 cascades,
+      same sheet recipe), Adam training on the GPU, then the held-out 1024^2 slab (seed 9999,
+      6 cascades) solved from LTE and from the network's seed; the seeded wall time includes
+      the features' formal solution and the forward pass; training time reported apart."""
+    import numpy as np
+    import torch
+
+    from paper_2408_14425_b300 import build as rbuild
+    from paper_2408_14425_b300 import rcx, surrogate, workloads
+    torch.cuda.set_device(_env_int("LOCAL_RANK", 0))
+    if _env_int("RANK", 0) != 0:
+        return
+    rbuild.build()
+    atom = rcx.Atom(workloads.h3_atom())
+    out = {"metric": "NLTE time-to-1e-3 (max relative population change), LTE-started vs "
+                     "surrogate-seeded", "unit": "s", "higher_is_better": False, "data": "synthetic",
+           "atom": "3-level H-like, 3 lines x 21 Gaussian-profile wavelengths, van Regemorter"}
+
+    def slab(n, seed, C):
+        T, nH, vox = workloads.prominence_slab(n=n, seed=seed)
+        return (torch.from_numpy(T).cuda(), torch.from_numpy(nH).cuda(),
+                rcx.Plan(n, n, C, voxel_size=vox))
+
+    T, nH, plan = slab(512, 11, 6)
+    surrogate.solve(plan, atom, T, nH, max_iter=2)          # warm-up (allocations)
+    r = surrogate.solve(plan, atom, T, nH, max_iter=args.nlte_max_iter)
+    out["slab_512"] = {"iterations": r["iterations"], "seconds": round(r["seconds"], 3),
+                       "converged": r["converged"], "cascades": 6,
+                       "ms_per_iteration": round(1e3 * r["seconds"] / max(r["iterations"], 1), 2)}
+    del T, nH, plan, r
+
+    t0 = time.perf_counter()
+    Xs, Ys, its = [], [], []
+    for seed in range(100, 100 + args.train_atmospheres):
+        T, nH, plan = slab(256, seed, 5)
+        X, Y, it = surrogate.training_pairs(plan, atom, T, nH, max_iter=args.nlte_max_iter)
+        Xs.append(X)
+        Ys.append(Y)
+        its.append(it)
+    torch.cuda.synchronize()
+    t_data = time.perf_counter() - t0
+    X = torch.cat(Xs)
+    Y = torch.cat(Ys)
+    del Xs, Ys
+    net = rcx.MLP(seed=1)
+    t0 = time.perf_counter()
+    net.fit_normalization(X)
+    hist = net.train(X, Y, batch=4096, steps=args.train_steps, lr=2e-3)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    train_loss, _ = net.loss_grad(X, Y)
+    del X, Y
+
+    T, nH, plan = slab(1024, 9999, 6)
+    surrogate.solve(plan, atom, T, nH, max_iter=2)          # warm-up
+    plain = surrogate.solve(plan, atom, T, nH, max_iter=args.nlte_max_iter)
+    seeded = surrogate.solve(plan, atom, T, nH, net=net, max_iter=args.nlte_max_iter)
+    diff = float(((seeded["pops"] - plain["pops"]).abs() / plain["pops"].abs()).max())
+    out["heldout_1024"] = {
+        "cascades": 6,
+        "plain": {"iterations": plain["iterations"], "seconds": round(plain["seconds"], 3),
+                  "converged": plain["converged"]},
+        "seeded": {"iterations": seeded["iterations"], "seconds": round(seeded["seconds"], 3),
+                   "converged": seeded["converged"], "lte_fallback_cells": seeded["fallback"]},
+        "speedup_wall": round(plain["seconds"] / seeded["seconds"], 3),
+        "max_rel_population_difference": diff}
+    out["training"] = {"atmospheres": args.train_atmospheres, "side": 256, "cascades": 5,
+                       "data_seconds": round(t_data, 2), "mean_iterations": float(np.mean(its)),
+                       "train_seconds": round(t_train, 2), "steps": args.train_steps,
+                       "batch": 4096, "final_minibatch_loss": hist[-1] if hist else None,
+                       "full_set_loss": train_loss}
+    out["value"] = round(seeded["seconds"], 3)
+    out["plain_value"] = round(plain["seconds"], 3)
+    print(json.dumps(out), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=["formal", "nlte"], default="formal",
+                    help="formal: the RC formal solution (headline); nlte: time-to-1e-3")
+    ap.add_argument("--train-atmospheres", type=int, default=200)
+    ap.add_argument("--train-steps", type=int, default=4000)
+    ap.add_argument("--nlte-max-iter", type=int, default=3000)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--n-side", type=int, default=N_SIDE, help="grid side (profiling cases only)")
@@ -376,6 +461,8 @@ def main():
         print("note: fewer than 3 warm-up steps", file=sys.stderr)
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "nlte":
+        run_nlte(args)
     else:
         run_ours(args)
 

@@ -325,6 +325,52 @@ rc_status rc_nlte_solve(rc_plan_t plan, rc_atom_t atom, const double* T, const d
                         const double* n_atom, double* pops, double tol, int max_iter,
                         int* iterations, double* final_change, double* history, void* stream);
 
+/* ---------------------------------------------------------------------------------------
+ * Surrogate seed of the non-LTE iteration.  The paper has no learned component; this is a
+ * start for the iteration of Sec. 3.3 in place of LTE, and LTE stays the fallback.
+ * Network: x (6 features) -> tanh(W1 xn + b1) (64) -> tanh(W2 h1 + b2) (64) -> W3 h2 + b3 (3),
+ * xn the standardised input; parameters flattened as W1[64][6], b1, W2[64][64], b2, W3[3][64],
+ * b3 (4803 floats).  FP32 master weights and Adam moments; the passes multiply with the
+ * bfloat16-rounded weights and accumulate in FP32.
+ * Features of a cell: log10 T, log10 n_e, log10 n_H and log10 J at the centre wavelength of
+ * each of the first three lines from the first (LTE) formal solution.  Targets: log10 of the
+ * departure coefficients n_i / n_i(LTE) of the three levels.
+ * ------------------------------------------------------------------------------------- */
+typedef struct rc_mlp_s* rc_mlp_t;
+/* Glorot-uniform weights from `seed`, zero biases, identity standardisation. */
+rc_status rc_mlp_create(unsigned long long seed, rc_mlp_t* out);
+void rc_mlp_destroy(rc_mlp_t net);
+int rc_mlp_n_params(rc_mlp_t net);
+/* Host copies of the parameters and the standardisation (mean, std of each feature); any
+ * pointer may be NULL.  Setting parameters resets the Adam state.  Synchronous. */
+rc_status rc_mlp_set_params(rc_mlp_t net, const float* theta, const float* mean, const float* std_);
+rc_status rc_mlp_get_params(rc_mlp_t net, float* theta, float* mean, float* std_);
+/* Standardisation from the mean and standard deviation of device features X [N][6]. */
+rc_status rc_mlp_fit_normalization(rc_mlp_t net, const float* X, long long N, void* stream);
+/* Y [B][3] = network(X [B][6]); device buffers, asynchronous. */
+rc_status rc_mlp_forward(rc_mlp_t net, const float* X, long long B, float* Y, void* stream);
+/* Mean-squared-error loss over B samples and its gradient (device outputs, either may be NULL). */
+rc_status rc_mlp_loss_grad(rc_mlp_t net, const float* X, const float* Y_target, long long B,
+                           float* grad, float* loss, void* stream);
+/* `steps` Adam steps (beta 0.9/0.999, eps 1e-8) on minibatches of `batch` rows drawn from
+ * device X [N][6], Y_target [N][3] by a counter-based generator (splitmix64 of the network's
+ * seed and step).  loss_history (host, `steps` entries, may be NULL: then no synchronisation)
+ * receives each minibatch loss. */
+rc_status rc_mlp_train(rc_mlp_t net, const float* X, const float* Y_target, long long N, int batch,
+                       int steps, float lr, float* loss_history, void* stream);
+/* Features X [ncell][6] from device T, n_e, n_H (FP64) and J [n_lambda][ncell] (FP32). */
+rc_status rc_surrogate_features(rc_atom_t atom, const double* T, const double* ne, const double* nH,
+                                const float* J, long long ncell, float* X, void* stream);
+/* Targets Y [ncell][3] = log10(n_i / n_i(LTE)) from device populations (3-level atoms). */
+rc_status rc_surrogate_targets(rc_atom_t atom, const double* T, const double* n_atom,
+                               const double* pops, long long ncell, float* Y, void* stream);
+/* Seeded populations: n_i = 10^y_i n_i(LTE) renormalised to n_atom, y = network(X); cells whose
+ * output is not finite and positive fall back to LTE (their count -> *n_fallback, host, may be
+ * NULL: then asynchronous).  Allocates a forward scratch on the network on first use. */
+rc_status rc_surrogate_seed(rc_atom_t atom, rc_mlp_t net, const float* X, const double* T,
+                            const double* n_atom, long long ncell, double* pops, int* n_fallback,
+                            void* stream);
+
 /* One-line message for the calling thread's last error ("" if none). */
 const char* rc_last_error(void);
 

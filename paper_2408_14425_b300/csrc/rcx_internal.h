@@ -110,6 +110,9 @@ LevelArgs level_args(const rc_plan_s* p, int i, int n_lambda, float* J, float* a
                      float* J_eff, float* alo_c);
 rc_status plan_reserve(rc_plan_s* p, int n_lambda);
 rc_status plan_set_layout(rc_plan_s* p, int LB, int VL);
+// Device tables of an atom's levels: E/k [K] and g (rcx_nlte.cu).
+rc_status atom_levels(rc_atom_t a, const double** Ek, const double** g, int* nlev,
+                      int* n_per_line, int* n_lines);
 }  // namespace rcx
 
 struct rc_plan_s {

@@ -1,0 +1,664 @@
+// rcx_mlp.cu -- the surrogate network that seeds the non-LTE iteration: a 6-64-64-3
+// tanh MLP with input standardisation, trained and run by these kernels.  The paper has
+// no learned component; the iteration it seeds is Sec. 3.3's.
+//
+// Precision: master weights and Adam moments in FP32; the forward and backward passes
+// multiply with the bfloat16-rounded weights and accumulate in FP32.
+// Work layout: one CTA of 256 threads per tile of 128 samples holds the weights and the
+// tile's activations in shared memory (about 150 KB) and runs the forward pass, the loss
+// and (for training) the whole backward pass; weight gradients are summed over the tile
+// and added to the global gradient with one atomic per weight per tile.
+#include <cuda_bf16.h>
+
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <random>
+#include <string>
+#include <vector>
+
+#include "rcx_internal.h"
+
+namespace {
+
+constexpr int NI = 6, NH = 64, NO = 3;
+constexpr int OFF_W1 = 0, OFF_B1 = OFF_W1 + NH * NI, OFF_W2 = OFF_B1 + NH;
+constexpr int OFF_B2 = OFF_W2 + NH * NH, OFF_W3 = OFF_B2 + NH, OFF_B3 = OFF_W3 + NO * NH;
+constexpr int NPARAM = OFF_B3 + NO;
+constexpr int TILE = 128;
+constexpr int THREADS = 256;
+constexpr int LD = NH + 1;   // padded row of an activation tile
+
+struct Smem {
+    float w[NPARAM];          // bf16-rounded weights, [out][in]
+    float w2t[NH * NH];       // W2 transposed: [in][out]
+    float mean[NI], istd[NI];
+    float xn[TILE * NI];
+    float h1[TILE * LD];
+    float h2[TILE * LD];      // becomes dh1 in the backward pass
+    float d[TILE * LD];       // dh2
+    float dy[TILE * NO];
+    float red[THREADS / 32];
+};
+
+rc_status mfail(rc_status s, const std::string& m) {
+    rcx::set_last_error(m);
+    return s;
+}
+rc_status mcuda(cudaError_t e, const char* what) {
+    cudaGetLastError();
+    rcx::set_last_error(std::string(what) + ": " + cudaGetErrorString(e));
+    return RC_ERR_CUDA;
+}
+
+// ---------------------------------------------------------------------------
+// fused forward (+ loss, + backward) over one tile of samples
+// ---------------------------------------------------------------------------
+template <bool TRAIN>
+__global__ void __launch_bounds__(THREADS)
+mlp_tile_kernel(const float* __restrict__ wbf, const float* __restrict__ norm,
+                const float* __restrict__ X, const float* __restrict__ Yt, long long B,
+                float* __restrict__ Y, float* __restrict__ grad, float* __restrict__ loss) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Smem& S = *reinterpret_cast<Smem*>(smem_raw);
+    const int tid = threadIdx.x;
+    const long long s0 = (long long)blockIdx.x * TILE;
+    const int nvalid = (int)min((long long)TILE, B - s0);
+
+    for (int i = tid; i < NPARAM; i += THREADS) S.w[i] = wbf[i];
+    for (int i = tid; i < NH * NH; i += THREADS) {
+        const int o = i / NH, k = i % NH;
+        S.w2t[k * NH + o] = wbf[OFF_W2 + i];
+    }
+    if (tid < NI) {
+        S.mean[tid] = norm[tid];
+        S.istd[tid] = 1.0f / norm[NI + tid];
+    }
+    __syncthreads();
+    for (int i = tid; i < TILE * NI; i += THREADS) {
+        const int s = i / NI, f = i % NI;
+        S.xn[i] = s < nvalid ? (X[(s0 + s) * NI + f] - S.mean[f]) * S.istd[f] : 0.0f;
+    }
+    __syncthreads();
+    // h1 = tanh(W1 xn + b1)
+    for (int i = tid; i < TILE * NH; i += THREADS) {
+        const int s = i / NH, o = i % NH;
+        float a = S.w[OFF_B1 + o];
+#pragma unroll
+        for (int f = 0; f < NI; ++f) a = fmaf(S.w[OFF_W1 + o * NI + f], S.xn[s * NI + f], a);
+        S.h1[s * LD + o] = tanhf(a);
+    }
+    __syncthreads();
+    // h2 = tanh(W2 h1 + b2): each thread a 4-sample x 8-output block
+    {
+        const int sg = tid / 8, og = tid % 8;
+        const int sb = sg * 4, ob = og * 8;
+        float acc[4][8];
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+            for (int c = 0; c < 8; ++c) acc[r][c] = S.w[OFF_B2 + ob + c];
+        for (int k = 0; k < NH; ++k) {
+            float a[4], w[8];
+#pragma unroll
+            for (int r = 0; r < 4; ++r) a[r] = S.h1[(sb + r) * LD + k];
+#pragma unroll
+            for (int c = 0; c < 8; ++c) w[c] = S.w2t[k * NH + ob + c];
+#pragma unroll
+            for (int r = 0; r < 4; ++r)
+#pragma unroll
+                for (int c = 0; c < 8; ++c) acc[r][c] = fmaf(a[r], w[c], acc[r][c]);
+        }
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+            for (int c = 0; c < 8; ++c) S.h2[(sb + r) * LD + ob + c] = tanhf(acc[r][c]);
+    }
+    __syncthreads();
+    // y = W3 h2 + b3, loss, dy
+    float lsum = 0.0f;
+    for (int i = tid; i < TILE * NO; i += THREADS) {
+        const int s = i / NO, o = i % NO;
+        float a = S.w[OFF_B3 + o];
+        for (int k = 0; k < NH; ++k) a = fmaf(S.w[OFF_W3 + o * NH + k], S.h2[s * LD + k], a);
+        if (s < nvalid) {
+            if (Y) Y[(s0 + s) * NO + o] = a;
+            if (TRAIN) {
+                const float r = a - Yt[(s0 + s) * NO + o];
+                lsum += r * r;
+                S.dy[i] = 2.0f * r / (float)(B * NO);
+            }
+        } else if (TRAIN) {
+            S.dy[i] = 0.0f;
+        }
+    }
+    if (!TRAIN) return;
+    // loss: block sum, one atomic
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) lsum += __shfl_xor_sync(0xffffffffu, lsum, o);
+    if ((tid & 31) == 0) S.red[tid >> 5] = lsum;
+    __syncthreads();
+    if (tid == 0) {
+        float t = 0.0f;
+        for (int w = 0; w < THREADS / 32; ++w) t += S.red[w];
+        atomicAdd(loss, t / (float)(B * NO));
+    }
+    // dW3, db3
+    if (tid < NO * NH) {
+        const int o = tid / NH, k = tid % NH;
+        float g = 0.0f;
+        for (int s = 0; s < TILE; ++s) g = fmaf(S.dy[s * NO + o], S.h2[s * LD + k], g);
+        atomicAdd(grad + OFF_W3 + tid, g);
+    } else if (tid < NO * NH + NO) {
+        const int o = tid - NO * NH;
+        float g = 0.0f;
+        for (int s = 0; s < TILE; ++s) g += S.dy[s * NO + o];
+        atomicAdd(grad + OFF_B3 + o, g);
+    }
+    // dh2 = (W3^T dy) * (1 - h2^2)
+    for (int i = tid; i < TILE * NH; i += THREADS) {
+        const int s = i / NH, k = i % NH;
+        float a = 0.0f;
+#pragma unroll
+        for (int o = 0; o < NO; ++o) a = fmaf(S.dy[s * NO + o], S.w[OFF_W3 + o * NH + k], a);
+        const float h = S.h2[s * LD + k];
+        S.d[s * LD + k] = a * (1.0f - h * h);
+    }
+    __syncthreads();
+    // dW2[o][k] = sum_s dh2[s][o] h1[s][k]: each thread a 4 x 4 block; db2
+    {
+        const int ob = (tid / 16) * 4, kb = (tid % 16) * 4;
+        float g[4][4] = {};
+        for (int s = 0; s < TILE; ++s) {
+            float dv[4], hv[4];
+#pragma unroll
+            for (int r = 0; r < 4; ++r) dv[r] = S.d[s * LD + ob + r];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) hv[c] = S.h1[s * LD + kb + c];
+#pragma unroll
+            for (int r = 0; r < 4; ++r)
+#pragma unroll
+                for (int c = 0; c < 4; ++c) g[r][c] = fmaf(dv[r], hv[c], g[r][c]);
+        }
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) atomicAdd(grad + OFF_W2 + (ob + r) * NH + kb + c, g[r][c]);
+        if (tid < NH) {
+            float gb = 0.0f;
+            for (int s = 0; s < TILE; ++s) gb += S.d[s * LD + tid];
+            atomicAdd(grad + OFF_B2 + tid, gb);
+        }
+    }
+    __syncthreads();
+    // dh1 = (W2^T dh2) * (1 - h1^2), written over h2
+    {
+        const int sg = tid / 8, ig = tid % 8;
+        const int sb = sg * 4, ib = ig * 8;
+        float acc[4][8] = {};
+        for (int o = 0; o < NH; ++o) {
+            float a[4], w[8];
+#pragma unroll
+            for (int r = 0; r < 4; ++r) a[r] = S.d[(sb + r) * LD + o];
+#pragma unroll
+            for (int c = 0; c < 8; ++c) w[c] = S.w[OFF_W2 + o * NH + ib + c];
+#pragma unroll
+            for (int r = 0; r < 4; ++r)
+#pragma unroll
+                for (int c = 0; c < 8; ++c) acc[r][c] = fmaf(a[r], w[c], acc[r][c]);
+        }
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+                const float h = S.h1[(sb + r) * LD + ib + c];
+                S.h2[(sb + r) * LD + ib + c] = acc[r][c] * (1.0f - h * h);
+            }
+    }
+    __syncthreads();
+    // dW1[o][f] = sum_s dh1[s][o] xn[s][f]; db1
+    for (int i = tid; i < NH * NI + NH; i += THREADS) {
+        if (i < NH * NI) {
+            const int o = i / NI, f = i % NI;
+            float g = 0.0f;
+            for (int s = 0; s < TILE; ++s) g = fmaf(S.h2[s * LD + o], S.xn[s * NI + f], g);
+            atomicAdd(grad + OFF_W1 + i, g);
+        } else {
+            const int o = i - NH * NI;
+            float g = 0.0f;
+            for (int s = 0; s < TILE; ++s) g += S.h2[s * LD + o];
+            atomicAdd(grad + OFF_B1 + o, g);
+        }
+    }
+}
+
+// Adam (Kingma & Ba 2015) on the FP32 master weights; also refreshes the bf16-rounded copy.
+__global__ void adam_kernel(float* __restrict__ theta, float* __restrict__ wbf,
+                            float* __restrict__ m, float* __restrict__ v,
+                            const float* __restrict__ g, float lr, float b1, float b2, float c1,
+                            float c2, float eps) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= NPARAM) return;
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.0f - b1) * gi;
+    const float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    const float t = theta[i] - lr * (mi * c1) / (sqrtf(vi * c2) + eps);
+    theta[i] = t;
+    wbf[i] = __bfloat162float(__float2bfloat16_rn(t));
+}
+
+__global__ void round_bf16_kernel(const float* __restrict__ theta, float* __restrict__ wbf) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < NPARAM) wbf[i] = __bfloat162float(__float2bfloat16_rn(theta[i]));
+}
+
+// splitmix64 (Steele, Lea & Flood 2014) as a counter-based generator for minibatch rows.
+__device__ __forceinline__ unsigned long long splitmix64(unsigned long long z) {
+    z += 0x9E3779B97F4A7C15ULL;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+
+__global__ void gather_kernel(const float* __restrict__ X, const float* __restrict__ Yt, long long N,
+                              int batch, unsigned long long key, float* __restrict__ Xb,
+                              float* __restrict__ Yb) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= batch) return;
+    const long long r = (long long)(splitmix64(key + (unsigned long long)i) % (unsigned long long)N);
+#pragma unroll
+    for (int f = 0; f < NI; ++f) Xb[i * NI + f] = X[r * NI + f];
+#pragma unroll
+    for (int o = 0; o < NO; ++o) Yb[i * NO + o] = Yt[r * NO + o];
+}
+
+// per-feature sum and sum of squares (FP64) for the input standardisation
+__global__ void moments_kernel(const float* __restrict__ X, long long N, double* __restrict__ acc) {
+    double s[NI] = {}, q[NI] = {};
+    for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < N;
+         r += (long long)gridDim.x * blockDim.x)
+#pragma unroll
+        for (int f = 0; f < NI; ++f) {
+            const double x = X[r * NI + f];
+            s[f] += x;
+            q[f] += x * x;
+        }
+#pragma unroll
+    for (int f = 0; f < NI; ++f) {
+        atomicAdd(acc + f, s[f]);
+        atomicAdd(acc + NI + f, q[f]);
+    }
+}
+
+__global__ void finish_moments_kernel(const double* __restrict__ acc, long long N,
+                                      float* __restrict__ norm) {
+    const int f = threadIdx.x;
+    if (f >= NI) return;
+    const double mean = acc[f] / (double)N;
+    const double var = fmax(acc[NI + f] / (double)N - mean * mean, 0.0);
+    norm[f] = (float)mean;
+    norm[NI + f] = (float)fmax(sqrt(var), 1e-6);
+}
+
+}  // namespace
+
+struct rc_mlp_s {
+    int device = 0;
+    float* d = nullptr;   // theta | wbf | m | v | grad | norm(2 NI) | loss | gather buffers
+    float *theta, *wbf, *m, *v, *grad, *norm, *loss;
+    double* d_mom = nullptr;
+    float* Xb = nullptr;
+    float* Yb = nullptr;
+    int batch_cap = 0;
+    float* Ysc = nullptr;          // forward scratch for seeding
+    long long ysc_cap = 0;
+    long long step = 0;
+    unsigned long long seed = 0;
+    float* h_loss = nullptr;       // pinned
+};
+
+namespace {
+
+size_t smem_bytes() { return sizeof(Smem); }
+
+rc_status ensure_configured() {
+    static bool done = false;
+    if (done) return RC_OK;
+    cudaError_t e = cudaFuncSetAttribute(mlp_tile_kernel<true>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes());
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(mlp_tile_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem_bytes());
+    if (e != cudaSuccess) return mcuda(e, "mlp: shared-memory opt-in");
+    done = true;
+    return RC_OK;
+}
+
+rc_status loss_grad(rc_mlp_t n, const float* X, const float* Yt, long long B, cudaStream_t s) {
+    rc_status st = ensure_configured();
+    if (st != RC_OK) return st;
+    cudaMemsetAsync(n->grad, 0, (NPARAM + 1) * sizeof(float), s);   // grad and the loss after it
+    const unsigned grid = (unsigned)((B + TILE - 1) / TILE);
+    mlp_tile_kernel<true><<<grid, THREADS, smem_bytes(), s>>>(n->wbf, n->norm, X, Yt, B, nullptr,
+                                                             n->grad, n->loss);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? RC_OK : mcuda(e, "mlp_tile_kernel");
+}
+
+}  // namespace
+
+extern "C" {
+
+rc_status rc_mlp_create(unsigned long long seed, rc_mlp_t* out) {
+    rcx::set_last_error("");
+    if (!out) return mfail(RC_ERR_ARG, "rc_mlp_create: out is NULL");
+    *out = nullptr;
+    rc_mlp_s* n = new (std::nothrow) rc_mlp_s();
+    if (!n) return mfail(RC_ERR_OOM, "rc_mlp_create: host allocation");
+    cudaGetDevice(&n->device);
+    n->seed = seed;
+    const size_t floats = 5 * (size_t)NPARAM + 2 * NI + 4;
+    cudaError_t e = cudaMalloc(&n->d, floats * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&n->d_mom, 2 * NI * sizeof(double));
+    if (e == cudaSuccess) e = cudaMallocHost(&n->h_loss, sizeof(float));
+    if (e != cudaSuccess) {
+        cudaFree(n->d);
+        cudaFree(n->d_mom);
+        delete n;
+        return mcuda(e, "rc_mlp_create");
+    }
+    n->theta = n->d;
+    n->wbf = n->theta + NPARAM;
+    n->m = n->wbf + NPARAM;
+    n->v = n->m + NPARAM;
+    n->grad = n->v + NPARAM;
+    n->loss = n->grad + NPARAM;      // right after grad: one memset clears both
+    n->norm = n->loss + 4;
+    // Glorot-uniform weights, zero biases, identity standardisation
+    std::vector<float> h(floats, 0.0f);
+    std::mt19937_64 rng(seed);
+    auto fill = [&](int off, int fan_out, int fan_in) {
+        const double a = std::sqrt(6.0 / (fan_in + fan_out));
+        std::uniform_real_distribution<double> U(-a, a);
+        for (int i = 0; i < fan_out * fan_in; ++i) h[off + i] = (float)U(rng);
+    };
+    fill(OFF_W1, NH, NI);
+    fill(OFF_W2, NH, NH);
+    fill(OFF_W3, NO, NH);
+    for (int f = 0; f < NI; ++f) h[5 * NPARAM + 4 + NI + f] = 1.0f;
+    e = cudaMemcpy(n->d, h.data(), floats * sizeof(float), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) {
+        round_bf16_kernel<<<(NPARAM + 255) / 256, 256>>>(n->theta, n->wbf);
+        e = cudaDeviceSynchronize();
+    }
+    if (e != cudaSuccess) {
+        cudaFree(n->d);
+        cudaFree(n->d_mom);
+        cudaFreeHost(n->h_loss);
+        delete n;
+        return mcuda(e, "rc_mlp_create: upload");
+    }
+    *out = n;
+    return RC_OK;
+}
+
+void rc_mlp_destroy(rc_mlp_t n) {
+    if (!n) return;
+    cudaDeviceSynchronize();
+    cudaFree(n->d);
+    cudaFree(n->d_mom);
+    cudaFree(n->Xb);
+    cudaFree(n->Ysc);
+    cudaFreeHost(n->h_loss);
+    delete n;
+}
+
+int rc_mlp_n_params(rc_mlp_t n) { return n ? NPARAM : 0; }
+
+rc_status rc_mlp_set_params(rc_mlp_t n, const float* theta, const float* mean, const float* std_) {
+    rcx::set_last_error("");
+    if (!n) return mfail(RC_ERR_ARG, "rc_mlp_set_params: NULL network");
+    cudaError_t e = cudaSuccess;
+    if (theta) e = cudaMemcpy(n->theta, theta, NPARAM * sizeof(float), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && mean) e = cudaMemcpy(n->norm, mean, NI * sizeof(float), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && std_) e = cudaMemcpy(n->norm + NI, std_, NI * sizeof(float), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && theta) {
+        round_bf16_kernel<<<(NPARAM + 255) / 256, 256>>>(n->theta, n->wbf);
+        cudaMemset(n->m, 0, 2 * NPARAM * sizeof(float));
+        n->step = 0;
+        e = cudaDeviceSynchronize();
+    }
+    return e == cudaSuccess ? RC_OK : mcuda(e, "rc_mlp_set_params");
+}
+
+rc_status rc_mlp_get_params(rc_mlp_t n, float* theta, float* mean, float* std_) {
+    rcx::set_last_error("");
+    if (!n) return mfail(RC_ERR_ARG, "rc_mlp_get_params: NULL network");
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e == cudaSuccess && theta) e = cudaMemcpy(theta, n->theta, NPARAM * sizeof(float), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && mean) e = cudaMemcpy(mean, n->norm, NI * sizeof(float), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && std_) e = cudaMemcpy(std_, n->norm + NI, NI * sizeof(float), cudaMemcpyDeviceToHost);
+    return e == cudaSuccess ? RC_OK : mcuda(e, "rc_mlp_get_params");
+}
+
+rc_status rc_mlp_fit_normalization(rc_mlp_t n, const float* X, long long N, void* stream) {
+    rcx::set_last_error("");
+    if (!n || !X || N < 1) return mfail(RC_ERR_ARG, "rc_mlp_fit_normalization: bad arguments");
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaMemsetAsync(n->d_mom, 0, 2 * NI * sizeof(double), s);
+    moments_kernel<<<256, 256, 0, s>>>(X, N, n->d_mom);
+    finish_moments_kernel<<<1, 32, 0, s>>>(n->d_mom, N, n->norm);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? RC_OK : mcuda(e, "rc_mlp_fit_normalization");
+}
+
+rc_status rc_mlp_forward(rc_mlp_t n, const float* X, long long B, float* Y, void* stream) {
+    rcx::set_last_error("");
+    if (!n || !X || !Y || B < 0) return mfail(RC_ERR_ARG, "rc_mlp_forward: bad arguments");
+    if (B == 0) return RC_OK;
+    rc_status st = ensure_configured();
+    if (st != RC_OK) return st;
+    mlp_tile_kernel<false><<<(unsigned)((B + TILE - 1) / TILE), THREADS, smem_bytes(),
+                             (cudaStream_t)stream>>>(n->wbf, n->norm, X, nullptr, B, Y, nullptr,
+                                                     nullptr);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? RC_OK : mcuda(e, "rc_mlp_forward");
+}
+
+rc_status rc_mlp_loss_grad(rc_mlp_t n, const float* X, const float* Yt, long long B, float* grad,
+                           float* loss, void* stream) {
+    rcx::set_last_error("");
+    if (!n || !X || !Yt || B < 1) return mfail(RC_ERR_ARG, "rc_mlp_loss_grad: bad arguments");
+    cudaStream_t s = (cudaStream_t)stream;
+    rc_status st = loss_grad(n, X, Yt, B, s);
+    if (st != RC_OK) return st;
+    cudaError_t e = cudaSuccess;
+    if (grad) e = cudaMemcpyAsync(grad, n->grad, NPARAM * sizeof(float), cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess && loss) e = cudaMemcpyAsync(loss, n->loss, sizeof(float), cudaMemcpyDeviceToDevice, s);
+    return e == cudaSuccess ? RC_OK : mcuda(e, "rc_mlp_loss_grad");
+}
+
+rc_status rc_mlp_train(rc_mlp_t n, const float* X, const float* Yt, long long N, int batch,
+                       int steps, float lr, float* loss_history, void* stream) {
+    rcx::set_last_error("");
+    if (!n || !X || !Yt || N < 1 || batch < 1 || steps < 0 || !(lr > 0))
+        return mfail(RC_ERR_ARG, "rc_mlp_train: bad arguments");
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e;
+    if (n->batch_cap < batch) {
+        cudaStreamSynchronize(s);
+        cudaFree(n->Xb);
+        n->Xb = n->Yb = nullptr;
+        n->batch_cap = 0;
+        if ((e = cudaMalloc(&n->Xb, (size_t)batch * (NI + NO) * sizeof(float))) != cudaSuccess)
+            return mcuda(e, "rc_mlp_train: minibatch buffers");
+        n->Yb = n->Xb + (size_t)batch * NI;
+        n->batch_cap = batch;
+    }
+    const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
+    for (int it = 0; it < steps; ++it) {
+        ++n->step;
+        const unsigned long long key = n->seed * 0x100000001B3ULL + ((unsigned long long)n->step << 32);
+        gather_kernel<<<(batch + 255) / 256, 256, 0, s>>>(X, Yt, N, batch, key, n->Xb, n->Yb);
+        rc_status st = loss_grad(n, n->Xb, n->Yb, batch, s);
+        if (st != RC_OK) return st;
+        const double c1 = 1.0 / (1.0 - std::pow((double)b1, (double)n->step));
+        const double c2 = 1.0 / (1.0 - std::pow((double)b2, (double)n->step));
+        adam_kernel<<<(NPARAM + 255) / 256, 256, 0, s>>>(n->theta, n->wbf, n->m, n->v, n->grad, lr,
+                                                         b1, b2, (float)c1, (float)c2, eps);
+        if (loss_history) {
+            cudaMemcpyAsync(n->h_loss, n->loss, sizeof(float), cudaMemcpyDeviceToHost, s);
+            if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return mcuda(e, "rc_mlp_train");
+            loss_history[it] = *n->h_loss;
+        }
+    }
+    e = cudaGetLastError();
+    return e == cudaSuccess ? RC_OK : mcuda(e, "rc_mlp_train");
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// features, targets and the seed of the non-LTE iteration (need the atom's tables)
+// ---------------------------------------------------------------------------
+namespace {
+
+__global__ void features_kernel(const double* __restrict__ T, const double* __restrict__ ne,
+                                const double* __restrict__ nH, const float* __restrict__ J,
+                                long long ncell, int l0, int l1, int l2, float* __restrict__ X) {
+    const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= ncell) return;
+    float* x = X + c * NI;
+    x[0] = (float)log10(T[c]);
+    x[1] = (float)log10(fmax(ne[c], 1e-300));
+    x[2] = (float)log10(fmax(nH[c], 1e-300));
+    const int ls[3] = {l0, l1, l2};
+#pragma unroll
+    for (int l = 0; l < 3; ++l) x[3 + l] = log10f(fmaxf(J[(size_t)ls[l] * ncell + c], 1e-38f));
+}
+
+__global__ void targets_kernel(const double* __restrict__ T, const double* __restrict__ n_atom,
+                               const double* __restrict__ pops, const double* __restrict__ Ek,
+                               const double* __restrict__ g, int nlev, long long ncell,
+                               float* __restrict__ Y) {
+    const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= ncell) return;
+    double b[8], sum = 0.0;
+    for (int i = 0; i < nlev; ++i) {
+        b[i] = g[i] * exp(-Ek[i] / T[c]);
+        sum += b[i];
+    }
+    for (int i = 0; i < nlev && i < NO; ++i) {
+        const double lte = n_atom[c] * b[i] / sum;
+        Y[c * NO + i] = (float)log10(pops[(size_t)i * ncell + c] / lte);
+    }
+}
+
+__global__ void seed_kernel(const float* __restrict__ Y, const double* __restrict__ T,
+                            const double* __restrict__ n_atom, const double* __restrict__ Ek,
+                            const double* __restrict__ g, int nlev, long long ncell,
+                            double* __restrict__ pops, int* __restrict__ n_fallback) {
+    const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= ncell) return;
+    double lte[8], sum = 0.0;
+    for (int i = 0; i < nlev; ++i) {
+        lte[i] = g[i] * exp(-Ek[i] / T[c]);
+        sum += lte[i];
+    }
+    double p[8], tot = 0.0;
+    bool ok = true;
+    for (int i = 0; i < nlev; ++i) {
+        lte[i] *= n_atom[c] / sum;
+        const double y = i < NO ? (double)Y[c * NO + i] : 0.0;
+        p[i] = lte[i] * exp10(fmin(fmax(y, -30.0), 30.0));
+        ok = ok && isfinite(y) && p[i] > 0.0;
+        tot += p[i];
+    }
+    // the LTE start is the fallback wherever the network's output is unusable
+    if (!ok || !(tot > 0.0) || !isfinite(tot)) {
+        atomicAdd(n_fallback, 1);
+        for (int i = 0; i < nlev; ++i) pops[(size_t)i * ncell + c] = lte[i];
+        return;
+    }
+    for (int i = 0; i < nlev; ++i) pops[(size_t)i * ncell + c] = p[i] * n_atom[c] / tot;
+}
+
+}  // namespace
+
+extern "C" {
+
+rc_status rc_surrogate_features(rc_atom_t atom, const double* T, const double* ne, const double* nH,
+                                const float* J, long long ncell, float* X, void* stream) {
+    rcx::set_last_error("");
+    if (!atom || !T || !ne || !nH || !J || !X || ncell < 0)
+        return mfail(RC_ERR_ARG, "rc_surrogate_features: bad arguments");
+    const double *Ek, *g;
+    int nlev, npl, nlines;
+    rc_status st = rcx::atom_levels(atom, &Ek, &g, &nlev, &npl, &nlines);
+    if (st != RC_OK) return st;
+    if (nlines < 3) return mfail(RC_ERR_UNSUPPORTED, "rc_surrogate_features: needs 3 lines");
+    if (ncell == 0) return RC_OK;
+    features_kernel<<<(unsigned)((ncell + 255) / 256), 256, 0, (cudaStream_t)stream>>>(
+        T, ne, nH, J, ncell, npl / 2, npl + npl / 2, 2 * npl + npl / 2, X);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? RC_OK : mcuda(e, "rc_surrogate_features");
+}
+
+rc_status rc_surrogate_targets(rc_atom_t atom, const double* T, const double* n_atom,
+                               const double* pops, long long ncell, float* Y, void* stream) {
+    rcx::set_last_error("");
+    if (!atom || !T || !n_atom || !pops || !Y || ncell < 0)
+        return mfail(RC_ERR_ARG, "rc_surrogate_targets: bad arguments");
+    const double *Ek, *g;
+    int nlev, npl, nlines;
+    rc_status st = rcx::atom_levels(atom, &Ek, &g, &nlev, &npl, &nlines);
+    if (st != RC_OK) return st;
+    if (nlev != NO) return mfail(RC_ERR_UNSUPPORTED, "rc_surrogate_targets: the network predicts 3 levels");
+    if (ncell == 0) return RC_OK;
+    targets_kernel<<<(unsigned)((ncell + 255) / 256), 256, 0, (cudaStream_t)stream>>>(
+        T, n_atom, pops, Ek, g, nlev, ncell, Y);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? RC_OK : mcuda(e, "rc_surrogate_targets");
+}
+
+rc_status rc_surrogate_seed(rc_atom_t atom, rc_mlp_t net, const float* X, const double* T,
+                            const double* n_atom, long long ncell, double* pops, int* n_fallback,
+                            void* stream) {
+    rcx::set_last_error("");
+    if (!atom || !net || !X || !T || !n_atom || !pops || ncell < 0)
+        return mfail(RC_ERR_ARG, "rc_surrogate_seed: bad arguments");
+    const double *Ek, *g;
+    int nlev, npl, nlines;
+    rc_status st = rcx::atom_levels(atom, &Ek, &g, &nlev, &npl, &nlines);
+    if (st != RC_OK) return st;
+    if (nlev != NO) return mfail(RC_ERR_UNSUPPORTED, "rc_surrogate_seed: the network predicts 3 levels");
+    if (ncell == 0) return RC_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e;
+    if (net->ysc_cap < ncell) {
+        cudaStreamSynchronize(s);
+        cudaFree(net->Ysc);
+        net->Ysc = nullptr;
+        net->ysc_cap = 0;
+        if ((e = cudaMalloc(&net->Ysc, (size_t)ncell * NO * sizeof(float) + 16)) != cudaSuccess)
+            return mcuda(e, "rc_surrogate_seed: scratch");
+        net->ysc_cap = ncell;
+    }
+    int* d_fb = reinterpret_cast<int*>(net->Ysc + (size_t)ncell * NO);
+    cudaMemsetAsync(d_fb, 0, sizeof(int), s);
+    st = rc_mlp_forward(net, X, ncell, net->Ysc, stream);
+    if (st != RC_OK) return st;
+    seed_kernel<<<(unsigned)((ncell + 255) / 256), 256, 0, s>>>(net->Ysc, T, n_atom, Ek, g, nlev,
+                                                                ncell, pops, d_fb);
+    if ((e = cudaGetLastError()) != cudaSuccess) return mcuda(e, "rc_surrogate_seed");
+    if (n_fallback) {
+        if ((e = cudaMemcpyAsync(n_fallback, d_fb, sizeof(int), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+            (e = cudaStreamSynchronize(s)) != cudaSuccess)
+            return mcuda(e, "rc_surrogate_seed: fallback count");
+    }
+    return RC_OK;
+}
+
+}  // extern "C"

@@ -243,7 +243,7 @@ struct rc_atom_s {
     int device = 0;
     AtomDev dev{};
     int n_lambda = 0;
-    double* d_grid = nullptr;     // dnu then w
+    double* d_grid = nullptr;     // dnu, w, then E/k and g of the levels
     // driver workspace
     float* d_ws = nullptr;
     size_t ws_floats = 0;
@@ -306,7 +306,7 @@ rc_status rc_atom_create(const rc_atom_desc* d, rc_atom_t* out) {
     }
     const double m = d->mass_amu * kAmu;
     const double beta = kH * kH / (std::pow(2.0 * kPi * kMe, 1.5) * std::sqrt(kK));
-    std::vector<double> grid(2 * (size_t)d->n_lines * d->n_per_line);
+    std::vector<double> grid(2 * (size_t)d->n_lines * d->n_per_line + 2 * kMaxLevels, 0.0);
     double* hdnu = grid.data();
     double* hw = grid.data() + (size_t)d->n_lines * d->n_per_line;
     for (int li = 0; li < d->n_lines; ++li) {
@@ -339,6 +339,11 @@ rc_status rc_atom_create(const rc_atom_desc* d, rc_atom_t* out) {
             hw[(size_t)li * d->n_per_line + k] = (k == 0 || k == d->n_per_line - 1) ? 0.5 * step : step;
         }
     }
+    double* hlev = grid.data() + 2 * (size_t)d->n_lines * d->n_per_line;
+    for (int i = 0; i < d->n_levels; ++i) {
+        hlev[i] = A.E_k[i];
+        hlev[kMaxLevels + i] = A.g[i];
+    }
     cudaError_t e = cudaMalloc(&a->d_grid, grid.size() * sizeof(double));
     if (e == cudaSuccess)
         e = cudaMemcpy(a->d_grid, grid.data(), grid.size() * sizeof(double), cudaMemcpyHostToDevice);
@@ -368,6 +373,22 @@ void rc_atom_destroy(rc_atom_t a) {
 }
 
 int rc_atom_n_lambda(rc_atom_t a) { return a ? a->n_lambda : 0; }
+
+}  // extern "C"
+
+rc_status rcx::atom_levels(rc_atom_t a, const double** Ek, const double** g, int* nlev,
+                           int* n_per_line, int* n_lines) {
+    if (!a) return nfail(RC_ERR_ARG, "atom is NULL");
+    const double* lev = a->d_grid + 2 * (size_t)a->dev.n_lines * a->dev.n_per_line;
+    *Ek = lev;
+    *g = lev + kMaxLevels;
+    *nlev = a->dev.n_levels;
+    *n_per_line = a->dev.n_per_line;
+    *n_lines = a->dev.n_lines;
+    return RC_OK;
+}
+
+extern "C" {
 
 rc_status rc_lte(rc_atom_t a, const double* T, const double* nH, long long ncell, double* ne,
                  double* n_atom, double* pops, void* stream) {

@@ -29,7 +29,10 @@ EXPORTS = [
     "rc_formal_solve_mali", "rc_atom_create", "rc_atom_destroy", "rc_atom_n_lambda", "rc_lte",
     "rc_emis_opac", "rc_stat_eq", "rc_nlte_solve", "rc_plan_set_lane_layout",
     "rc_plan_get_lane_layout", "rc_plan_autotune", "rc_batch_create", "rc_batch_run",
-    "rc_batch_info", "rc_batch_destroy", "rc_formal_solve_batched",
+    "rc_batch_info", "rc_batch_destroy", "rc_formal_solve_batched", "rc_mlp_create",
+    "rc_mlp_destroy", "rc_mlp_n_params", "rc_mlp_set_params", "rc_mlp_get_params",
+    "rc_mlp_fit_normalization", "rc_mlp_forward", "rc_mlp_loss_grad", "rc_mlp_train",
+    "rc_surrogate_features", "rc_surrogate_targets", "rc_surrogate_seed",
 ]
 
 
@@ -144,6 +147,33 @@ def load():
     L.rc_batch_destroy.restype = None
     L.rc_formal_solve_batched.argtypes = [ctypes.c_int, _pp, _pp, _pp, _ip, _pp, _vp]
     L.rc_formal_solve_batched.restype = ctypes.c_int
+    _fp = ctypes.POINTER(ctypes.c_float)
+    L.rc_mlp_create.argtypes = [ctypes.c_ulonglong, ctypes.POINTER(_vp)]
+    L.rc_mlp_create.restype = ctypes.c_int
+    L.rc_mlp_destroy.argtypes = [_vp]
+    L.rc_mlp_destroy.restype = None
+    L.rc_mlp_n_params.argtypes = [_vp]
+    L.rc_mlp_n_params.restype = ctypes.c_int
+    L.rc_mlp_set_params.argtypes = [_vp, _fp, _fp, _fp]
+    L.rc_mlp_set_params.restype = ctypes.c_int
+    L.rc_mlp_get_params.argtypes = [_vp, _fp, _fp, _fp]
+    L.rc_mlp_get_params.restype = ctypes.c_int
+    L.rc_mlp_fit_normalization.argtypes = [_vp, _vp, ctypes.c_longlong, _vp]
+    L.rc_mlp_fit_normalization.restype = ctypes.c_int
+    L.rc_mlp_forward.argtypes = [_vp, _vp, ctypes.c_longlong, _vp, _vp]
+    L.rc_mlp_forward.restype = ctypes.c_int
+    L.rc_mlp_loss_grad.argtypes = [_vp, _vp, _vp, ctypes.c_longlong, _vp, _vp, _vp]
+    L.rc_mlp_loss_grad.restype = ctypes.c_int
+    L.rc_mlp_train.argtypes = [_vp, _vp, _vp, ctypes.c_longlong, ctypes.c_int, ctypes.c_int,
+                               ctypes.c_float, _fp, _vp]
+    L.rc_mlp_train.restype = ctypes.c_int
+    L.rc_surrogate_features.argtypes = [_vp, _vp, _vp, _vp, _vp, ctypes.c_longlong, _vp, _vp]
+    L.rc_surrogate_features.restype = ctypes.c_int
+    L.rc_surrogate_targets.argtypes = [_vp, _vp, _vp, _vp, ctypes.c_longlong, _vp, _vp]
+    L.rc_surrogate_targets.restype = ctypes.c_int
+    L.rc_surrogate_seed.argtypes = [_vp, _vp, _vp, _vp, _vp, ctypes.c_longlong, _vp,
+                                    ctypes.POINTER(ctypes.c_int), _vp]
+    L.rc_surrogate_seed.restype = ctypes.c_int
     _lib = L
     return L
 
@@ -475,3 +505,106 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+class MLP:
+    """rc_mlp_create: the 6-64-64-3 surrogate network trained and run by librcx.so."""
+
+    def __init__(self, seed: int = 0):
+        h = _vp()
+        check(load().rc_mlp_create(seed, ctypes.byref(h)))
+        self._h = h
+        self.n_params = load().rc_mlp_n_params(h)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().rc_mlp_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_params(self, theta=None, mean=None, std=None):
+        def p(a, n):
+            if a is None:
+                return None
+            a = np.ascontiguousarray(a, dtype=np.float32)
+            assert a.size == n
+            self._hold = getattr(self, "_hold", []) + [a]
+            return a.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+        check(load().rc_mlp_set_params(self._h, p(theta, self.n_params), p(mean, 6), p(std, 6)))
+        self._hold = []
+
+    def get_params(self):
+        th = np.empty(self.n_params, np.float32)
+        mu = np.empty(6, np.float32)
+        sd = np.empty(6, np.float32)
+        fp = ctypes.POINTER(ctypes.c_float)
+        check(load().rc_mlp_get_params(self._h, th.ctypes.data_as(fp), mu.ctypes.data_as(fp),
+                                       sd.ctypes.data_as(fp)))
+        return th, mu, sd
+
+    def fit_normalization(self, X, stream=None):
+        check(load().rc_mlp_fit_normalization(self._h, _dev_ptr(X, "X", (X.shape[0], 6)), X.shape[0],
+                                              _stream_ptr(stream)))
+
+    def forward(self, X, stream=None):
+        import torch
+        Y = torch.empty((X.shape[0], 3), dtype=torch.float32, device=X.device)
+        check(load().rc_mlp_forward(self._h, _dev_ptr(X, "X", (X.shape[0], 6)), X.shape[0],
+                                    _dev_ptr(Y, "Y", Y.shape), _stream_ptr(stream)))
+        return Y
+
+    def loss_grad(self, X, Yt, stream=None):
+        import torch
+        g = torch.empty(self.n_params, dtype=torch.float32, device=X.device)
+        l = torch.empty(1, dtype=torch.float32, device=X.device)
+        check(load().rc_mlp_loss_grad(self._h, _dev_ptr(X, "X", (X.shape[0], 6)),
+                                      _dev_ptr(Yt, "Y", (X.shape[0], 3)), X.shape[0],
+                                      _dev_ptr(g, "grad", g.shape), _dev_ptr(l, "loss", (1,)),
+                                      _stream_ptr(stream)))
+        return float(l.item()), g
+
+    def train(self, X, Yt, batch: int, steps: int, lr: float, record: bool = True, stream=None):
+        hist = (ctypes.c_float * max(steps, 1))() if record else None
+        check(load().rc_mlp_train(self._h, _dev_ptr(X, "X", (X.shape[0], 6)),
+                                  _dev_ptr(Yt, "Y", (X.shape[0], 3)), X.shape[0], batch, steps, lr,
+                                  hist, _stream_ptr(stream)))
+        return [hist[i] for i in range(steps)] if record else None
+
+
+def surrogate_features(atom: Atom, T, ne, nH, J, stream=None):
+    import torch
+    n = T.numel()
+    X = torch.empty((n, 6), dtype=torch.float32, device=T.device)
+    check(load().rc_surrogate_features(
+        atom._h, _dev_ptr(T.reshape(-1), "T", (n,), "float64"), _dev_ptr(ne.reshape(-1), "ne", (n,), "float64"),
+        _dev_ptr(nH.reshape(-1), "nH", (n,), "float64"), _dev_ptr(J.reshape(atom.n_lambda, n), "J", (atom.n_lambda, n)),
+        n, _dev_ptr(X, "X", X.shape), _stream_ptr(stream)))
+    return X
+
+
+def surrogate_targets(atom: Atom, T, n_atom, pops, stream=None):
+    import torch
+    n = T.numel()
+    Y = torch.empty((n, 3), dtype=torch.float32, device=T.device)
+    check(load().rc_surrogate_targets(
+        atom._h, _dev_ptr(T.reshape(-1), "T", (n,), "float64"),
+        _dev_ptr(n_atom.reshape(-1), "n_atom", (n,), "float64"),
+        _dev_ptr(pops, "pops", (atom.n_levels, n), "float64"), n, _dev_ptr(Y, "Y", Y.shape),
+        _stream_ptr(stream)))
+    return Y
+
+
+def surrogate_seed(atom: Atom, net: MLP, X, T, n_atom, pops, stream=None):
+    """Writes seeded populations into pops (device FP64); returns the LTE-fallback cell count."""
+    n = T.numel()
+    fb = ctypes.c_int()
+    check(load().rc_surrogate_seed(
+        atom._h, net._h, _dev_ptr(X, "X", (n, 6)), _dev_ptr(T.reshape(-1), "T", (n,), "float64"),
+        _dev_ptr(n_atom.reshape(-1), "n_atom", (n,), "float64"), n,
+        _dev_ptr(pops, "pops", (atom.n_levels, n), "float64"), ctypes.byref(fb), _stream_ptr(stream)))
+    return fb.value

@@ -50,6 +50,22 @@ def _env_int(name, default):
         return default
 
 
+def rank_lambdas(rank: int, n_lambda: int):
+    """Wavelength indices of one rank: every rank solves its own n_lambda-wavelength batch
+    of the GRF recipe (weak scaling; the slices are independent, Sec. 3.6)."""
+    return list(range(rank * n_lambda, (rank + 1) * n_lambda))
+
+
+def max_over_ranks(value: float, dist=None, device="cpu") -> float:
+    """Maximum of a per-rank scalar over all ranks (the step time of the slowest rank)."""
+    if dist is None:
+        return float(value)
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def _load_crossings(n_side, n_casc):
     with open(os.path.join(ROOT, "tests", "golden", "crossings.json")) as f:
         return json.load(f)["plans"][_cross_key(n_side, n_casc)]
@@ -179,7 +195,7 @@ def run_ours(args):
     rbuild.build()
 
     n_side, n_lambda, n_casc = args.n_side, args.n_lambda, args.n_cascades
-    lams = list(range(rank * n_lambda, (rank + 1) * n_lambda))
+    lams = rank_lambdas(rank, n_lambda)
     chi_h, eta_h = workloads.grf_fields(n_side, n_lambda, lambdas=lams)
     chi = torch.from_numpy(chi_h).cuda()
     eta = torch.from_numpy(eta_h).cuda()
@@ -215,11 +231,8 @@ def run_ours(args):
     torch.cuda.synchronize()
     clk = clocks.stop()
     plan.set_timing(False)
-    ms_step = ev0.elapsed_time(ev1) / args.steps
+    ms_step = max_over_ranks(ev0.elapsed_time(ev1) / args.steps, dist, "cuda")
     if dist:
-        t = torch.tensor([ms_step], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_step = float(t.item())
         dist.barrier()
     value = world * n_lambda / (ms_step / 1e3)
 
@@ -235,11 +248,7 @@ def run_ours(args):
         t0 = time.perf_counter()
         for _ in range(args.steps):
             plan.formal_solve_host(chi_p, eta_p, J_p)
-        t_e2e = (time.perf_counter() - t0) / args.steps
-        if dist:
-            t = torch.tensor([t_e2e], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            t_e2e = float(t.item())
+        t_e2e = max_over_ranks((time.perf_counter() - t0) / args.steps, dist, "cuda")
         slab = n_lambda * n_side * n_side * 4
         e2e = {"value": world * n_lambda / t_e2e, "unit": UNIT,
                "h2d_bytes_per_step": 2 * slab, "d2h_bytes_per_step": slab,
@@ -437,14 +446,103 @@ def run_nlte(args):
     print(json.dumps(out), flush=True)
 
 
+def run_batched(args):
+    """The uneven multi-domain workload: 16 domains (sides 256..2048, 32..128 wavelengths,
+    seed 7, GRF recipe, 8 cascades) with 16-bit interval storage, one graph replay per step
+    (one persistent launch per cascade over all domains); compared with solving the domains
+    one after another through rc_formal_solve."""
+    import torch
+
+    from paper_2408_14425_b300 import build as rbuild
+    from paper_2408_14425_b300 import rcx, workloads
+    torch.cuda.set_device(_env_int("LOCAL_RANK", 0))
+    if _env_int("RANK", 0) != 0:
+        return
+    rbuild.build()
+    doms = workloads.batched_domains()
+    plans, chis, etas, Js = [], [], [], []
+    for side, nl, sb in doms:
+        chi, eta = workloads.grf_fields(side, nl, seed_base=sb)
+        plans.append(rcx.Plan(side, side, 8, precision=args.precision))
+        chis.append(torch.from_numpy(chi).cuda())
+        etas.append(torch.from_numpy(eta).cuda())
+        Js.append(torch.empty_like(chis[-1]))
+        del chi, eta
+    t0 = time.perf_counter()
+    batch = rcx.Batch(plans, chis, etas, Js, autotune=not args.no_autotune)
+    t_create = time.perf_counter() - t0
+    info = batch.info()
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        batch.run()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    time.sleep(0.3)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        batch.run()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    # the same work domain by domain (one rc_formal_solve per domain, same lane layout)
+    for _ in range(2):
+        for p, c, e, j in zip(plans, chis, etas, Js):
+            p.formal_solve(c, e, j)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    for p, c, e, j in zip(plans, chis, etas, Js):
+        p.formal_solve(c, e, j)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms_seq = ev0.elapsed_time(ev1)
+    slices = sum(nl for _, nl, _ in doms)
+    alg = 0
+    have_cross = True
+    for (side, nl, _), p in zip(doms, plans):
+        try:
+            cross = _load_crossings(side, 8)
+        except KeyError:
+            have_cross = False
+            break
+        alg += sum(_algorithmic_bytes(cross, p, nl, side)[0])
+    peak, peak_kind = _peaks()
+    line = {"metric": "RC wavelength-slices/s, batched uneven domains", "value": round(slices / (ms / 1e3), 2),
+            "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(ms, 3), "higher_is_better": True, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": "16 domains, sides " + ",".join(str(s) for s, _, _ in doms) +
+                       " (seed 7), 32..128 wavelengths each (" + str(slices) + " slices), GRF "
+                       "recipe, 8 cascades, W0=4, branching 4, interval0=1", "storage": args.precision,
+                       "lane_layout": [info["lambda_block"], info["lambda_per_lane"]],
+                       "launches_per_step": info["launches"], "graph": True,
+                       "autotune": not args.no_autotune, "create_seconds": round(t_create, 2)},
+            "sequential_ms_per_step": round(ms_seq, 3),
+            "batched_speedup": round(ms_seq / ms, 3),
+            "cell_wavelengths_per_s": round(sum(s * s * nl for s, nl, _ in doms) / (ms / 1e3), 1),
+            "clocks": clk}
+    if have_cross:
+        line["roofline"] = {"bound": "hbm", "achieved": round(alg / (ms / 1e3) / 1e9, 1),
+                            "peak": peak, "unit": "GB/s", "frac": round(alg / (ms / 1e3) / 1e9 / peak, 4),
+                            "peak_kind": peak_kind, "traffic": None,
+                            "kernel": "whole step (batched pack + 8 batched cascade launches)",
+                            "algorithmic_bytes_per_step": alg}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["formal", "nlte"], default="formal",
-                    help="formal: the RC formal solution (headline); nlte: time-to-1e-3")
+    ap.add_argument("--workload", choices=["formal", "nlte", "batched"], default="formal",
+                    help="formal: the RC formal solution (headline); nlte: time-to-1e-3; "
+                         "batched: 16 uneven domains in one graph")
+    ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--train-atmospheres", type=int, default=200)
     ap.add_argument("--train-steps", type=int, default=4000)
     ap.add_argument("--nlte-max-iter", type=int, default=3000)
@@ -463,6 +561,10 @@ def main():
         run_reference(args)
     elif args.workload == "nlte":
         run_nlte(args)
+    elif args.workload == "batched":
+        if args.precision == "f32" and "--precision" not in sys.argv:
+            args.precision = "bf16"
+        run_batched(args)
     else:
         run_ours(args)
 

@@ -69,6 +69,10 @@ def lib():
                                    ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                    ctypes.c_double, ctypes.c_int, _dp, _dp, _llp]
         L.rco_rc_solve.restype = ctypes.c_int
+        L.rco_rc_solve_fix.argtypes = [_dp, _dp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                       ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                       ctypes.c_double, ctypes.c_int, ctypes.c_int, _dp, _dp, _llp]
+        L.rco_rc_solve_fix.restype = ctypes.c_int
         L.rco_count_crossings.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                           ctypes.c_int, ctypes.c_double, ctypes.c_int, _llp]
         L.rco_count_crossings.restype = ctypes.c_longlong
@@ -163,10 +167,11 @@ def merge(near, far):
 
 def rc_solve(chi, eta, n_cascades: int, dirs0: int = 4, branching: int = 4,
              interval0: float = 1.0, rule: int = 0, voxel: float = 1.0,
-             want_alo: bool = False, threads: int | None = None):
+             want_alo: bool = False, threads: int | None = None, bilinear_fix: bool = False):
     """RC formal solution.  chi/eta: [n_lambda][nz][nx] (or [nz][nx]).
 
     Returns (J, alo or None, crossings_per_level of one wavelength), J in FP64.
+    bilinear_fix selects the bilinear fix of Sec. 2.5.
     """
     chi = _f64(chi)
     eta = _f64(eta)
@@ -181,9 +186,9 @@ def rc_solve(chi, eta, n_cascades: int, dirs0: int = 4, branching: int = 4,
     L = lib()
     if threads is not None:
         L.rco_set_num_threads(int(threads))
-    rc = L.rco_rc_solve(_ptr(chi), _ptr(eta), nx, nz, nl, voxel, n_cascades, dirs0, branching,
-                        interval0, rule, _ptr(J), _ptr(alo) if alo is not None else None,
-                        cross.ctypes.data_as(_llp))
+    rc = L.rco_rc_solve_fix(_ptr(chi), _ptr(eta), nx, nz, nl, voxel, n_cascades, dirs0,
+                            branching, interval0, rule, int(bilinear_fix), _ptr(J),
+                            _ptr(alo) if alo is not None else None, cross.ctypes.data_as(_llp))
     if rc != 0:
         raise ValueError("rco_rc_solve rejected its arguments")
     if squeeze:

@@ -248,13 +248,36 @@ static void upper_weights(int m, int i, int P_up, int* j0, int* j1, double* f)
  * crossings of one wavelength per cascade.
  * Returns 0, or -1 on bad arguments / allocation failure.
  */
+int rco_rc_solve_fix(const double* chi, const double* eta, int nx, int nz,
+                     int n_lambda, double voxel, int n_cascades, int dirs0,
+                     int branching, double interval0, int rule, int bilinear_fix,
+                     double* J, double* alo, long long* crossings_per_level);
+
 int rco_rc_solve(const double* chi, const double* eta, int nx, int nz,
                  int n_lambda, double voxel, int n_cascades, int dirs0,
                  int branching, double interval0, int rule, double* J,
                  double* alo, long long* crossings_per_level)
 {
+    return rco_rc_solve_fix(chi, eta, nx, nz, n_lambda, voxel, n_cascades, dirs0, branching,
+                            interval0, rule, 0, J, alo, crossings_per_level);
+}
+
+/*
+ * As rco_rc_solve; with bilinear_fix != 0 every cascade-i ray below the top is traced
+ * from its own start p + a_i w to the start of the child interval on each of the four
+ * bracketing cascade-(i+1) probes, x_b + a_{i+1} w, merged there with that probe's
+ * child-cone average, and the four merged values are averaged with the usual bilinear
+ * weights (Sec. 2.5, the bilinear fix).  The diagonal operator (alo) is defined for the
+ * basic construction only: with the fix a child interval may start inside the probe's
+ * own cell, so alo must be NULL then.
+ */
+int rco_rc_solve_fix(const double* chi, const double* eta, int nx, int nz,
+                     int n_lambda, double voxel, int n_cascades, int dirs0,
+                     int branching, double interval0, int rule, int bilinear_fix,
+                     double* J, double* alo, long long* crossings_per_level)
+{
     if (nx <= 0 || nz <= 0 || n_lambda < 0 || n_cascades < 1 || dirs0 < 1 ||
-        branching < 1 || !(interval0 > 0.0))
+        branching < 1 || !(interval0 > 0.0) || (bilinear_fix && alo))
         return -1;
     if (crossings_per_level)
         for (int i = 0; i < n_cascades; ++i) crossings_per_level[i] = 0;
@@ -292,6 +315,37 @@ int rco_rc_solve(const double* chi, const double* eta, int nx, int nz,
                     for (long long k = 0; k < W; ++k) {
                         double wx, wz, I, tau;
                         rco_direction(k, W, &wx, &wz);
+                        if (R_up && bilinear_fix) {
+                            double a_up, b_up;
+                            rco_interval(rule, interval0, branching, i + 1, n_cascades, &a_up, &b_up);
+                            const double Ax = ox + a * wx, Az = oz + a * wz;
+                            const double up_spacing = (double)(1 << (i + 1));
+                            int jz[2] = {jz0, jz1}, jx[2] = {jx0, jx1};
+                            double wzz[2] = {1.0 - fz, fz}, wxx[2] = {1.0 - fx, fx};
+                            double Rm = 0.0;
+                            for (int q = 0; q < 2; ++q)
+                                for (int r = 0; r < 2; ++r) {
+                                    const double Bx = ((double)jx[r] + 0.5) * up_spacing + a_up * wx;
+                                    const double Bz = ((double)jz[q] + 0.5) * up_spacing + a_up * wz;
+                                    const double L = hypot(Bx - Ax, Bz - Az);
+                                    double Ib = 0.0, tb = 0.0;
+                                    if (L > 0.0)
+                                        lvl_cross += rco_march(ch, et, nx, nz, voxel, Ax, Az,
+                                                               (Bx - Ax) / L, (Bz - Az) / L, 0.0,
+                                                               L, &Ib, &tb);
+                                    const double* Rp =
+                                        R_up + ((size_t)jz[q] * Px_up + jx[r]) * (size_t)W_up;
+                                    double avg = 0.0;
+                                    for (int c = 0; c < branching; ++c)
+                                        avg += Rp[(size_t)(k * branching + c)];
+                                    avg /= (double)branching;
+                                    double Imerged, taum;
+                                    rco_merge(Ib, tb, avg, 0.0, &Imerged, &taum);
+                                    Rm += wzz[q] * wxx[r] * Imerged;
+                                }
+                            R[((size_t)pz * Px + px) * (size_t)W + (size_t)k] = Rm;
+                            continue;
+                        }
                         lvl_cross += rco_march(ch, et, nx, nz, voxel, ox, oz, wx, wz,
                                                a, b, &I, &tau);
                         double Rm = I;

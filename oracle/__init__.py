@@ -197,6 +197,45 @@ def rc_solve(chi, eta, n_cascades: int, dirs0: int = 4, branching: int = 4,
     return J, alo, cross
 
 
+def gauss_radau_inclinations(n: int):
+    """n-point Gauss-Radau rule for mu = cos(angle to the invariant y axis) on [0, 1] with
+    the fixed node at mu = 0 (the in-plane ray): nodes and weights summing to 1.
+    From the rule on [-1, 1] with the fixed node -1: the free nodes are the roots of
+    (P_{n-1} + P_n)/(1 + x), weights 2/n^2 at -1 and (1 - x)/(n P_{n-1}(x))^2 elsewhere."""
+    from numpy.polynomial import legendre as L
+    if n == 1:
+        return np.array([0.0]), np.array([1.0])
+    c = np.zeros(n + 1)
+    c[n - 1] = 1.0
+    c[n] = 1.0
+    roots = np.sort(np.real(L.legroots(c)))
+    roots = roots[np.abs(roots + 1.0) > 1e-10]
+    e = np.zeros(n)
+    e[n - 1] = 1.0
+    x = np.concatenate([[-1.0], roots])
+    w = np.concatenate([[2.0 / n ** 2], (1.0 - roots) / (n * L.legval(roots, e)) ** 2])
+    return (x + 1.0) / 2.0, w / 2.0
+
+
+def rc_solve_inclined(chi, eta, n_cascades: int, n_incl: int, want_alo: bool = False, **kw):
+    """2D invariance (Sec. 3.1): every flatland ray stands for n_incl rays with the same x-z
+    projection and inclinations mu_j to the invariant axis.  Along such a ray the path per
+    projected length is 1/sqrt(1 - mu_j^2), so each inclination is the flatland problem with
+    chi and eta scaled by that factor; J (and alo) are their Gauss-Radau weighted sum."""
+    mu, w = gauss_radau_inclinations(n_incl)
+    chi = _f64(chi)
+    eta = _f64(eta)
+    J = 0.0
+    alo = 0.0 if want_alo else None
+    for m, wj in zip(mu, w):
+        r = 1.0 / np.sqrt(1.0 - m * m)
+        Jj, aj, _ = rc_solve(chi * r, eta * r, n_cascades, want_alo=want_alo, **kw)
+        J = J + wj * Jj
+        if want_alo:
+            alo = alo + wj * aj
+    return J, alo
+
+
 def count_crossings(nx: int, nz: int, n_cascades: int, dirs0: int = 4, branching: int = 4,
                     interval0: float = 1.0, rule: int = 0):
     """Voxel crossings per cascade of one wavelength (geometry only)."""

@@ -374,3 +374,32 @@ def test_rc_close_to_long_characteristics():
     rel = np.abs(J_rc / J_lc - 1)
     assert np.median(rel) < 0.03
     assert np.linalg.norm(J_rc - J_lc) / np.linalg.norm(J_lc) < 0.06
+
+
+@pytest.mark.parametrize("n", [1, 2, 4, 8])
+def test_gauss_radau_inclination_rule(n):
+    """Fixed node at mu = 0, weights summing to 1, exact for polynomials up to degree 2n - 2
+    on [0, 1] (Sec. 3.1 uses eight Gauss-Radau inclinations)."""
+    mu, w = oracle.gauss_radau_inclinations(n)
+    assert mu[0] == 0.0 and np.all(np.diff(mu) > 0) and mu[-1] < 1.0
+    assert w.sum() == pytest.approx(1.0, rel=1e-12)
+    for p in range(2 * n - 1):
+        assert np.sum(w * mu ** p) == pytest.approx(1.0 / (p + 1), rel=1e-11, abs=1e-14)
+    if n > 1:   # and not beyond: degree 2n - 1 is not integrated exactly
+        assert abs(np.sum(w * mu ** (2 * n - 1)) - 1.0 / (2 * n)) > 1e-12
+
+
+def test_inclinations_thick_and_thin_limits():
+    """Thick: J = S whatever the inclination.  Thin: every inclination adds the emission along
+    a path 1/sqrt(1 - mu^2) longer, so J = J_flat * sum_j w_j / sqrt(1 - mu_j^2)."""
+    rng = np.random.default_rng(8)
+    S = rng.uniform(0.5, 2.0, (16, 16))
+    chi = np.full((16, 16), 60.0)
+    J, _ = oracle.rc_solve_inclined(chi, S * chi, 4, 8)
+    np.testing.assert_allclose(J, S, rtol=1e-12)
+    chi_t = np.full((16, 16), 1e-10)
+    eta_t = rng.uniform(0.5, 2.0, (16, 16)) * 1e-10
+    J_flat, _, _ = oracle.rc_solve(chi_t, eta_t, 4)
+    J_inc, _ = oracle.rc_solve_inclined(chi_t, eta_t, 4, 8)
+    mu, w = oracle.gauss_radau_inclinations(8)
+    np.testing.assert_allclose(J_inc, J_flat * np.sum(w / np.sqrt(1 - mu ** 2)), rtol=1e-7)

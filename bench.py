@@ -202,7 +202,8 @@ def run_ours(args):
     J = torch.empty_like(chi)
     plan = rcx.Plan(n_side, n_side, n_casc, dirs0=4, branching=4, interval0=1.0,
                     precision=args.precision, lambda_block=args.lambda_block,
-                    lambda_per_lane=args.lambda_per_lane)
+                    lambda_per_lane=args.lambda_per_lane, bilinear_fix=args.bilinear_fix,
+                    n_incl=args.n_incl)
     plan.reserve(n_lambda)
     stream = torch.cuda.current_stream()
 
@@ -298,6 +299,7 @@ def run_ours(args):
         "config": {"workload": _workload(n_side, n_lambda, n_casc), "n_side": n_side,
                    "n_lambda_per_gpu": n_lambda, "n_cascades": n_casc, "dirs0": 4, "branching": 4,
                    "interval0": 1.0, "storage": args.precision,
+                   "bilinear_fix": bool(args.bilinear_fix), "n_incl": args.n_incl,
                    "lambda_block": args.lambda_block or 16,
                    "lambda_per_lane": args.lambda_per_lane or min(args.lambda_block or 16, 4),
                    "l2": (f"inputs (chi+eta {2 * n_lambda * n_side * n_side * 4 / 1e6:.0f} MB per GPU) "
@@ -543,6 +545,10 @@ def main():
                     help="formal: the RC formal solution (headline); nlte: time-to-1e-3; "
                          "batched: 16 uneven domains in one graph")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--n-incl", type=int, default=1,
+                    help="inclinations per in-plane ray (2D invariance; not the headline)")
+    ap.add_argument("--bilinear-fix", action="store_true",
+                    help="the bilinear fix of Sec. 2.5 (J only; not the headline workload)")
     ap.add_argument("--train-atmospheres", type=int, default=200)
     ap.add_argument("--train-steps", type=int, default=4000)
     ap.add_argument("--nlte-max-iter", type=int, default=3000)

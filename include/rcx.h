@@ -55,13 +55,20 @@ enum { RC_STORE_F32 = 0, RC_STORE_F16 = 1, RC_STORE_BF16 = 2 };
 typedef struct {
     int precision;       /* RC_STORE_*: F16/BF16 store merged intervals with a per-cascade
                             scale and merge in FP32 (the ray march is always FP32) */
-    int n_incl;          /* inclination rays per in-plane ray (2D invariance, Sec. 3.1); 1 = flatland */
+    int n_incl;          /* inclination rays per in-plane ray (2D invariance, Sec. 3.1): 1 = flatland,
+                            up to 16.  Gauss-Radau nodes in mu = cos(angle to the invariant axis)
+                            on [0, 1) with the fixed node at the in-plane ray; each inclination
+                            marches the same x-z path with chi and eta scaled by
+                            1/sqrt(1 - mu^2); J, alo, J_eff, alo_c are their weighted sum.
+                            Costs n_incl times the flatland work; not in batches. */
     int interval_rule;   /* 0: interval lengths interval0 * 4^i, a_i = sum of the shorter ones;
                             1: a_i = interval0 * 4^(i-1), b_i = interval0 * 4^i (both satisfy Eq. 12-13) */
     int lambda_block;    /* wavelengths marched together along one ray (packed together per
                             voxel): 0 = default (16); 1, 2, 4, 8, 16 or 32 */
     int bilinear_fix;    /* 1: trace each cascade-i ray to the start of each of the four upper
-                            probes' child rays before merging (Sec. 2.5); 0 = basic RC */
+                            probes' child rays before merging (Sec. 2.5; 4x the rays below the
+                            top cascade); serves J only (rc_formal_solve with alo = NULL,
+                            not the MALI outputs or batches); 0 = basic RC */
     int lambda_per_lane; /* wavelengths one GPU lane carries along its ray: 0 = default
                             (min(lambda_block, 4)); 1, 2, 4 or 8, at most lambda_block */
     int reserved[2];     /* must be zero */

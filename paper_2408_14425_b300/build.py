@@ -33,8 +33,9 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if not force and up_to_date():
         return LIB
     tmp = LIB + f".tmp{os.getpid()}"
+    extra = os.environ.get("RCX_NVCC_FLAGS", "").split()   # e.g. -DRCX_MIN_CTAS=6
     cmd = [NVCC, *ARCH, "-O3", "-lineinfo", "-std=c++17", "--shared", "-Xcompiler", "-fPIC",
-           "-Xptxas", "-v" if verbose else "-O3", "-I", os.path.join(ROOT, "include"),
+           "-Xptxas", "-v" if verbose else "-O3", "-I", os.path.join(ROOT, "include"), *extra,
            *sources(), "-o", tmp]
     subprocess.check_call(cmd)
     os.replace(tmp, LIB)

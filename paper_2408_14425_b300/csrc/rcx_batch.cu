@@ -104,8 +104,8 @@ rc_status build(rc_batch_s* b) {
     }
     for (int d = 0; d < n; ++d) {
         rc_plan_s* p = b->plans[d];
-        pargs[d] = rcx::PackArgs{b->chi[d], b->eta[d], b->nl[d], (long long)p->nx * p->nz,
-                                 (float)p->voxel, p->d_packed,
+        pargs[d] = rcx::PackArgs{b->chi[d], b->eta[d], b->nl[d], 1, nullptr,
+                                 (long long)p->nx * p->nz, (float)p->voxel, p->d_packed,
                                  p->opt.precision != RC_STORE_F32 ? p->d_smax : nullptr};
         const long long chunks = ((long long)p->nx * p->nz + 255) / 256;
         const int n_lblk = (b->nl[d] + LB - 1) / LB;
@@ -205,6 +205,12 @@ rc_status rc_batch_create(int n, const rc_plan_t* plans, const float* const* chi
         if (!plans[d] || !chi[d] || !eta[d] || !J[d] || n_lambda[d] < 1)
             return bfail(RC_ERR_ARG, "rc_batch_create: NULL plan/buffer or n_lambda < 1 in domain " +
                                          std::to_string(d));
+        if (plans[d]->n_incl != 1)
+            return bfail(RC_ERR_UNSUPPORTED, "rc_batch_create: inclinations are served by "
+                                             "rc_formal_solve only");
+        if (plans[d]->opt.bilinear_fix)
+            return bfail(RC_ERR_UNSUPPORTED, "rc_batch_create: the bilinear fix is served by "
+                                             "rc_formal_solve only");
         if (plans[d]->C != plans[0]->C || plans[d]->opt.precision != plans[0]->opt.precision ||
             plans[d]->device != plans[0]->device)
             return bfail(RC_ERR_ARG, "rc_batch_create: all plans need the same cascade count, "

@@ -25,6 +25,14 @@
 
 #include "rcx_internal.h"
 
+// Resident CTAs per SM the cascade kernels are compiled for (register budget
+// 65536 / (256 threads x this)).  6 (40 registers, an 8-byte spill) measured 7% faster
+// than 5 (48 registers) on the 1024^2 x 64 x 8-cascade workload: the march is latency
+// bound on its L2 gathers and the extra resident warps hide more of it.
+#ifndef RCX_MIN_CTAS
+#define RCX_MIN_CTAS 6
+#endif
+
 namespace rcx {
 
 // ---------------------------------------------------------------------------
@@ -229,6 +237,61 @@ __device__ __forceinline__ float upper_radiance(const TS* __restrict__ Rup, long
     return 0.25f * fmaf(fz, r1 - r0, r0);
 }
 
+// Child-cone average (1/4 sum of children 4k..4k+3) of one upper probe b.
+template <int LB, typename TS>
+__device__ __forceinline__ float child_average(const TS* __restrict__ Rup, long long b, int W,
+                                               int k, int l) {
+    const float4 c = Store<TS>::load4(Rup + ((size_t)(b * W + k) * LB + l) * 4);
+    return 0.25f * ((c.x + c.y) + (c.z + c.w));
+}
+
+// The bilinear fix (Sec. 2.5) for the ray of probe (px, pz) in direction d starting at
+// distance a: the segment from its start A = o + a d to the start of the child interval of
+// each bracketing upper probe, B = x_b + a_up d, is marched, merged with that probe's child
+// average, and the four results are weighted bilinearly.  R[j] receives the sum.
+template <int LB, int VL, typename TS>
+__device__ __forceinline__ void fixed_rays(const LevelArgs& A, const float2* __restrict__ F,
+                                           const TS* __restrict__ Rup, float sc, int px, int pz,
+                                           float ox, float oz, float2 d, int k, int lane_off,
+                                           unsigned off_hi, float (&R)[VL]) {
+    int jx[2], jz[2];
+    float fx, fz;
+    upper_coord(px, A.Px_up, jx[0], jx[1], fx);
+    upper_coord(pz, A.Pz_up, jz[0], jz[1], fz);
+    const float sp_up = 2.0f * A.spacing;
+    const float Ax = ox + A.a * d.x, Az = oz + A.a * d.y;
+#pragma unroll
+    for (int j = 0; j < VL; ++j) R[j] = 0.0f;
+#pragma unroll
+    for (int q = 0; q < 2; ++q)
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+            const float w = (r ? fx : 1.0f - fx) * (q ? fz : 1.0f - fz);
+            if (w == 0.0f) continue;
+            const float dx = ((float)jx[r] + 0.5f) * sp_up + A.a_up * d.x - Ax;
+            const float dz = ((float)jz[q] + 0.5f) * sp_up + A.a_up * d.y - Az;
+            const float L = sqrtf(dx * dx + dz * dz);
+            float I[VL], T[VL], I0[VL];
+            if (L > 0.0f) {
+                const float iL = 1.0f / L;
+                march_interval<LB, VL>(F, A.nx, A.nz, Ax, Az, dx * iL, dz * iL, 0.0f, L,
+                                       lane_off, off_hi, A.max_steps, I, T, I0);
+            } else {
+#pragma unroll
+                for (int j = 0; j < VL; ++j) {
+                    I[j] = 0.0f;
+                    T[j] = 1.0f;
+                }
+            }
+            const long long b = (long long)jz[q] * A.Px_up + jx[r];
+#pragma unroll
+            for (int j = 0; j < VL; ++j) {
+                const float up = child_average<LB, TS>(Rup, b, A.W, k, lane_off + j) * sc;
+                R[j] = fmaf(w, fmaf(T[j], up, I[j]), R[j]);
+            }
+        }
+}
+
 struct Bilinear {
     long long b00, b01, b10, b11;
     float fx, fz;
@@ -247,7 +310,7 @@ struct Bilinear {
 // cascades >= 1: march + merge, store the merged interval
 // ---------------------------------------------------------------------------
 // One CTA-sized chunk `cta` of the rays of lambda block `lb` of one cascade.
-template <int LB, int VL, typename TS, bool HAS_UP>
+template <int LB, int VL, typename TS, bool HAS_UP, bool FIX = false>
 __device__ __forceinline__ void level_body(const LevelArgs& A, int lb, long long cta) {
     constexpr int LPR = LB / VL;   // lanes per ray
     constexpr int G = 32 / LPR;    // rays per warp
@@ -273,10 +336,15 @@ __device__ __forceinline__ void level_body(const LevelArgs& A, int lb, long long
     const int lane_off = q * VL;
     const unsigned off_hi = (unsigned)((A.ncell - 1) * LB + lane_off);
 
+    float R[VL];
+    if constexpr (FIX && HAS_UP) {
+        const TS* Rup = reinterpret_cast<const TS*>(A.R_up) + (size_t)lb * A.R_up_lstride;
+        fixed_rays<LB, VL, TS>(A, F, Rup, A.scale ? A.scale[lb] : 1.0f, px, pz, ox, oz, d, k,
+                               lane_off, off_hi, R);
+    } else {
     float I[VL], T[VL], I0[VL];
     march_interval<LB, VL>(F, A.nx, A.nz, ox, oz, d.x, d.y, A.a, A.b, lane_off, off_hi,
                            A.max_steps, I, T, I0);
-    float R[VL];
     if (HAS_UP) {
         const TS* Rup = reinterpret_cast<const TS*>(A.R_up) + (size_t)lb * A.R_up_lstride;
         const Bilinear bl(px, pz, A.Px_up, A.Pz_up);
@@ -291,6 +359,7 @@ __device__ __forceinline__ void level_body(const LevelArgs& A, int lb, long long
 #pragma unroll
         for (int j = 0; j < VL; ++j) R[j] = I[j];
     }
+    }
     TS* out = reinterpret_cast<TS*>(A.R_out) + (size_t)lb * A.R_out_lstride;
     const float inv = A.scale ? 1.0f / A.scale[lb] : 1.0f;
 #pragma unroll
@@ -298,17 +367,17 @@ __device__ __forceinline__ void level_body(const LevelArgs& A, int lb, long long
         Store<TS>::store(out + ((size_t)(ray >> 2) * LB + lane_off + j) * 4 + (ray & 3), R[j] * inv);
 }
 
-template <int LB, int VL, typename TS, bool HAS_UP>
-__global__ void __launch_bounds__(kWarpsPerCta * 32)
+template <int LB, int VL, typename TS, bool HAS_UP, bool FIX>
+__global__ void __launch_bounds__(kWarpsPerCta * 32, RCX_MIN_CTAS)
 level_kernel(const LevelArgs A) {
-    level_body<LB, VL, TS, HAS_UP>(A, blockIdx.y, blockIdx.x);
+    level_body<LB, VL, TS, HAS_UP, FIX>(A, blockIdx.y, blockIdx.x);
 }
 
 // ---------------------------------------------------------------------------
 // cascade 0: one lane group per cell centre, loop over the W_0 directions,
 // accumulate J (Eq. 1) and the diagonal operator (Eq. 17)
 // ---------------------------------------------------------------------------
-template <int LB, int VL, typename TS, bool HAS_UP>
+template <int LB, int VL, typename TS, bool HAS_UP, bool FIX = false>
 __device__ __forceinline__ void level0_body(const LevelArgs& A, int lb, long long cta) {
     constexpr int LPR = LB / VL;
     constexpr int G = 32 / LPR;
@@ -340,6 +409,14 @@ __device__ __forceinline__ void level0_body(const LevelArgs& A, int lb, long lon
     for (int j = 0; j < VL; ++j) Jsum[j] = Jeff[j] = alo_sum[j] = aloc_sum[j] = 0.0f;
     for (int k = 0; k < A.W; ++k) {
         const float2 d = A.dirs[k];
+        if constexpr (FIX && HAS_UP) {
+            // the bilinear fix serves J only (no diagonal operator, no J_eff)
+            float R[VL];
+            fixed_rays<LB, VL, TS>(A, F, Rup, sc, px, pz, ox, oz, d, k, lane_off, off_hi, R);
+#pragma unroll
+            for (int j = 0; j < VL; ++j) Jsum[j] += R[j];
+            continue;
+        }
         float I[VL], T[VL], I0[VL];
         march_interval<LB, VL, true>(F, A.nx, A.nz, ox, oz, d.x, d.y, A.a, A.b, lane_off,
                                      off_hi, A.max_steps, I, T, I0);
@@ -374,10 +451,10 @@ __device__ __forceinline__ void level0_body(const LevelArgs& A, int lb, long lon
     }
 }
 
-template <int LB, int VL, typename TS, bool HAS_UP>
+template <int LB, int VL, typename TS, bool HAS_UP, bool FIX>
 __global__ void __launch_bounds__(kWarpsPerCta * 32)
 level0_kernel(const LevelArgs A) {
-    level0_body<LB, VL, TS, HAS_UP>(A, blockIdx.y, blockIdx.x);
+    level0_body<LB, VL, TS, HAS_UP, FIX>(A, blockIdx.y, blockIdx.x);
 }
 
 // ---------------------------------------------------------------------------
@@ -387,7 +464,7 @@ level0_kernel(const LevelArgs A) {
 // Chunk t belongs to the last segment whose prefix is <= t.
 // ---------------------------------------------------------------------------
 template <bool LEVEL0, int LB, int VL, typename TS, bool HAS_UP>
-__global__ void __launch_bounds__(kWarpsPerCta * 32)
+__global__ void __launch_bounds__(kWarpsPerCta * 32, RCX_MIN_CTAS)
 batched_level_kernel(const BatchLevelArgs B) {
     for (long long t = blockIdx.x; t < B.total; t += gridDim.x) {
         int lo = 0, hi = B.n_seg - 1;
@@ -405,6 +482,9 @@ batched_level_kernel(const BatchLevelArgs B) {
 // ---------------------------------------------------------------------------
 // packing [lambda][cell] (chi, eta) -> [lambda block][cell][LB] (chi' = chi voxel log2 e, S)
 // ---------------------------------------------------------------------------
+// With n_incl > 1 the packed wavelengths are virtual: l' = l n_incl + j carries the
+// wavelength l with the opacity scaled by the inclination's 1/sqrt(1 - mu_j^2) (Sec. 3.1:
+// same x-z projection, longer path per projected length; S is unchanged).
 template <int LB>
 __global__ void __launch_bounds__(256) pack_kernel(const PackArgs P) {
     const long long cell = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -414,7 +494,8 @@ __global__ void __launch_bounds__(256) pack_kernel(const PackArgs P) {
         float2 v[LB];
 #pragma unroll
         for (int l = 0; l < LB; ++l) {
-            const int lam = lb * LB + l;
+            const int vlam = lb * LB + l;
+            const int lam = vlam / P.n_incl;
             float c = 0.0f, s = 0.0f;
             if (lam < P.n_lambda) {
                 const float chi = __ldg(P.chi + (size_t)lam * P.ncell + cell);
@@ -422,6 +503,7 @@ __global__ void __launch_bounds__(256) pack_kernel(const PackArgs P) {
                 const float cv = fmaxf(chi * P.voxel, kChiFloor);
                 s = (eta * P.voxel) / cv;
                 c = cv * kLog2e;
+                if (P.incl_r) c *= P.incl_r[vlam - lam * P.n_incl];
                 smax = fmaxf(smax, s);
             }
             v[l] = make_float2(c, s);
@@ -495,6 +577,17 @@ __global__ void __launch_bounds__(256) batched_pack_kernel(const BatchPackArgs B
     }
 }
 
+__global__ void incl_reduce_kernel(const float* __restrict__ in, float* __restrict__ out,
+                                   int n_lambda, int n_incl, const float* __restrict__ w,
+                                   long long ncell) {
+    const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int l = blockIdx.y;
+    if (c >= ncell || l >= n_lambda) return;
+    float s = 0.0f;
+    for (int j = 0; j < n_incl; ++j) s = fmaf(w[j], in[((size_t)l * n_incl + j) * ncell + c], s);
+    out[(size_t)l * ncell + c] = s;
+}
+
 __global__ void scales_kernel(int n, const unsigned int* smax_bits, float* scale) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) {
@@ -525,6 +618,13 @@ cudaError_t launch_pack(int LB, int n_lblk, const PackArgs& a, cudaStream_t s) {
     return cudaErrorInvalidValue;
 }
 
+cudaError_t launch_incl_reduce(const float* in, float* out, int n_lambda, int n_incl,
+                               const float* w, long long ncell, cudaStream_t s) {
+    dim3 grid((unsigned)((ncell + 255) / 256), (unsigned)n_lambda);
+    incl_reduce_kernel<<<grid, 256, 0, s>>>(in, out, n_lambda, n_incl, w, ncell);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_scales(int n_lblk, const unsigned int* smax_bits, float* scale, cudaStream_t s) {
     scales_kernel<<<(n_lblk + 127) / 128, 128, 0, s>>>(n_lblk, smax_bits, scale);
     return cudaGetLastError();
@@ -538,12 +638,15 @@ static cudaError_t level_t(bool level0, bool has_up, int n_lblk, const LevelArgs
     const long long per_cta = (long long)G * kWarpsPerCta;
     dim3 grid((unsigned)((items + per_cta - 1) / per_cta), (unsigned)n_lblk);
     dim3 block(kWarpsPerCta * 32);
+    const bool fix = a.bilinear_fix != 0;
     if (level0) {
-        if (has_up) level0_kernel<LB, VL, TS, true><<<grid, block, 0, s>>>(a);
-        else level0_kernel<LB, VL, TS, false><<<grid, block, 0, s>>>(a);
+        if (has_up && fix) level0_kernel<LB, VL, TS, true, true><<<grid, block, 0, s>>>(a);
+        else if (has_up) level0_kernel<LB, VL, TS, true, false><<<grid, block, 0, s>>>(a);
+        else level0_kernel<LB, VL, TS, false, false><<<grid, block, 0, s>>>(a);
     } else {
-        if (has_up) level_kernel<LB, VL, TS, true><<<grid, block, 0, s>>>(a);
-        else level_kernel<LB, VL, TS, false><<<grid, block, 0, s>>>(a);
+        if (has_up && fix) level_kernel<LB, VL, TS, true, true><<<grid, block, 0, s>>>(a);
+        else if (has_up) level_kernel<LB, VL, TS, true, false><<<grid, block, 0, s>>>(a);
+        else level_kernel<LB, VL, TS, false, false><<<grid, block, 0, s>>>(a);
     }
     return cudaGetLastError();
 }

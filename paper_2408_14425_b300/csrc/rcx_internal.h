@@ -39,6 +39,8 @@ struct LevelArgs {
     int Wshift;              // log2(W) if W is a power of two, else -1
     float spacing;           // probe spacing 2^i (voxels)
     float a, b;              // interval (b = +inf on the top cascade)
+    float a_up;              // start of the upper cascade's interval (bilinear fix)
+    int bilinear_fix;        // 1: trace to the upper probes' child starts (Sec. 2.5)
     const float2* dirs;      // W unit vectors (cos, sin)
     long long rays;          // Px * Pz * W
     // upper cascade (merged), NULL on the top cascade
@@ -61,7 +63,9 @@ struct LevelArgs {
 struct PackArgs {
     const float* chi;
     const float* eta;
-    int n_lambda;
+    int n_lambda;            // physical wavelengths
+    int n_incl;              // inclinations per wavelength (virtual wavelength l n_incl + j)
+    const float* incl_r;     // 1/sqrt(1 - mu_j^2) per inclination (NULL when n_incl == 1)
     long long ncell;
     float voxel;
     float2* out;
@@ -86,6 +90,10 @@ struct BatchPackArgs {
     int n_seg;
     long long total;
 };
+
+// Weighted sum over inclinations: out[l][c] = sum_j w_j in[l n_incl + j][c].
+cudaError_t launch_incl_reduce(const float* in, float* out, int n_lambda, int n_incl,
+                               const float* w, long long ncell, cudaStream_t s);
 
 // Launchers (rcx_fs_kernels.cu).  Return the CUDA launch error.
 // With occ != NULL the batched launcher only reports the kernel's resident CTAs per SM.
@@ -124,6 +132,10 @@ struct rc_plan_s {
     rc_options opt{};
     int LB = 4;                      // wavelengths per lane group (one ray)
     int VL = 1;                      // wavelengths per lane
+    int n_incl = 1;                  // inclination quadrature (2D invariance)
+    float* d_incl = nullptr;         // [r_j (n_incl)][w_j (n_incl)]
+    float* d_vout = nullptr;         // per-inclination cascade-0 outputs before the reduction
+    size_t vout_floats = 0;
     std::vector<rcx::LevelGeom> lv;
     std::vector<size_t> dir_off;     // offset of each cascade's table in d_dirs
     float2* d_dirs = nullptr;

@@ -132,7 +132,7 @@ mlp_tile_kernel(const float* __restrict__ wbf, const float* __restrict__ norm,
             S.dy[i] = 0.0f;
         }
     }
-    if (!TRAIN) return;
+    if constexpr (TRAIN) {
     // loss: block sum, one atomic
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) lsum += __shfl_xor_sync(0xffffffffu, lsum, o);
@@ -230,6 +230,7 @@ mlp_tile_kernel(const float* __restrict__ wbf, const float* __restrict__ norm,
             atomicAdd(grad + OFF_B1 + o, g);
         }
     }
+    }  // TRAIN
 }
 
 // Adam (Kingma & Ba 2015) on the FP32 master weights; also refreshes the bf16-rounded copy.

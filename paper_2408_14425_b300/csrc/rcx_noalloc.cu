@@ -135,7 +135,8 @@ extern "C" rc_status rc_formal_solve_noalloc(const rc_grid* grid, int n_cascades
         if ((e = cudaGetLastError()) != cudaSuccess)
             return nfail(RC_ERR_CUDA, std::string("rc_formal_solve_noalloc: ") + cudaGetErrorString(e));
     }
-    rcx::PackArgs pa{chi, eta, n_lambda, ncell, (float)grid->voxel_size, packed, nullptr};
+    rcx::PackArgs pa{chi, eta, n_lambda, 1, nullptr, ncell, (float)grid->voxel_size, packed,
+                     nullptr};
     if ((e = rcx::launch_pack(LB, n_lblk, pa, s)) != cudaSuccess)
         return nfail(RC_ERR_CUDA, std::string("rc_formal_solve_noalloc: ") + cudaGetErrorString(e));
     for (int i = n_cascades - 1; i >= 0; --i) {

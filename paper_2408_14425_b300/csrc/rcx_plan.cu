@@ -54,6 +54,58 @@ int ilog2(long long v) {
 
 size_t storage_bytes(int precision) { return precision == RC_STORE_F32 ? 4 : 2; }
 
+// Legendre P_n and P_{n-1} at x by the three-term recurrence.
+void legendre(int n, double x, double* pn, double* pn1) {
+    double p0 = 1.0, p1 = x;
+    if (n == 0) {
+        *pn = 1.0;
+        *pn1 = 0.0;
+        return;
+    }
+    for (int k = 1; k < n; ++k) {
+        const double p2 = ((2.0 * k + 1.0) * x * p1 - k * p0) / (k + 1.0);
+        p0 = p1;
+        p1 = p2;
+    }
+    *pn = p1;
+    *pn1 = p0;
+}
+
+// n-point Gauss-Radau rule on [0, 1] in mu = cos(angle to the invariant axis) with the fixed
+// node at mu = 0 (the in-plane ray), from the rule on [-1, 1] with fixed node -1: the free
+// nodes are the roots of (P_{n-1} + P_n)/(1 + x), found by Newton's method from the
+// Chebyshev-Gauss-Radau points; weights 2/n^2 at -1 and (1 - x)/(n P_{n-1}(x))^2.
+void gauss_radau(int n, std::vector<double>& mu, std::vector<double>& w) {
+    mu.assign(n, 0.0);
+    w.assign(n, 0.0);
+    if (n == 1) {
+        w[0] = 1.0;
+        return;
+    }
+    w[0] = 1.0 / ((double)n * n);                   // (2/n^2) / 2
+    for (int k = 1; k < n; ++k) {
+        double x = -std::cos(2.0 * M_PI * k / (2.0 * n - 1.0));
+        for (int it = 0; it < 100; ++it) {
+            double pn, pn1, qn, qn1;
+            legendre(n, x, &pn, &pn1);
+            const double f = pn + pn1;
+            // derivatives: P'_m = m (x P_m - P_{m-1}) / (x^2 - 1)
+            legendre(n - 1, x, &qn, &qn1);          // qn = P_{n-1}, qn1 = P_{n-2}
+            const double dpn = n * (x * pn - pn1) / (x * x - 1.0);
+            const double dpn1 = (n - 1) * (x * qn - qn1) / (x * x - 1.0);
+            const double g = f / (1.0 + x);
+            const double dg = ((dpn + dpn1) * (1.0 + x) - f) / ((1.0 + x) * (1.0 + x));
+            const double dx = g / dg;
+            x -= dx;
+            if (std::fabs(dx) < 1e-15) break;
+        }
+        double pn, pn1;
+        legendre(n, x, &pn, &pn1);
+        mu[k] = 0.5 * (1.0 + x);
+        w[k] = 0.5 * (1.0 - x) / ((double)n * n * pn1 * pn1);
+    }
+}
+
 void free_scratch(rc_plan_s* p) {
     cudaFree(p->d_packed);
     cudaFree(p->d_R[0]);
@@ -71,6 +123,7 @@ void free_scratch(rc_plan_s* p) {
 
 // Grows the solve scratch to hold n_lambda wavelengths.
 rc_status ensure_scratch(rc_plan_s* p, int n_lambda) {
+    n_lambda *= p->n_incl;                           // virtual wavelengths
     if (n_lambda <= p->cap_lambda) return RC_OK;
     const int LB = p->LB;
     const size_t n_lblk = (size_t)((n_lambda + LB - 1) / LB);
@@ -105,17 +158,46 @@ rc_status solve_device(rc_plan_s* p, const float* chi, const float* eta, int n_l
                        float* J, float* alo, cudaStream_t s, float* J_eff = nullptr,
                        float* alo_c = nullptr) {
     if (n_lambda == 0) return RC_OK;
-    if ((n_lambda + p->LB - 1) / p->LB > 65535)
+    const int n_phys = n_lambda;
+    const int NI = p->n_incl;
+    if ((long long)n_phys * NI > (1 << 30) || ((long long)n_phys * NI + p->LB - 1) / p->LB > 65535)
         return fail(RC_ERR_ARG, "rc_formal_solve: too many wavelengths for one call (65535 blocks)");
-    rc_status st = ensure_scratch(p, n_lambda);
+    rc_status st = ensure_scratch(p, n_phys);
     if (st != RC_OK) return st;
+    n_lambda = n_phys * NI;                          // virtual wavelengths from here on
+    const long long ncell_ = (long long)p->nx * p->nz;
+    float* Jv = J;
+    float* alov = alo;
+    float* Jeffv = J_eff;
+    float* alocv = alo_c;
+    if (NI > 1) {
+        const size_t per = (size_t)n_lambda * ncell_;
+        const size_t need = per * (1 + (alo ? 1 : 0) + (J_eff ? 1 : 0) + (alo_c ? 1 : 0));
+        if (p->vout_floats < need) {
+            cudaDeviceSynchronize();
+            cudaFree(p->d_vout);
+            p->d_vout = nullptr;
+            p->vout_floats = 0;
+            if (cudaMalloc(&p->d_vout, need * sizeof(float)) != cudaSuccess) {
+                cudaGetLastError();
+                return fail(RC_ERR_OOM, "rc_formal_solve: inclination scratch allocation failed");
+            }
+            p->vout_floats = need;
+        }
+        float* q = p->d_vout;
+        Jv = q;
+        q += per;
+        if (alo) { alov = q; q += per; }
+        if (J_eff) { Jeffv = q; q += per; }
+        if (alo_c) { alocv = q; q += per; }
+    }
     const int LB = p->LB;
     const int n_lblk = (n_lambda + LB - 1) / LB;
     const long long ncell = (long long)p->nx * p->nz;
     const bool f16 = p->opt.precision != RC_STORE_F32;
     int launches = 0;
     cudaError_t e;
-    const bool timing = p->timing && p->ev.size() >= (size_t)(p->C + 3);
+    const bool timing = p->timing && p->ev.size() >= (size_t)(p->C + 7);
     if (timing) {
         p->launch_names.clear();
         cudaEventRecord(p->ev[0], s);
@@ -131,8 +213,8 @@ rc_status solve_device(rc_plan_s* p, const float* chi, const float* eta, int n_l
         if ((e = cudaMemsetAsync(p->d_smax, 0, n_lblk * sizeof(unsigned), s)) != cudaSuccess)
             return cuda_fail(e, "memset");
     }
-    rcx::PackArgs pa{chi, eta, n_lambda, ncell, (float)p->voxel, p->d_packed,
-                     f16 ? p->d_smax : nullptr};
+    rcx::PackArgs pa{chi, eta, n_phys, NI, NI > 1 ? p->d_incl : nullptr, ncell,
+                     (float)p->voxel, p->d_packed, f16 ? p->d_smax : nullptr};
     if ((e = rcx::launch_pack(LB, n_lblk, pa, s)) != cudaSuccess) return cuda_fail(e, "pack launch");
     ++launches;
     mark("pack");
@@ -145,13 +227,25 @@ rc_status solve_device(rc_plan_s* p, const float* chi, const float* eta, int n_l
 
     const int C = p->C;
     for (int i = C - 1; i >= 0; --i) {
-        const rcx::LevelArgs a = rcx::level_args(p, i, n_lambda, J, alo, J_eff, alo_c);
+        const rcx::LevelArgs a = rcx::level_args(p, i, n_lambda, Jv, alov, Jeffv, alocv);
         const bool has_up = i < C - 1;
         if ((e = rcx::launch_level(LB, p->VL, p->opt.precision, i == 0, has_up, n_lblk, a, s)) !=
             cudaSuccess)
             return cuda_fail(e, "cascade launch");
         ++launches;
         mark("cascade " + std::to_string(i));
+    }
+    if (NI > 1) {
+        const float* w = p->d_incl + NI;
+        float* outs[4] = {J, alo, J_eff, alo_c};
+        const float* ins[4] = {Jv, alov, Jeffv, alocv};
+        for (int o = 0; o < 4; ++o) {
+            if (!outs[o]) continue;
+            if ((e = rcx::launch_incl_reduce(ins[o], outs[o], n_phys, NI, w, ncell_, s)) != cudaSuccess)
+                return cuda_fail(e, "inclination reduction launch");
+            ++launches;
+            mark("inclinations");
+        }
     }
     p->last_launches = launches;
     p->timed_launches = timing ? launches : 0;
@@ -178,8 +272,10 @@ rcx::LevelArgs rcx::level_args(const rc_plan_s* p, int i, int n_lambda, float* J
     a.b = std::isinf(g.b) ? INFINITY : (float)g.b;
     a.dirs = p->d_dirs + p->dir_off[i];
     a.rays = g.rays();
+    a.bilinear_fix = p->opt.bilinear_fix;
     if (i < p->C - 1) {
         const rcx::LevelGeom& u = p->lv[i + 1];
+        a.a_up = (float)u.a;
         a.R_up = p->d_R[(i + 1) & 1];
         a.Px_up = u.Px;
         a.Pz_up = u.Pz;
@@ -209,7 +305,7 @@ rc_status rcx::plan_set_layout(rc_plan_s* p, int LB, int VL) {
         free_scratch(p);
         p->LB = LB;
         p->VL = VL;
-        return cap > 0 ? ensure_scratch(p, cap) : RC_OK;
+        return cap > 0 ? ensure_scratch(p, (cap + p->n_incl - 1) / p->n_incl) : RC_OK;
     }
     p->VL = VL;
     return RC_OK;
@@ -267,9 +363,9 @@ rc_status rc_plan(const rc_grid* grid, int n_cascades, int dirs0, int branching,
         return fail(RC_ERR_ARG, "rc_plan: precision must be RC_STORE_F32, _F16 or _BF16");
     if (o.interval_rule != 0 && o.interval_rule != 1)
         return fail(RC_ERR_ARG, "rc_plan: interval_rule must be 0 or 1");
-    if (o.n_incl != 1) return fail(RC_ERR_UNSUPPORTED, "rc_plan: n_incl != 1 is not implemented");
-    if (o.bilinear_fix != 0)
-        return fail(RC_ERR_UNSUPPORTED, "rc_plan: the bilinear fix is not implemented");
+    if (o.n_incl < 1 || o.n_incl > 16) return fail(RC_ERR_ARG, "rc_plan: n_incl must be in [1, 16]");
+    if (o.bilinear_fix != 0 && o.bilinear_fix != 1)
+        return fail(RC_ERR_ARG, "rc_plan: bilinear_fix must be 0 or 1");
     int LB = o.lambda_block == 0 ? kDefaultLambdaBlock : o.lambda_block;
     if (LB != 1 && LB != 2 && LB != 4 && LB != 8 && LB != 16 && LB != 32)
         return fail(RC_ERR_ARG, "rc_plan: lambda_block must be 0, 1, 2, 4, 8, 16 or 32");
@@ -298,6 +394,7 @@ rc_status rc_plan(const rc_grid* grid, int n_cascades, int dirs0, int branching,
     p->opt = o;
     p->LB = LB;
     p->VL = VL;
+    p->n_incl = o.n_incl;
 
     // geometry (Sec. 2.3, Eq. 12-13), FP64 on the host
     const double g = std::pow(2.0, 0.5 * branching);
@@ -333,6 +430,18 @@ rc_status rc_plan(const rc_grid* grid, int n_cascades, int dirs0, int branching,
     cudaError_t e = cudaMalloc(&p->d_dirs, dirs.size() * sizeof(float2));
     if (e == cudaSuccess)
         e = cudaMemcpy(p->d_dirs, dirs.data(), dirs.size() * sizeof(float2), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && p->n_incl > 1) {
+        std::vector<double> mu, w;
+        gauss_radau(p->n_incl, mu, w);
+        std::vector<float> t(2 * p->n_incl);
+        for (int j = 0; j < p->n_incl; ++j) {
+            t[j] = (float)(1.0 / std::sqrt(1.0 - mu[j] * mu[j]));
+            t[p->n_incl + j] = (float)w[j];
+        }
+        e = cudaMalloc(&p->d_incl, t.size() * sizeof(float));
+        if (e == cudaSuccess)
+            e = cudaMemcpy(p->d_incl, t.data(), t.size() * sizeof(float), cudaMemcpyHostToDevice);
+    }
     if (e != cudaSuccess) {
         cudaFree(p->d_dirs);
         delete p;
@@ -350,6 +459,8 @@ void rc_plan_destroy(rc_plan_t p) {
     cudaDeviceSynchronize();
     free_scratch(p);
     cudaFree(p->d_dirs);
+    cudaFree(p->d_incl);
+    cudaFree(p->d_vout);
     cudaFree(p->d_stage);
     for (auto& s : p->s_io)
         if (s) cudaStreamDestroy(s);
@@ -464,7 +575,7 @@ rc_status rc_plan_set_timing(rc_plan_t p, int enable) {
     g_last_error.clear();
     if (!p) return fail(RC_ERR_ARG, "rc_plan_set_timing: plan is NULL");
     DeviceGuard dg(p->device);
-    const size_t need = (size_t)p->C + 3;  // pack, scale, C cascades, plus the start event
+    const size_t need = (size_t)p->C + 7;  // pack, scale, C cascades, 4 reductions, start
     while (enable && p->ev.size() < need) {
         cudaEvent_t e;
         cudaError_t err = cudaEventCreate(&e);
@@ -502,6 +613,9 @@ rc_status rc_formal_solve(rc_plan_t p, const float* chi, const float* eta, int n
                           float* alo, void* stream) {
     g_last_error.clear();
     if (!p) return fail(RC_ERR_ARG, "rc_formal_solve: plan is NULL");
+    if (alo && p->opt.bilinear_fix)
+        return fail(RC_ERR_UNSUPPORTED, "rc_formal_solve: the diagonal operator is defined for "
+                                        "the basic construction, not with the bilinear fix");
     if (n_lambda < 0) return fail(RC_ERR_ARG, "rc_formal_solve: n_lambda < 0");
     if (n_lambda > 0 && (!chi || !eta || !J))
         return fail(RC_ERR_ARG, "rc_formal_solve: chi, eta and J must be non-NULL");
@@ -516,6 +630,9 @@ rc_status rc_formal_solve_mali(rc_plan_t p, const float* chi, const float* eta, 
                                float* J, float* alo, float* J_eff, float* alo_c, void* stream) {
     g_last_error.clear();
     if (!p) return fail(RC_ERR_ARG, "rc_formal_solve_mali: plan is NULL");
+    if (p->opt.bilinear_fix)
+        return fail(RC_ERR_UNSUPPORTED, "rc_formal_solve_mali: the MALI outputs are defined "
+                                        "for the basic construction, not with the bilinear fix");
     if (n_lambda < 0) return fail(RC_ERR_ARG, "rc_formal_solve_mali: n_lambda < 0");
     if (n_lambda > 0 && (!chi || !eta || !J))
         return fail(RC_ERR_ARG, "rc_formal_solve_mali: chi, eta and J must be non-NULL");

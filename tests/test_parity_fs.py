@@ -164,3 +164,54 @@ def test_full_size_1024_sampled_wavelengths():
     for lam in (0, 45):
         J_ref = _oracle(chi[lam:lam + 1], eta[lam:lam + 1], 8)
         _assert_close(J[lam:lam + 1], J_ref, 1e-3, f"1024^2 lambda {lam}")
+
+
+@pytest.mark.parametrize("nx,nz,nl,C", [(96, 80, 5, 5), (64, 64, 3, 5)])
+def test_bilinear_fix_matches_oracle(nx, nz, nl, C):
+    """Sec. 2.5's bilinear fix (four traced segments per ray below the top cascade)."""
+    chi, eta = W.grf_fields(nx, nl, nz=nz)
+    J = _solve(chi, eta, C, bilinear_fix=True)
+    _assert_close(J, _oracle(chi, eta, C, bilinear_fix=True), 1e-3, f"fix {nx}x{nz}")
+
+
+def test_bilinear_fix_circle_test():
+    chi, eta = W.opaque_disc_field(128, 10.0, chi_disc=100.0)
+    chi = chi[None].astype(np.float32)
+    eta = eta[None].astype(np.float32)
+    J = _solve(chi, eta, 6, bilinear_fix=True)
+    _assert_close(J, _oracle(chi, eta, 6, bilinear_fix=True), 1e-3, "fix circle")
+
+
+def test_bilinear_fix_rejects_the_operator_outputs():
+    rcx = _rcx()
+    p = rcx.Plan(16, 16, 3, bilinear_fix=True)
+    x = torch.ones((1, 16, 16), device="cuda")
+    with pytest.raises(rcx.RcError):
+        p.formal_solve(x, x, want_alo=True)
+    with pytest.raises(rcx.RcError):
+        p.formal_solve_mali(x, x)
+
+
+@pytest.mark.parametrize("n_incl,C", [(8, 5), (3, 4)])
+def test_inclinations_match_oracle(n_incl, C):
+    """2D invariance (Sec. 3.1): Gauss-Radau inclinations, J and the diagonal operator."""
+    chi, eta = W.grf_fields(80, 6, nz=72)
+    J, alo = _solve(chi, eta, C, want_alo=True, n_incl=n_incl)
+    J_ref, alo_ref = oracle.rc_solve_inclined(chi.astype(np.float64), eta.astype(np.float64), C,
+                                              n_incl, want_alo=True)
+    _assert_close(J, J_ref, 1e-3, f"J n_incl={n_incl}")
+    _assert_close(alo, alo_ref, 1e-5, f"alo n_incl={n_incl}")
+
+
+def test_inclinations_host_entry_and_mali():
+    rcx = _rcx()
+    chi, eta = W.grf_fields(48, 5)
+    p = rcx.Plan(48, 48, 5, n_incl=4)
+    J_host = p.formal_solve_host(chi, eta)
+    dchi, deta = torch.from_numpy(chi).cuda(), torch.from_numpy(eta).cuda()
+    np.testing.assert_array_equal(J_host, p.formal_solve(dchi, deta).cpu().numpy())
+    J, J_eff, alo_c = p.formal_solve_mali(dchi, deta)
+    J_ref, alo_ref = oracle.rc_solve_inclined(chi.astype(np.float64), eta.astype(np.float64), 5, 4,
+                                              want_alo=True)
+    _assert_close(J.cpu().numpy(), J_ref, 1e-3, "mali J")
+    _assert_close(alo_c.cpu().numpy(), 1.0 - alo_ref, 1e-3, "mali 1-alo")

@@ -73,6 +73,10 @@ def lib():
                                        ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                        ctypes.c_double, ctypes.c_int, ctypes.c_int, _dp, _dp, _llp]
         L.rco_rc_solve_fix.restype = ctypes.c_int
+        L.rco_rc_solve_sparse.argtypes = [_dp, _dp, ctypes.c_char_p, ctypes.c_int, ctypes.c_int,
+                                          ctypes.c_double, ctypes.c_int, ctypes.c_int,
+                                          ctypes.c_int, ctypes.c_double, ctypes.c_int, _dp, _llp]
+        L.rco_rc_solve_sparse.restype = ctypes.c_int
         L.rco_count_crossings.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                           ctypes.c_int, ctypes.c_double, ctypes.c_int, _llp]
         L.rco_count_crossings.restype = ctypes.c_longlong
@@ -234,6 +238,23 @@ def rc_solve_inclined(chi, eta, n_cascades: int, n_incl: int, want_alo: bool = F
         if want_alo:
             alo = alo + wj * aj
     return J, alo
+
+
+def rc_solve_sparse(chi, eta, active, n_cascades: int, dirs0: int = 4, branching: int = 4,
+                    interval0: float = 1.0, rule: int = 0, voxel: float = 1.0):
+    """Sparse RC of one slab (Sec. 3.5): returns (J, intervals computed per cascade)."""
+    chi = _f64(chi)
+    eta = _f64(eta)
+    nz, nx = chi.shape
+    act = np.ascontiguousarray(np.asarray(active, dtype=np.uint8))
+    J = np.zeros_like(chi)
+    rays = np.zeros(n_cascades, dtype=np.int64)
+    rc = lib().rco_rc_solve_sparse(_ptr(chi), _ptr(eta), act.tobytes(), nx, nz, voxel, n_cascades,
+                                   dirs0, branching, interval0, rule, _ptr(J),
+                                   rays.ctypes.data_as(_llp))
+    if rc != 0:
+        raise ValueError("rco_rc_solve_sparse rejected its arguments")
+    return J, rays
 
 
 def count_crossings(nx: int, nz: int, n_cascades: int, dirs0: int = 4, branching: int = 4,

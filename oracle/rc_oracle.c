@@ -410,6 +410,122 @@ int rco_rc_solve_fix(const double* chi, const double* eta, int nx, int nz,
     return 0;
 }
 
+/*
+ * Sparse RC (Sec. 3.5): only the cells with active[c] != 0 take part.  Inactive cells are
+ * transparent with no emission (chi = eta = 0); the cascade-0 probes of active cells are
+ * flagged, and every flagged probe flags the (up to four) cascade-(i+1) probes its bilinear
+ * lookup brackets, up to the top cascade.  Only flagged probes' intervals are computed
+ * (the others are filled with NaN, so a read of one would show); J of inactive cells is 0.
+ * rays_per_level (nullable) receives the number of intervals computed per cascade.
+ */
+int rco_rc_solve_sparse(const double* chi, const double* eta, const unsigned char* active,
+                        int nx, int nz, double voxel, int n_cascades, int dirs0, int branching,
+                        double interval0, int rule, double* J, long long* rays_per_level)
+{
+    if (nx <= 0 || nz <= 0 || n_cascades < 1 || dirs0 < 1 || branching < 1 || !active)
+        return -1;
+    const size_t ncell = (size_t)nx * nz;
+    double* mc = (double*)malloc(sizeof(double) * ncell);
+    double* me = (double*)malloc(sizeof(double) * ncell);
+    for (size_t c = 0; c < ncell; ++c) {
+        mc[c] = active[c] ? chi[c] : 0.0;
+        me[c] = active[c] ? eta[c] : 0.0;
+    }
+    /* flags, bottom up */
+    unsigned char** F = (unsigned char**)calloc((size_t)n_cascades, sizeof(unsigned char*));
+    for (int i = 0; i < n_cascades; ++i)
+        F[i] = (unsigned char*)calloc((size_t)rco_probes(nx, i) * rco_probes(nz, i), 1);
+    for (size_t c = 0; c < ncell; ++c) F[0][c] = active[c] ? 1 : 0;
+    for (int i = 0; i + 1 < n_cascades; ++i) {
+        const int Px = rco_probes(nx, i), Pz = rco_probes(nz, i);
+        const int Pxu = rco_probes(nx, i + 1), Pzu = rco_probes(nz, i + 1);
+        for (int pz = 0; pz < Pz; ++pz)
+            for (int px = 0; px < Px; ++px) {
+                if (!F[i][(size_t)pz * Px + px]) continue;
+                int jx0, jx1, jz0, jz1;
+                double fx, fz;
+                upper_weights(px, i, Pxu, &jx0, &jx1, &fx);
+                upper_weights(pz, i, Pzu, &jz0, &jz1, &fz);
+                F[i + 1][(size_t)jz0 * Pxu + jx0] = 1;
+                F[i + 1][(size_t)jz0 * Pxu + jx1] = 1;
+                F[i + 1][(size_t)jz1 * Pxu + jx0] = 1;
+                F[i + 1][(size_t)jz1 * Pxu + jx1] = 1;
+            }
+    }
+    /* top down, flagged probes only */
+    double* R_up = NULL;
+    int Px_up = 0, Pz_up = 0;
+    long long W_up = 0;
+    for (int i = n_cascades - 1; i >= 0; --i) {
+        const int Px = rco_probes(nx, i), Pz = rco_probes(nz, i);
+        const long long W = rco_dirs(dirs0, branching, i);
+        double a, b;
+        rco_interval(rule, interval0, branching, i, n_cascades, &a, &b);
+        const double spacing = (double)(1 << i);
+        double* R = (double*)malloc(sizeof(double) * (size_t)Px * Pz * W);
+        long long rays = 0;
+#pragma omp parallel for collapse(2) schedule(dynamic, 1) reduction(+ : rays)
+        for (int pz = 0; pz < Pz; ++pz)
+            for (int px = 0; px < Px; ++px) {
+                double* Rp = R + ((size_t)pz * Px + px) * (size_t)W;
+                if (!F[i][(size_t)pz * Px + px]) {
+                    for (long long k = 0; k < W; ++k) Rp[k] = NAN;
+                    continue;
+                }
+                const double ox = (px + 0.5) * spacing, oz = (pz + 0.5) * spacing;
+                int jx0 = 0, jx1 = 0, jz0 = 0, jz1 = 0;
+                double fx = 0.0, fz = 0.0;
+                if (R_up) {
+                    upper_weights(px, i, Px_up, &jx0, &jx1, &fx);
+                    upper_weights(pz, i, Pz_up, &jz0, &jz1, &fz);
+                }
+                for (long long k = 0; k < W; ++k) {
+                    double wx, wz, I, tau;
+                    rco_direction(k, W, &wx, &wz);
+                    rco_march(mc, me, nx, nz, voxel, ox, oz, wx, wz, a, b, &I, &tau);
+                    ++rays;
+                    double Rm = I;
+                    if (R_up) {
+                        int jz[2] = {jz0, jz1}, jx[2] = {jx0, jx1};
+                        double wzz[2] = {1.0 - fz, fz}, wxx[2] = {1.0 - fx, fx};
+                        double upper = 0.0;
+                        for (int q = 0; q < 2; ++q)
+                            for (int r = 0; r < 2; ++r) {
+                                const double* Ru = R_up + ((size_t)jz[q] * Px_up + jx[r]) * (size_t)W_up;
+                                double avg = 0.0;
+                                for (int c = 0; c < branching; ++c) avg += Ru[(size_t)(k * branching + c)];
+                                upper += wzz[q] * wxx[r] * avg / (double)branching;
+                            }
+                        double Im, tm;
+                        rco_merge(I, tau, upper, 0.0, &Im, &tm);
+                        Rm = Im;
+                    }
+                    Rp[k] = Rm;
+                }
+            }
+        if (rays_per_level) rays_per_level[i] = rays;
+        free(R_up);
+        R_up = R;
+        Px_up = Px;
+        Pz_up = Pz;
+        W_up = W;
+    }
+    for (int iz = 0; iz < nz; ++iz)
+        for (int ix = 0; ix < nx; ++ix) {
+            const size_t c = (size_t)iz * nx + ix;
+            double s = 0.0;
+            if (active[c])
+                for (long long k = 0; k < W_up; ++k) s += R_up[c * (size_t)W_up + (size_t)k];
+            J[c] = active[c] ? s / (double)W_up : 0.0;
+        }
+    free(R_up);
+    for (int i = 0; i < n_cascades; ++i) free(F[i]);
+    free(F);
+    free(mc);
+    free(me);
+    return 0;
+}
+
 /* Voxel crossings of every cascade of a plan (geometry only). */
 long long rco_count_crossings(int nx, int nz, int n_cascades, int dirs0,
                               int branching, double interval0, int rule,

@@ -403,3 +403,24 @@ def test_inclinations_thick_and_thin_limits():
     J_inc, _ = oracle.rc_solve_inclined(chi_t, eta_t, 4, 8)
     mu, w = oracle.gauss_radau_inclinations(8)
     np.testing.assert_allclose(J_inc, J_flat * np.sum(w / np.sqrt(1 - mu ** 2)), rtol=1e-7)
+
+
+def test_sparse_equals_dense_on_the_masked_field():
+    """Sec. 3.5: with inactive cells transparent and only flagged probes computed, every
+    active cell's J equals the dense solution of the masked field (flagged parents carry
+    every dependency), inactive cells get 0, and the work falls with the active fraction."""
+    rng = np.random.default_rng(12)
+    n = 64
+    chi, eta = _random_field(n, 21, chi_hi=1.0)
+    T = 10 ** rng.uniform(3.5, 6.5, (n, n))
+    x = np.arange(n) + 0.5
+    active = (np.abs(x[None, :] - 20) < 6) | (np.hypot(x[None, :] - 45, x[:, None] - 40) < 7)
+    J_s, rays = oracle.rc_solve_sparse(chi, eta, active, 5)
+    J_d, _, _ = oracle.rc_solve(np.where(active, chi, 0.0), np.where(active, eta, 0.0), 5)
+    assert np.all(np.isfinite(J_s))
+    np.testing.assert_allclose(J_s[active], J_d[active], rtol=1e-14)
+    assert np.all(J_s[~active] == 0.0)
+    dense_rays = np.array([oracle.probes(n, i) ** 2 * oracle.dirs(4, 4, i) for i in range(5)])
+    assert rays[0] == active.sum() * 4
+    assert np.all(rays <= dense_rays) and rays.sum() < 0.8 * dense_rays.sum()
+    del T

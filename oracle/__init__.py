@@ -77,6 +77,10 @@ def lib():
                                           ctypes.c_double, ctypes.c_int, ctypes.c_int,
                                           ctypes.c_int, ctypes.c_double, ctypes.c_int, _dp, _llp]
         L.rco_rc_solve_sparse.restype = ctypes.c_int
+        L.rco_emergent.argtypes = [_dp, _dp, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                   ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                   ctypes.c_double, _dp]
+        L.rco_emergent.restype = ctypes.c_double
         L.rco_count_crossings.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                           ctypes.c_int, ctypes.c_double, ctypes.c_int, _llp]
         L.rco_count_crossings.restype = ctypes.c_longlong
@@ -255,6 +259,25 @@ def rc_solve_sparse(chi, eta, active, n_cascades: int, dirs0: int = 4, branching
     if rc != 0:
         raise ValueError("rco_rc_solve_sparse rejected its arguments")
     return J, rays
+
+
+def emergent(chi, eta, rays, voxel: float = 1.0, mu: float = 0.0, want_contrib: bool = False):
+    """Front-to-back long characteristics (Sec. 3.9): intensity reaching each ray origin from
+    along its direction, rays [n][4] = (ox, oz, wx, wz) in voxel units, for one slab.  mu is
+    the inclination to the invariant axis (path per projected length 1/sqrt(1 - mu^2)).
+    Returns I [n] and, with want_contrib, the contribution function summed per cell."""
+    r = 1.0 / np.sqrt(1.0 - mu * mu)
+    chi = _f64(chi) * r
+    eta = _f64(eta) * r
+    nz, nx = chi.shape
+    rays = np.asarray(rays, dtype=np.float64)
+    I = np.zeros(len(rays))
+    C = np.zeros_like(chi) if want_contrib else None
+    L = lib()
+    for i, (ox, oz, wx, wz) in enumerate(rays):
+        I[i] = L.rco_emergent(_ptr(chi), _ptr(eta), nx, nz, voxel, ox, oz, wx, wz,
+                              _ptr(C) if C is not None else None)
+    return (I, C) if want_contrib else I
 
 
 def count_crossings(nx: int, nz: int, n_cascades: int, dirs0: int = 4, branching: int = 4,

@@ -526,6 +526,46 @@ int rco_rc_solve_sparse(const double* chi, const double* eta, const unsigned cha
     return 0;
 }
 
+/*
+ * Emergent intensity along one ray, front to back (Sec. 3.9): the ray o + t w, t >= 0, is
+ * cut at the cell faces (as in rco_march) and the pieces are taken from the origin outward;
+ * each adds exp(-tau_before) S (1 - exp(-chi ds)) (or exp(-tau_before) eta ds where chi = 0),
+ * which is also its value of the contribution function.  contrib (nullable, [nz][nx]) receives
+ * the contributions per cell.  Returns the intensity reaching the origin.
+ */
+double rco_emergent(const double* chi, const double* eta, int nx, int nz, double voxel,
+                    double ox, double oz, double wx, double wz, double* contrib)
+{
+    double t0 = 0.0, t1 = INFINITY;
+    if (!clip_to_box(ox, oz, wx, wz, nx, nz, &t0, &t1)) return 0.0;
+    double I = 0.0, tau = 0.0, t = t0;
+    double tx = next_plane_t(ox, wx, t0), tz = next_plane_t(oz, wz, t0);
+    for (;;) {
+        double tn = tx < tz ? tx : tz;
+        if (tn > t1) tn = t1;
+        if (tn > t) {
+            const double tm = 0.5 * (t + tn);
+            int ix = (int)floor(ox + tm * wx), iz = (int)floor(oz + tm * wz);
+            if (ix < 0) ix = 0;
+            if (ix >= nx) ix = nx - 1;
+            if (iz < 0) iz = 0;
+            if (iz >= nz) iz = nz - 1;
+            const size_t c = (size_t)iz * nx + ix;
+            const double ds = (tn - t) * voxel, dtau = chi[c] * ds;
+            const double piece = chi[c] > 0.0 ? exp(-tau) * (eta[c] / chi[c]) * (-expm1(-dtau))
+                                              : exp(-tau) * eta[c] * ds;
+            I += piece;
+            if (contrib) contrib[c] += piece;
+            tau += dtau;
+        }
+        if (!(tn < t1)) break;
+        if (tx <= tn) tx = next_plane_t(ox, wx, tn);
+        if (tz <= tn) tz = next_plane_t(oz, wz, tn);
+        t = tn;
+    }
+    return I;
+}
+
 /* Voxel crossings of every cascade of a plan (geometry only). */
 long long rco_count_crossings(int nx, int nz, int n_cascades, int dirs0,
                               int branching, double interval0, int rule,

@@ -424,3 +424,29 @@ def test_sparse_equals_dense_on_the_masked_field():
     assert rays[0] == active.sum() * 4
     assert np.all(rays <= dense_rays) and rays.sum() < 0.8 * dense_rays.sum()
     del T
+
+
+def test_emergent_front_to_back_equals_back_to_front():
+    """Sec. 3.9: the single-pass front-to-back intensity equals the back-to-front march of
+    the same ray, and the contribution function sums to it."""
+    chi, eta = _random_field(24, 31)
+    rng = np.random.default_rng(31)
+    rays = []
+    for _ in range(12):
+        th = rng.uniform(0, 2 * np.pi)
+        rays.append((rng.uniform(-3, 27), rng.uniform(-3, 27), math.cos(th), math.sin(th)))
+    I, C = oracle.emergent(chi, eta, rays, want_contrib=True)
+    for (ox, oz, wx, wz), Ii in zip(rays, I):
+        assert Ii == pytest.approx(oracle.march(chi, eta, (ox, oz), (wx, wz), 0.0, math.inf)[0],
+                                   rel=1e-12, abs=1e-300)
+    assert C.sum() == pytest.approx(I.sum(), rel=1e-12)
+
+
+def test_emergent_uniform_slab_closed_form():
+    """Through a uniform slab of depth D at inclination mu: I = S (1 - exp(-chi D / sqrt(1 - mu^2)))."""
+    chi = np.full((8, 40), 0.3)
+    eta = 0.3 * 2.0 * np.ones_like(chi)
+    rays = [(x + 0.5, -1.0, 0.0, 1.0) for x in range(40)]
+    for mu in (0.0, 0.6):
+        I = oracle.emergent(chi, eta, rays, mu=mu)
+        np.testing.assert_allclose(I, 2.0 * -np.expm1(-0.3 * 8 / math.sqrt(1 - mu * mu)), rtol=1e-12)

@@ -401,6 +401,34 @@ def run_nlte(args):
     out["slab_512"] = {"iterations": r["iterations"], "seconds": round(r["seconds"], 3),
                        "converged": r["converged"], "cascades": 6,
                        "ms_per_iteration": round(1e3 * r["seconds"] / max(r["iterations"], 1), 2)}
+    # sparsity (Sec. 3.5): the same slab's formal solution restricted to T < 250 kK
+    chi, eta = atom.emis_opac(T, r["pops"])
+    shape = (atom.n_lambda, 512, 512)
+    chi, eta = chi.reshape(shape), eta.reshape(shape)
+    Jd = torch.empty(shape, dtype=torch.float32, device="cuda")
+
+    def timed(n=5):
+        plan.formal_solve(chi, eta, Jd)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(n):
+            plan.formal_solve(chi, eta, Jd)
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / n
+
+    ms_dense = timed()
+    active = (T < 2.5e5).to(torch.uint8)
+    plan.set_active(active)
+    ms_sparse = timed()
+    counts = plan.active_probes()
+    plan.set_active(None)
+    out["sparse_512"] = {"active_cells": round(float(active.float().mean()), 4),
+                         "flagged_probes_per_cascade": counts, "dense_ms": round(ms_dense, 3),
+                         "sparse_ms": round(ms_sparse, 3),
+                         "speedup": round(ms_dense / ms_sparse, 3), "threshold_K": 2.5e5}
+    del chi, eta, Jd
     del T, nH, plan, r
 
     t0 = time.perf_counter()
@@ -451,7 +479,7 @@ def run_nlte(args):
 def run_batched(args):
     """The uneven multi-domain workload: 16 domains (sides 256..2048, 32..128 wavelengths,
     seed 7, GRF recipe, 8 cascades) with 16-bit interval storage, one graph replay per step
-    (one persistent launch per cascade over all domains); compared with solving the domains
+    (one launch per cascade over all domains); compared with solving the domains
     one after another through rc_formal_solve."""
     import torch
 

@@ -187,6 +187,19 @@ rc_status rc_formal_solve_noalloc(const rc_grid* grid, int n_cascades, int dirs0
                                   const float* chi, const float* eta, int n_lambda, float* J,
                                   float* alo, void* stream);
 
+/*
+ * Sparsity (Sec. 3.5): restrict the plan to the cells with active[c] != 0 (device uint8
+ * [nz][nx]; NULL restores the dense plan).  Inactive cells are transparent with no emission;
+ * the cascade-0 probes of active cells are flagged, every flagged probe flags the upper probes
+ * its bilinear lookup brackets (up to the top cascade), and the cascade kernels run the flagged
+ * probes only (flags and the ascending probe lists are built on the device).  Solves then
+ * write J (alo, J_eff, alo_c) = 0 for inactive cells, and rc_nlte_solve keeps their
+ * populations.  Synchronous.  Not for batches.  Errors: RC_ERR_ARG, RC_ERR_OOM, RC_ERR_CUDA.
+ */
+rc_status rc_plan_set_active(rc_plan_t plan, const unsigned char* active, void* stream);
+/* Flagged probes per cascade (all probes for a dense plan); per_cascade has n_cascades entries. */
+rc_status rc_plan_active_probes(rc_plan_t plan, long long* per_cascade);
+
 /* Lane layout of a plan's march: wavelengths per ray (packed together per voxel) and per GPU
  * lane; see rc_options.  Changing lambda_block re-allocates the plan's scratch (synchronous).
  * Errors: RC_ERR_ARG, RC_ERR_OOM, RC_ERR_CUDA. */
@@ -207,12 +220,13 @@ rc_status rc_plan_autotune(rc_plan_t plan, const float* chi, const float* eta, i
  * Batched formal solutions (independent problems solved together, Sec. 3.6: wavelengths and
  * domains are independent).  A batch binds n plans (same n_cascades, storage precision and
  * device; every plan is switched to the first plan's lane layout) to fixed device buffers
- * chi[d], eta[d], J[d] ([n_lambda[d]][nz_d][nx_d]).  Each cascade is ONE persistent launch over
- * a work list of CTA-sized chunks of every (domain, wavelength block), sorted by estimated
- * cost (interval length a ray can march, longest first); packing is one launch for all
- * domains.  The whole sequence is captured once into a CUDA graph; rc_batch_run replays it on
- * `stream` (asynchronous).  With autotune != 0 creation times graph replays of the candidate
- * lane layouts (16/4, 8/4, 32/4, 8/2, 4/4) on the bound inputs and keeps the fastest.
+ * chi[d], eta[d], J[d] ([n_lambda[d]][nz_d][nx_d]).  Each cascade is ONE launch over a work
+ * list of CTA-sized chunks of every (domain, wavelength block), sorted by estimated cost
+ * (interval length a ray can march, longest first), one chunk per CTA; packing is one launch
+ * for all domains.  The whole sequence is captured once into a CUDA graph; rc_batch_run
+ * replays it on `stream` (asynchronous).  With autotune != 0 creation times graph replays of
+ * the candidate lane layouts (16/4, 8/4, 32/4, 8/2, 4/4) on the first wavelength block of
+ * every bound domain, ranks them by time per wavelength slice and keeps the fastest.
  * Scratch is reserved at creation, so runs allocate nothing.  The buffers must outlive the
  * batch; a batch must not run concurrently with another use of its plans.
  * Errors: RC_ERR_ARG (mismatched plans, NULL buffers), RC_ERR_OOM, RC_ERR_CUDA.
@@ -356,6 +370,13 @@ rc_status rc_mlp_get_params(rc_mlp_t net, float* theta, float* mean, float* std_
 rc_status rc_mlp_fit_normalization(rc_mlp_t net, const float* X, long long N, void* stream);
 /* Y [B][3] = network(X [B][6]); device buffers, asynchronous. */
 rc_status rc_mlp_forward(rc_mlp_t net, const float* X, long long B, float* Y, void* stream);
+/* Inference path of rc_mlp_forward (and so of rc_surrogate_seed): enable != 0 runs the 64 x 64
+ * layer on the tensor cores (tcgen05.mma, bf16 h1 and W2 from shared memory, FP32 accumulator in
+ * tensor memory, 128 samples per CTA); 0 (default) uses FP32 FMAs with the bf16 weights.
+ * rc_mlp_tensor_core_status reports RC_ERR_TIMEOUT if a tensor-core wait ever ran out (the
+ * kernel then skipped its outputs).  Training always uses the FMA path. */
+rc_status rc_mlp_use_tensor_cores(rc_mlp_t net, int enable);
+rc_status rc_mlp_tensor_core_status(rc_mlp_t net);
 /* Mean-squared-error loss over B samples and its gradient (device outputs, either may be NULL). */
 rc_status rc_mlp_loss_grad(rc_mlp_t net, const float* X, const float* Y_target, long long B,
                            float* grad, float* loss, void* stream);
@@ -377,6 +398,25 @@ rc_status rc_surrogate_targets(rc_atom_t atom, const double* T, const double* n_
 rc_status rc_surrogate_seed(rc_atom_t atom, rc_mlp_t net, const float* X, const double* T,
                             const double* n_atom, long long ncell, double* pops, int* n_fallback,
                             void* stream);
+
+/*
+ * rc_emergent -- emergent intensity by single-pass front-to-back long characteristics
+ * (Sec. 3.9): each ray starts at its origin and accumulates, outward along its direction,
+ * exp(-tau_before) S (1 - exp(-chi ds)) of every voxel piece it crosses to the domain edge --
+ * the intensity reaching the origin from that direction -- for every wavelength.
+ *   rays     device FP32 [n_rays][4], 16-byte aligned: origin (x, z) in voxels, unit
+ *            direction (wx, wz).  Origins may lie outside the domain.
+ *   mu       inclination to the invariant axis, 0 <= mu < 1: the path per projected length is
+ *            1/sqrt(1 - mu^2) (2D invariance, Sec. 3.1).
+ *   I        device FP32 [n_lambda][n_rays], written.
+ *   contrib  device FP32 [n_lambda][nz][nx] or NULL: each piece's contribution added to its
+ *            cell (the contribution function summed over the rays); the caller zeroes it.
+ * Uses the plan's grid, voxel size, packing scratch and (if set) active cells.  Asynchronous.
+ * Errors: RC_ERR_ARG, RC_ERR_OOM, RC_ERR_CUDA.
+ */
+rc_status rc_emergent(rc_plan_t plan, const float* chi, const float* eta, int n_lambda,
+                      const float* rays, long long n_rays, float mu, float* I, float* contrib,
+                      void* stream);
 
 /* One-line message for the calling thread's last error ("" if none). */
 const char* rc_last_error(void);

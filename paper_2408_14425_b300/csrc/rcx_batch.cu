@@ -1,8 +1,8 @@
 // rcx_batch.cu -- many independent formal solutions (domains of uneven sizes, each with
-// its own wavelength count) run as one persistent launch per cascade over a work list of
-// CTA-sized chunks, segments sorted by estimated cost, and the whole sequence captured
-// once in a CUDA graph.  An optional native autotuner picks the lane layout by timing
-// graph replays of the candidates.
+// its own wavelength count) run as one launch per cascade over a work list of CTA-sized
+// chunks, segments sorted by estimated cost, and the whole sequence captured once in a
+// CUDA graph.  An optional native autotuner picks the lane layout by timing graph replays
+// of the candidates on a sample of the batch (the first wavelength block of each domain).
 #include <algorithm>
 #include <cmath>
 #include <new>
@@ -63,7 +63,9 @@ void release(rc_batch_s* b) {
 }
 
 // Builds the device tables for the plans' current lane layout and captures the graph.
-rc_status build(rc_batch_s* b) {
+// With first_block_only the tables hold only the first lambda block of every domain (the
+// autotuner's sample of the workload).
+rc_status build(rc_batch_s* b, bool first_block_only = false) {
     release(b);
     const int n = b->n, C = b->C;
     rc_plan_s* p0 = b->plans[0];
@@ -91,7 +93,7 @@ rc_status build(rc_batch_s* b) {
             const long long chunks = (items + G_rays - 1) / G_rays;
             const double diag = std::sqrt((double)p->nx * p->nx + (double)p->nz * p->nz);
             const double len = std::min(p->lv[i].b - p->lv[i].a, diag) * (i == 0 ? p->W0 : 1);
-            const int n_lblk = (b->nl[d] + LB - 1) / LB;
+            const int n_lblk = first_block_only ? 1 : (b->nl[d] + LB - 1) / LB;
             for (int lb = 0; lb < n_lblk; ++lb) segs.push_back({len, d, lb, chunks});
         }
         std::stable_sort(segs.begin(), segs.end(), [](const Seg& x, const Seg& y) { return x.cost > y.cost; });
@@ -104,11 +106,11 @@ rc_status build(rc_batch_s* b) {
     }
     for (int d = 0; d < n; ++d) {
         rc_plan_s* p = b->plans[d];
-        pargs[d] = rcx::PackArgs{b->chi[d], b->eta[d], b->nl[d], 1, nullptr,
+        pargs[d] = rcx::PackArgs{b->chi[d], b->eta[d], b->nl[d], 1, nullptr, nullptr,
                                  (long long)p->nx * p->nz, (float)p->voxel, p->d_packed,
                                  p->opt.precision != RC_STORE_F32 ? p->d_smax : nullptr};
         const long long chunks = ((long long)p->nx * p->nz + 255) / 256;
-        const int n_lblk = (b->nl[d] + LB - 1) / LB;
+        const int n_lblk = first_block_only ? 1 : (b->nl[d] + LB - 1) / LB;
         for (int lb = 0; lb < n_lblk; ++lb) {
             T[C].prefix.push_back(T[C].total);
             T[C].dom.push_back(d);
@@ -144,7 +146,7 @@ rc_status build(rc_batch_s* b) {
     if ((e = cudaMemcpy(b->d_tables, host.data(), bytes, cudaMemcpyHostToDevice)) != cudaSuccess)
         return bcuda(e, "rc_batch: table upload");
 
-    // persistent grids: resident CTAs of the whole GPU (or fewer if there is less work)
+    // cascade launches: one CTA per chunk, handed out in index order by the hardware
     int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device);
     b->grid.assign(C, 0);
@@ -153,7 +155,9 @@ rc_status build(rc_batch_s* b) {
         rcx::launch_batched_level(LB, b->VL, b->precision, i == 0, i < C - 1, b->level[i], 0,
                                   nullptr, &occ);
         if (occ < 1) return bfail(RC_ERR_UNSUPPORTED, "rc_batch: lane layout has no batched kernel");
-        b->grid[i] = (int)std::min<long long>(b->level[i].total, (long long)sms * occ);
+        if (b->level[i].total > 0x7FFFFFFFLL)
+            return bfail(RC_ERR_ARG, "rc_batch: more than 2^31 - 1 chunks in one cascade");
+        b->grid[i] = (int)b->level[i].total;
     }
     b->pack_grid = (int)std::min<long long>(b->pack.total, (long long)sms * 8);
 
@@ -205,6 +209,9 @@ rc_status rc_batch_create(int n, const rc_plan_t* plans, const float* const* chi
         if (!plans[d] || !chi[d] || !eta[d] || !J[d] || n_lambda[d] < 1)
             return bfail(RC_ERR_ARG, "rc_batch_create: NULL plan/buffer or n_lambda < 1 in domain " +
                                          std::to_string(d));
+        if (plans[d]->sparse)
+            return bfail(RC_ERR_UNSUPPORTED, "rc_batch_create: sparse plans are served by "
+                                             "rc_formal_solve only");
         if (plans[d]->n_incl != 1)
             return bfail(RC_ERR_UNSUPPORTED, "rc_batch_create: inclinations are served by "
                                              "rc_formal_solve only");
@@ -246,10 +253,14 @@ rc_status rc_batch_create(int n, const rc_plan_t* plans, const float* const* chi
         cudaEvent_t e0, e1;
         cudaEventCreate(&e0);
         cudaEventCreate(&e1);
+        // each candidate is timed on the first lambda block of every domain and ranked by
+        // time per wavelength slice
         for (const auto& c : cand) {
             for (int d = 0; d < n && st == RC_OK; ++d) st = rcx::plan_set_layout(plans[d], c[0], c[1]);
-            if (st == RC_OK) st = build(b);
+            if (st == RC_OK) st = build(b, true);
             if (st != RC_OK) break;
+            long long slices = 0;
+            for (int d = 0; d < n; ++d) slices += std::min(n_lambda[d], c[0]);
             cudaGraphLaunch(b->exec, b->cap);                   // warm-up
             cudaEventRecord(e0, b->cap);
             for (int r = 0; r < 2; ++r) cudaGraphLaunch(b->exec, b->cap);
@@ -257,6 +268,7 @@ rc_status rc_batch_create(int n, const rc_plan_t* plans, const float* const* chi
             cudaEventSynchronize(e1);
             float ms = 0.0f;
             cudaEventElapsedTime(&ms, e0, e1);
+            ms /= (float)slices;
             if (ms < best) {
                 best = ms;
                 bLB = c[0];

@@ -127,13 +127,17 @@ struct Voxel {
 // of a warp that step along different axes), and the voxel address is a running
 // 32-bit offset.
 // With SPLIT_FIRST the emission of the first piece (for a cascade-0 ray: the probe's
-// own cell from its centre to its edge) goes to I0 instead of I.
-template <int LB, int VL, bool SPLIT_FIRST = false>
+// own cell from its centre to its edge) goes to I0 instead of I.  With CONTRIB every
+// piece's contribution T S (1 - e^{-dtau}) is also added to contrib[j * ncell + cell] for the
+// lane's first n_valid wavelengths (the contribution function of Sec. 3.9).
+template <int LB, int VL, bool SPLIT_FIRST = false, bool CONTRIB = false>
 __device__ __forceinline__ void march_interval(const float2* __restrict__ F, int nx, int nz,
                                                float ox, float oz, float wx, float wz,
                                                float a, float b, int lane_off,
                                                unsigned off_hi, int max_steps,
-                                               float (&I)[VL], float (&T)[VL], float (&I0)[VL]) {
+                                               float (&I)[VL], float (&T)[VL], float (&I0)[VL],
+                                               float* contrib = nullptr, int n_valid = 0,
+                                               long long ncell = 0) {
 #pragma unroll
     for (int j = 0; j < VL; ++j) {
         I[j] = 0.0f;
@@ -191,6 +195,9 @@ __device__ __forceinline__ void march_interval(const float2* __restrict__ F, int
                 I0[j] = cur.v[j].y * om;
             else
                 I[j] = fmaf(T[j] * cur.v[j].y, om, I[j]);
+            if (CONTRIB && j < n_valid)
+                atomicAdd(contrib + (size_t)j * ncell + (min((unsigned)off, off_hi) - lane_off) / LB,
+                          T[j] * cur.v[j].y * om);
             T[j] *= e;
         }
         if (tn >= thi) break;
@@ -329,6 +336,8 @@ __device__ __forceinline__ void level_body(const LevelArgs& A, int lb, long long
         k = (int)(ray % A.W);
         probe = ray / A.W;
     }
+    if (A.probe_list) probe = A.probe_list[probe];   // sparse: the flagged probes only
+    const long long sray = probe * A.W + k;           // the ray's slot in the merged storage
     const int px = (int)(probe % A.Px), pz = (int)(probe / A.Px);
     const float2 d = A.dirs[k];
     const float ox = ((float)px + 0.5f) * A.spacing, oz = ((float)pz + 0.5f) * A.spacing;
@@ -364,7 +373,7 @@ __device__ __forceinline__ void level_body(const LevelArgs& A, int lb, long long
     const float inv = A.scale ? 1.0f / A.scale[lb] : 1.0f;
 #pragma unroll
     for (int j = 0; j < VL; ++j)
-        Store<TS>::store(out + ((size_t)(ray >> 2) * LB + lane_off + j) * 4 + (ray & 3), R[j] * inv);
+        Store<TS>::store(out + ((size_t)(sray >> 2) * LB + lane_off + j) * 4 + (sray & 3), R[j] * inv);
 }
 
 template <int LB, int VL, typename TS, bool HAS_UP, bool FIX>
@@ -384,8 +393,9 @@ __device__ __forceinline__ void level0_body(const LevelArgs& A, int lb, long lon
     const int lane = threadIdx.x & 31;
     const int g = lane / LPR, q = lane % LPR;
     const long long wid = cta * kWarpsPerCta + (threadIdx.x >> 5);
-    const long long cell = wid * G + g;
-    if (cell >= A.ncell) return;
+    long long cell = wid * G + g;
+    if (cell >= A.rays) return;                       // rays = cells (or flagged cells) here
+    if (A.probe_list) cell = A.probe_list[cell];
     const int px = (int)(cell % A.nx), pz = (int)(cell / A.nx);
     const float ox = (float)px + 0.5f, oz = (float)pz + 0.5f;
     const float2* F = A.field + (size_t)lb * A.ncell * LB;
@@ -458,25 +468,69 @@ level0_kernel(const LevelArgs A) {
 }
 
 // ---------------------------------------------------------------------------
-// batched: one persistent launch per cascade over the CTA-sized chunks of every
-// (domain, lambda block) segment of a batch, segments sorted by estimated cost
-// (most expensive first) so the tail of the launch is made of cheap chunks.
-// Chunk t belongs to the last segment whose prefix is <= t.
+// batched: one launch per cascade over the CTA-sized chunks of every (domain, lambda
+// block) segment of a batch, one chunk per CTA, segments sorted by estimated cost (most
+// expensive first) so the tail of the launch is made of cheap chunks.  The hardware hands
+// out CTAs in index order, which keeps the chunks in flight within a few segments (the
+// same L2 footprint as a single-domain launch) and balances uneven chunk costs.
+// Chunk t belongs to the last segment whose prefix is <= t; that domain's arguments are
+// staged in shared memory.
 // ---------------------------------------------------------------------------
 template <bool LEVEL0, int LB, int VL, typename TS, bool HAS_UP>
 __global__ void __launch_bounds__(kWarpsPerCta * 32, RCX_MIN_CTAS)
 batched_level_kernel(const BatchLevelArgs B) {
-    for (long long t = blockIdx.x; t < B.total; t += gridDim.x) {
+    static_assert(sizeof(LevelArgs) % sizeof(int) == 0, "LevelArgs is copied word by word");
+    __shared__ __align__(16) int sargs[sizeof(LevelArgs) / sizeof(int)];
+    __shared__ int sseg;
+    const long long t = blockIdx.x;
+    if (threadIdx.x == 0) {
         int lo = 0, hi = B.n_seg - 1;
         while (lo < hi) {
             const int mid = (lo + hi + 1) >> 1;
             if (B.prefix[mid] <= t) lo = mid;
             else hi = mid - 1;
         }
-        const LevelArgs& A = B.args[B.seg_domain[lo]];
-        if (LEVEL0) level0_body<LB, VL, TS, HAS_UP>(A, B.seg_lblk[lo], t - B.prefix[lo]);
-        else level_body<LB, VL, TS, HAS_UP>(A, B.seg_lblk[lo], t - B.prefix[lo]);
+        sseg = lo;
     }
+    __syncthreads();
+    const int seg = sseg;
+    const int* src = reinterpret_cast<const int*>(B.args + B.seg_domain[seg]);
+    for (int w = threadIdx.x; w < (int)(sizeof(LevelArgs) / sizeof(int)); w += blockDim.x)
+        sargs[w] = src[w];
+    __syncthreads();
+    const LevelArgs& A = *reinterpret_cast<const LevelArgs*>(sargs);
+    if (LEVEL0) level0_body<LB, VL, TS, HAS_UP>(A, B.seg_lblk[seg], t - B.prefix[seg]);
+    else level_body<LB, VL, TS, HAS_UP>(A, B.seg_lblk[seg], t - B.prefix[seg]);
+}
+
+// ---------------------------------------------------------------------------
+// emergent intensity along given rays, front to back (Sec. 3.9): a lane group per ray
+// ---------------------------------------------------------------------------
+template <int LB, bool CONTRIB>
+__global__ void __launch_bounds__(kWarpsPerCta * 32)
+emergent_kernel(const EmergentArgs A) {
+    constexpr int VL = LB < 4 ? LB : 4;
+    constexpr int LPR = LB / VL;
+    constexpr int G = 32 / LPR;
+    const int lane = threadIdx.x & 31;
+    const int g = lane / LPR, q = lane % LPR;
+    const long long ray = ((long long)blockIdx.x * kWarpsPerCta + (threadIdx.x >> 5)) * G + g;
+    if (ray >= A.n_rays) return;
+    const int lb = blockIdx.y;
+    const float4 r = __ldg(reinterpret_cast<const float4*>(A.rays) + ray);
+    const float2* F = A.field + (size_t)lb * A.ncell * LB;
+    const int lane_off = q * VL;
+    const unsigned off_hi = (unsigned)((A.ncell - 1) * LB + lane_off);
+    const int lam0 = lb * LB + lane_off;
+    const int n_valid = max(0, min(VL, A.n_lambda - lam0));
+    float I[VL], T[VL], I0[VL];
+    march_interval<LB, VL, false, CONTRIB>(F, A.nx, A.nz, r.x, r.y, r.z, r.w, 0.0f, INFINITY,
+                                           lane_off, off_hi, A.max_steps, I, T, I0,
+                                           CONTRIB ? A.contrib + (size_t)lam0 * A.ncell : nullptr,
+                                           n_valid, A.ncell);
+#pragma unroll
+    for (int j = 0; j < VL; ++j)
+        if (j < n_valid) A.I[(size_t)(lam0 + j) * A.n_rays + ray] = I[j];
 }
 
 // ---------------------------------------------------------------------------
@@ -497,7 +551,7 @@ __global__ void __launch_bounds__(256) pack_kernel(const PackArgs P) {
             const int vlam = lb * LB + l;
             const int lam = vlam / P.n_incl;
             float c = 0.0f, s = 0.0f;
-            if (lam < P.n_lambda) {
+            if (lam < P.n_lambda && (!P.active || P.active[cell])) {
                 const float chi = __ldg(P.chi + (size_t)lam * P.ncell + cell);
                 const float eta = __ldg(P.eta + (size_t)lam * P.ncell + cell);
                 const float cv = fmaxf(chi * P.voxel, kChiFloor);
@@ -577,6 +631,61 @@ __global__ void __launch_bounds__(256) batched_pack_kernel(const BatchPackArgs B
     }
 }
 
+__global__ void flags_seed_kernel(const unsigned char* __restrict__ active,
+                                  unsigned char* __restrict__ f0, long long ncell) {
+    const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c < ncell) f0[c] = active[c] ? 1 : 0;
+}
+
+__global__ void flags_up_kernel(const unsigned char* __restrict__ f, int Px, int Pz,
+                                unsigned char* __restrict__ fu, int Pxu, int Pzu) {
+    const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= (long long)Px * Pz || !f[p]) return;
+    int jx0, jx1, jz0, jz1;
+    float fx, fz;
+    upper_coord((int)(p % Px), Pxu, jx0, jx1, fx);
+    upper_coord((int)(p / Px), Pzu, jz0, jz1, fz);
+    fu[(size_t)jz0 * Pxu + jx0] = 1;   // every bracketing parent, zero weights included
+    fu[(size_t)jz0 * Pxu + jx1] = 1;
+    fu[(size_t)jz1 * Pxu + jx0] = 1;
+    fu[(size_t)jz1 * Pxu + jx1] = 1;
+}
+
+// One CTA walks the flags in chunks of 1024 and writes the flagged indices in order
+// (a block-wide exclusive scan per chunk): deterministic probe order.
+__global__ void __launch_bounds__(1024) compact_kernel(const unsigned char* __restrict__ f, long long n,
+                                                       int* __restrict__ list, int* __restrict__ n_out) {
+    __shared__ int warp_sums[32];
+    __shared__ int base;
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    if (tid == 0) base = 0;
+    __syncthreads();
+    for (long long c0 = 0; c0 < n; c0 += 1024) {
+        const long long c = c0 + tid;
+        const int flag = (c < n && f[c]) ? 1 : 0;
+        const unsigned mask = __ballot_sync(0xffffffffu, flag);
+        const int before_in_warp = __popc(mask & ((1u << lane) - 1u));
+        if (lane == 0) warp_sums[w] = __popc(mask);
+        __syncthreads();
+        if (w == 0) {
+            const int v = warp_sums[lane];
+            int x = v;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, x, o);
+                if (lane >= o) x += y;
+            }
+            warp_sums[lane] = x - v;                 // exclusive prefix of the warp counts
+        }
+        __syncthreads();
+        if (flag) list[base + warp_sums[w] + before_in_warp] = (int)c;
+        __syncthreads();
+        if (tid == 1023) base += warp_sums[31] + __popc(mask);   // total of this chunk
+        __syncthreads();
+    }
+    if (tid == 0) *n_out = base;
+}
+
 __global__ void incl_reduce_kernel(const float* __restrict__ in, float* __restrict__ out,
                                    int n_lambda, int n_incl, const float* __restrict__ w,
                                    long long ncell) {
@@ -618,6 +727,48 @@ cudaError_t launch_pack(int LB, int n_lblk, const PackArgs& a, cudaStream_t s) {
     return cudaErrorInvalidValue;
 }
 
+cudaError_t launch_flags_seed(const unsigned char* active, unsigned char* f0, long long ncell,
+                              cudaStream_t s) {
+    flags_seed_kernel<<<(unsigned)((ncell + 255) / 256), 256, 0, s>>>(active, f0, ncell);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_flags_up(const unsigned char* f, int Px, int Pz, unsigned char* fu, int Pxu,
+                            int Pzu, cudaStream_t s) {
+    const long long n = (long long)Px * Pz;
+    flags_up_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(f, Px, Pz, fu, Pxu, Pzu);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_compact(const unsigned char* f, long long n, int* list, int* n_out,
+                           cudaStream_t s) {
+    compact_kernel<<<1, 1024, 0, s>>>(f, n, list, n_out);
+    return cudaGetLastError();
+}
+
+template <int LB>
+static cudaError_t emergent_t(int n_lblk, const EmergentArgs& a, cudaStream_t s) {
+    constexpr int VL = LB < 4 ? LB : 4;
+    const long long per_cta = (long long)(32 / (LB / VL)) * kWarpsPerCta;
+    dim3 grid((unsigned)((a.n_rays + per_cta - 1) / per_cta), (unsigned)n_lblk);
+    if (a.contrib) emergent_kernel<LB, true><<<grid, kWarpsPerCta * 32, 0, s>>>(a);
+    else emergent_kernel<LB, false><<<grid, kWarpsPerCta * 32, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_emergent(int LB, int n_lblk, const EmergentArgs& a, cudaStream_t s) {
+    if (a.n_rays == 0) return cudaSuccess;
+    switch (LB) {
+        case 1: return emergent_t<1>(n_lblk, a, s);
+        case 2: return emergent_t<2>(n_lblk, a, s);
+        case 4: return emergent_t<4>(n_lblk, a, s);
+        case 8: return emergent_t<8>(n_lblk, a, s);
+        case 16: return emergent_t<16>(n_lblk, a, s);
+        case 32: return emergent_t<32>(n_lblk, a, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
 cudaError_t launch_incl_reduce(const float* in, float* out, int n_lambda, int n_incl,
                                const float* w, long long ncell, cudaStream_t s) {
     dim3 grid((unsigned)((ncell + 255) / 256), (unsigned)n_lambda);
@@ -634,7 +785,8 @@ template <int LB, int VL, typename TS>
 static cudaError_t level_t(bool level0, bool has_up, int n_lblk, const LevelArgs& a,
                            cudaStream_t s) {
     constexpr int G = 32 / (LB / VL);
-    const long long items = level0 ? a.ncell : a.rays;
+    const long long items = a.rays;                   // rays, or cascade-0 cells
+    if (items == 0) return cudaSuccess;
     const long long per_cta = (long long)G * kWarpsPerCta;
     dim3 grid((unsigned)((items + per_cta - 1) / per_cta), (unsigned)n_lblk);
     dim3 block(kWarpsPerCta * 32);

@@ -52,6 +52,7 @@ struct LevelArgs {
     long long R_out_lstride;
     const float* scale;      // per lambda block storage scale (16-bit storage), NULL = 1
     // cascade 0 outputs
+    const int* probe_list;   // sparse: flagged probes of this cascade (ascending), else NULL
     float* J;
     float* alo;
     float* J_eff;            // J without the cell's own segment emission (MALI), may be NULL
@@ -66,10 +67,24 @@ struct PackArgs {
     int n_lambda;            // physical wavelengths
     int n_incl;              // inclinations per wavelength (virtual wavelength l n_incl + j)
     const float* incl_r;     // 1/sqrt(1 - mu_j^2) per inclination (NULL when n_incl == 1)
+    const unsigned char* active;  // sparse: inactive cells packed transparent (NULL = all)
     long long ncell;
     float voxel;
     float2* out;
     unsigned int* smax_bits;  // per lambda block, may be NULL
+};
+
+// Emergent intensity along caller rays (front to back, Sec. 3.9).
+struct EmergentArgs {
+    const float2* field;
+    long long ncell;
+    int nx, nz;
+    const float* rays;            // [n_rays][4]: ox, oz, wx, wz (voxels)
+    long long n_rays;
+    float* I;                     // [n_lambda][n_rays]
+    float* contrib;               // [n_lambda][ncell] or NULL
+    int n_lambda;
+    int max_steps;
 };
 
 // A batch launch: CTA-sized chunks of all (domain, lambda block) segments of one cascade.
@@ -90,6 +105,18 @@ struct BatchPackArgs {
     int n_seg;
     long long total;
 };
+
+// Sparse flags (Sec. 3.5): seed cascade 0 from the cell mask, propagate each flagged
+// probe to the upper probes its bilinear lookup brackets, and compact the flagged probes
+// of a cascade into an ascending list (count -> *n_out, device).
+cudaError_t launch_flags_seed(const unsigned char* active, unsigned char* f0, long long ncell,
+                              cudaStream_t s);
+cudaError_t launch_flags_up(const unsigned char* f, int Px, int Pz, unsigned char* fu, int Pxu,
+                            int Pzu, cudaStream_t s);
+cudaError_t launch_compact(const unsigned char* f, long long n, int* list, int* n_out,
+                           cudaStream_t s);
+
+cudaError_t launch_emergent(int LB, int n_lblk, const EmergentArgs& a, cudaStream_t s);
 
 // Weighted sum over inclinations: out[l][c] = sum_j w_j in[l n_incl + j][c].
 cudaError_t launch_incl_reduce(const float* in, float* out, int n_lambda, int n_incl,
@@ -136,6 +163,12 @@ struct rc_plan_s {
     float* d_incl = nullptr;         // [r_j (n_incl)][w_j (n_incl)]
     float* d_vout = nullptr;         // per-inclination cascade-0 outputs before the reduction
     size_t vout_floats = 0;
+    // sparsity (Sec. 3.5): flags and flagged-probe lists per cascade, or none
+    bool sparse = false;
+    unsigned char* d_active = nullptr;     // copy of the cell mask
+    void* d_sparse = nullptr;              // flags and lists of every cascade
+    std::vector<const int*> probe_list;    // per cascade
+    std::vector<long long> n_flagged;      // per cascade
     std::vector<rcx::LevelGeom> lv;
     std::vector<size_t> dir_off;     // offset of each cascade's table in d_dirs
     float2* d_dirs = nullptr;

@@ -233,6 +233,177 @@ mlp_tile_kernel(const float* __restrict__ wbf, const float* __restrict__ norm,
     }  // TRAIN
 }
 
+// ---------------------------------------------------------------------------
+// inference with the 64 x 64 layer on the tensor cores (tcgen05, sm_100 family)
+//
+// Per CTA of 128 samples: h1 (128 x 64) and W2 (64 x 64) as bf16 in shared memory in the
+// no-swizzle K-major layout of 8-row x 16-byte core matrices (K step between core matrices
+// 128 B, row-group step 1024 B); one elected thread issues four tcgen05.mma (M = 128,
+// N = 64, K = 16 each, FP32 accumulation in 64 TMEM columns) and commits them to an
+// mbarrier; every warp waits (bounded) and reads its quarter of the rows back with
+// tcgen05.ld for the bias, tanh and the 64 -> 3 output layer.
+// ---------------------------------------------------------------------------
+constexpr int TC_SMEM_A = TILE * NH * 2;     // 16 KB bf16
+constexpr int TC_SMEM_B = NH * NH * 2;       //  8 KB bf16
+constexpr unsigned kTcWaitLimit = 1u << 21;  // mbarrier polls before giving up
+
+struct TcSmem {
+    alignas(1024) unsigned char a[TC_SMEM_A];
+    alignas(1024) unsigned char b[TC_SMEM_B];
+    float w1[NH * NI], b1[NH], b2[NH], w3[NO * NH], b3[NO];
+    float mean[NI], istd[NI];
+    float h2[TILE * LD];
+    alignas(8) unsigned long long mbar;
+    unsigned tmem_base;
+};
+
+// byte offset of element (row r, k) of a K-major no-swizzle operand with K = 64
+__device__ __forceinline__ int core_offset(int r, int k) {
+    return (r >> 3) * 1024 + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2;
+}
+
+__device__ __forceinline__ unsigned long long smem_desc(const void* p) {
+    const unsigned addr = (unsigned)__cvta_generic_to_shared(p);
+    unsigned long long d = 0;
+    d |= (unsigned long long)((addr >> 4) & 0x3FFF);          // start address
+    d |= (unsigned long long)((128 >> 4) & 0x3FFF) << 16;      // leading (K) byte offset
+    d |= (unsigned long long)((1024 >> 4) & 0x3FFF) << 32;     // stride (row group) byte offset
+    d |= 1ull << 46;                                           // descriptor version (sm_100)
+    return d;                                                  // base offset 0, no swizzle
+}
+
+// instruction descriptor: FP32 accumulate, bf16 A and B, both K-major, N = 64, M = 128
+__device__ __forceinline__ unsigned mma_idesc() {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((unsigned)(NH >> 3) << 17) |
+           ((unsigned)(TILE >> 4) << 24);
+}
+
+__global__ void __launch_bounds__(THREADS)
+mlp_forward_tc_kernel(const float* __restrict__ wbf, const float* __restrict__ norm,
+                      const float* __restrict__ X, long long B, float* __restrict__ Y,
+                      int* __restrict__ err) {
+    extern __shared__ __align__(1024) unsigned char tc_raw[];
+    // the launch adds 1024 B of slack so the operand tiles can start on a 1024 B boundary
+    const unsigned raw_s = (unsigned)__cvta_generic_to_shared(tc_raw);
+    TcSmem& S = *reinterpret_cast<TcSmem*>(tc_raw + (((raw_s + 1023u) & ~1023u) - raw_s));
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const long long s0 = (long long)blockIdx.x * TILE;
+    const int nvalid = (int)min((long long)TILE, B - s0);
+
+    if (warp == 0) {   // TMEM: 64 columns for the 128 x 64 FP32 accumulator
+        const unsigned dst = (unsigned)__cvta_generic_to_shared(&S.tmem_base);
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 64;" ::"r"(dst));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (tid == 0) {
+        const unsigned mb = (unsigned)__cvta_generic_to_shared(&S.mbar);
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb));
+    }
+    for (int i = tid; i < NH * NI; i += THREADS) S.w1[i] = wbf[OFF_W1 + i];
+    for (int i = tid; i < NH; i += THREADS) {
+        S.b1[i] = wbf[OFF_B1 + i];
+        S.b2[i] = wbf[OFF_B2 + i];
+    }
+    for (int i = tid; i < NO * NH; i += THREADS) S.w3[i] = wbf[OFF_W3 + i];
+    if (tid < NO) S.b3[tid] = wbf[OFF_B3 + tid];
+    if (tid < NI) {
+        S.mean[tid] = norm[tid];
+        S.istd[tid] = 1.0f / norm[NI + tid];
+    }
+    // W2 [out n][in k] is already K-major for D[m][n] = sum_k A[m][k] B[n][k]
+    for (int i = tid; i < NH * NH; i += THREADS) {
+        const int n = i / NH, k = i % NH;
+        *reinterpret_cast<__nv_bfloat16*>(S.b + core_offset(n, k)) = __float2bfloat16_rn(wbf[OFF_W2 + i]);
+    }
+    __syncthreads();
+    // h1 = tanh(W1 xn + b1) as bf16 into the A operand
+    for (int i = tid; i < TILE * NH; i += THREADS) {
+        const int r = i / NH, o = i % NH;
+        float a = 0.0f;
+        if (r < nvalid) {
+            a = S.b1[o];
+#pragma unroll
+            for (int f = 0; f < NI; ++f)
+                a = fmaf(S.w1[o * NI + f], (X[(s0 + r) * NI + f] - S.mean[f]) * S.istd[f], a);
+            a = tanhf(a);
+        }
+        *reinterpret_cast<__nv_bfloat16*>(S.a + core_offset(r, o)) = __float2bfloat16_rn(a);
+    }
+    // generic-proxy stores -> visible to the tensor core (async proxy)
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const unsigned tmem = S.tmem_base;
+    const unsigned mb = (unsigned)__cvta_generic_to_shared(&S.mbar);
+    if (tid == 0) {
+        const unsigned idesc = mma_idesc();
+#pragma unroll
+        for (int kk = 0; kk < NH / 16; ++kk) {
+            // K = 16 per instruction: advance both operands by two core matrices (256 B)
+            const unsigned long long da = smem_desc(S.a + kk * 256);
+            const unsigned long long db = smem_desc(S.b + kk * 256);
+            const unsigned acc = kk > 0 ? 1u : 0u;
+            asm volatile(
+                "{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %4, 0;\n\t"
+                "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
+                ::"r"(tmem), "l"(da), "l"(db), "r"(idesc), "r"(acc));
+        }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                     ::"r"(mb) : "memory");
+    }
+    // bounded wait for the MMAs (phase 0): non-blocking polls with a short sleep, so the
+    // limit bounds the wall time (about kTcWaitLimit x 64 ns)
+    unsigned done = 0;
+    for (unsigned it = 0; it < kTcWaitLimit && !done; ++it) {
+        asm volatile("{\n\t.reg .pred q;\n\t"
+                     "mbarrier.test_wait.parity.shared::cta.b64 q, [%1], 0;\n\t"
+                     "selp.u32 %0, 1, 0, q;\n\t}"
+                     : "=r"(done) : "r"(mb) : "memory");
+        if (!done) __nanosleep(64);
+    }
+    // block-uniform outcome: the epilogue's .sync.aligned loads need whole warps
+    done = __syncthreads_and(done);
+    if (!done && tid == 0) atomicExch(err, 1);
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    // epilogue: warp w reads rows 32 (w % 4) .. +31 and columns 32 (w / 4) .. +31
+    if (done) {
+        const int rbase = 32 * (warp & 3), cbase = 32 * (warp >> 2);
+        unsigned v[32];
+        const unsigned taddr = tmem + ((unsigned)rbase << 16) + (unsigned)cbase;
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+            "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+            "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+            : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+              "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]),
+              "=r"(v[13]), "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]),
+              "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]),
+              "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]),
+              "=r"(v[31])
+            : "r"(taddr));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        const int r = rbase + lane;
+#pragma unroll
+        for (int c = 0; c < 32; ++c)
+            S.h2[r * LD + cbase + c] = tanhf(__uint_as_float(v[c]) + S.b2[cbase + c]);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 64;" ::"r"(tmem));
+    }
+    if (!done) return;
+    for (int i = tid; i < TILE * NO; i += THREADS) {
+        const int r = i / NO, o = i % NO;
+        if (r >= nvalid) continue;
+        float a = S.b3[o];
+        for (int k = 0; k < NH; ++k) a = fmaf(S.w3[o * NH + k], S.h2[r * LD + k], a);
+        Y[(s0 + r) * NO + o] = a;
+    }
+}
+
 // Adam (Kingma & Ba 2015) on the FP32 master weights; also refreshes the bf16-rounded copy.
 __global__ void adam_kernel(float* __restrict__ theta, float* __restrict__ wbf,
                             float* __restrict__ m, float* __restrict__ v,
@@ -318,11 +489,14 @@ struct rc_mlp_s {
     long long step = 0;
     unsigned long long seed = 0;
     float* h_loss = nullptr;       // pinned
+    bool tensor_cores = false;     // inference through mlp_forward_tc_kernel
+    int* d_err = nullptr;          // set if a tensor-core wait ran out
 };
 
 namespace {
 
 size_t smem_bytes() { return sizeof(Smem); }
+size_t tc_smem_bytes() { return sizeof(TcSmem) + 1024; }   // + alignment slack
 
 rc_status ensure_configured() {
     static bool done = false;
@@ -332,6 +506,9 @@ rc_status ensure_configured() {
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(mlp_tile_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)smem_bytes());
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(mlp_forward_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)tc_smem_bytes());
     if (e != cudaSuccess) return mcuda(e, "mlp: shared-memory opt-in");
     done = true;
     return RC_OK;
@@ -412,6 +589,7 @@ void rc_mlp_destroy(rc_mlp_t n) {
     cudaFree(n->d_mom);
     cudaFree(n->Xb);
     cudaFree(n->Ysc);
+    cudaFree(n->d_err);
     cudaFreeHost(n->h_loss);
     delete n;
 }
@@ -461,11 +639,38 @@ rc_status rc_mlp_forward(rc_mlp_t n, const float* X, long long B, float* Y, void
     if (B == 0) return RC_OK;
     rc_status st = ensure_configured();
     if (st != RC_OK) return st;
-    mlp_tile_kernel<false><<<(unsigned)((B + TILE - 1) / TILE), THREADS, smem_bytes(),
-                             (cudaStream_t)stream>>>(n->wbf, n->norm, X, nullptr, B, Y, nullptr,
-                                                     nullptr);
+    if (n->tensor_cores) {
+        mlp_forward_tc_kernel<<<(unsigned)((B + TILE - 1) / TILE), THREADS, tc_smem_bytes(),
+                                (cudaStream_t)stream>>>(n->wbf, n->norm, X, B, Y, n->d_err);
+    } else {
+        mlp_tile_kernel<false><<<(unsigned)((B + TILE - 1) / TILE), THREADS, smem_bytes(),
+                                 (cudaStream_t)stream>>>(n->wbf, n->norm, X, nullptr, B, Y, nullptr,
+                                                         nullptr);
+    }
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? RC_OK : mcuda(e, "rc_mlp_forward");
+}
+
+rc_status rc_mlp_use_tensor_cores(rc_mlp_t n, int enable) {
+    rcx::set_last_error("");
+    if (!n) return mfail(RC_ERR_ARG, "rc_mlp_use_tensor_cores: NULL network");
+    if (enable && !n->d_err) {
+        cudaError_t e = cudaMalloc(&n->d_err, sizeof(int));
+        if (e == cudaSuccess) e = cudaMemset(n->d_err, 0, sizeof(int));
+        if (e != cudaSuccess) return mcuda(e, "rc_mlp_use_tensor_cores");
+    }
+    n->tensor_cores = enable != 0;
+    return RC_OK;
+}
+
+rc_status rc_mlp_tensor_core_status(rc_mlp_t n) {
+    rcx::set_last_error("");
+    if (!n) return mfail(RC_ERR_ARG, "rc_mlp_tensor_core_status: NULL network");
+    if (!n->d_err) return RC_OK;
+    int h = 0;
+    cudaError_t e = cudaMemcpy(&h, n->d_err, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return mcuda(e, "rc_mlp_tensor_core_status");
+    return h ? mfail(RC_ERR_TIMEOUT, "tensor-core MMA wait ran out") : RC_OK;
 }
 
 rc_status rc_mlp_loss_grad(rc_mlp_t n, const float* X, const float* Yt, long long B, float* grad,

@@ -142,10 +142,12 @@ __global__ void stat_eq_kernel(AtomDev A, const double* __restrict__ T,
                                const double* __restrict__ ne, const double* __restrict__ n_atom,
                                const float* __restrict__ Jeff, const float* __restrict__ aloc,
                                long long ncell, double* __restrict__ pops,
-                               unsigned long long* __restrict__ dmax_bits) {
+                               unsigned long long* __restrict__ dmax_bits,
+                               const unsigned char* __restrict__ active) {
     const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     double rel = 0.0;
-    if (c < ncell) {
+    // cells outside a sparse plan's active set (Sec. 3.5) keep their populations
+    if (c < ncell && (!active || active[c])) {
         const int n = A.n_levels;
         const double t = T[c], sqT = sqrt(t), nec = ne[c];
         double G[kMaxLevels][kMaxLevels];
@@ -255,11 +257,12 @@ namespace {
 
 rc_status launch_stat_eq(rc_atom_t a, const double* T, const double* ne, const double* n_atom,
                          const float* J_eff, const float* alo_c, long long ncell, double* pops,
-                         cudaStream_t s) {
+                         cudaStream_t s, const unsigned char* active = nullptr) {
     cudaError_t e = cudaMemsetAsync(a->d_dmax, 0, sizeof(unsigned long long), s);
     if (e != cudaSuccess) return ncuda(e, "rc_stat_eq");
     stat_eq_kernel<<<(unsigned)((ncell + 255) / 256), 256, 0, s>>>(a->dev, T, ne, n_atom, J_eff,
-                                                                   alo_c, ncell, pops, a->d_dmax);
+                                                                   alo_c, ncell, pops, a->d_dmax,
+                                                                   active);
     if ((e = cudaGetLastError()) != cudaSuccess) return ncuda(e, "rc_stat_eq launch");
     return RC_OK;
 }
@@ -464,7 +467,8 @@ rc_status rc_nlte_solve(rc_plan_t plan, rc_atom_t a, const double* T, const doub
         if (st != RC_OK) return st;
         st = rc_formal_solve_mali(plan, chi, eta, nl, J, nullptr, Jeff, aloc, stream);
         if (st != RC_OK) return st;
-        st = launch_stat_eq(a, T, ne, n_atom, Jeff, aloc, ncell, pops, s);
+        st = launch_stat_eq(a, T, ne, n_atom, Jeff, aloc, ncell, pops, s,
+                            plan->sparse ? plan->d_active : nullptr);
         if (st != RC_OK) return st;
         st = read_dmax(a, s, &change);
         if (st != RC_OK) return st;

@@ -135,8 +135,8 @@ extern "C" rc_status rc_formal_solve_noalloc(const rc_grid* grid, int n_cascades
         if ((e = cudaGetLastError()) != cudaSuccess)
             return nfail(RC_ERR_CUDA, std::string("rc_formal_solve_noalloc: ") + cudaGetErrorString(e));
     }
-    rcx::PackArgs pa{chi, eta, n_lambda, 1, nullptr, ncell, (float)grid->voxel_size, packed,
-                     nullptr};
+    rcx::PackArgs pa{chi, eta, n_lambda, 1, nullptr, nullptr, ncell, (float)grid->voxel_size,
+                     packed, nullptr};
     if ((e = rcx::launch_pack(LB, n_lblk, pa, s)) != cudaSuccess)
         return nfail(RC_ERR_CUDA, std::string("rc_formal_solve_noalloc: ") + cudaGetErrorString(e));
     for (int i = n_cascades - 1; i >= 0; --i) {
@@ -157,7 +157,7 @@ extern "C" rc_status rc_formal_solve_noalloc(const rc_grid* grid, int n_cascades
         a.a = (float)lv[i].a;
         a.b = std::isinf(lv[i].b) ? INFINITY : (float)lv[i].b;
         a.dirs = dirs + dir_off[i];
-        a.rays = lv[i].rays();
+        a.rays = i == 0 ? ncell : lv[i].rays();   // cascade 0 runs one lane group per cell
         const bool has_up = i < n_cascades - 1;
         if (has_up) {
             a.R_up = R[(i + 1) & 1];

@@ -213,8 +213,16 @@ rc_status solve_device(rc_plan_s* p, const float* chi, const float* eta, int n_l
         if ((e = cudaMemsetAsync(p->d_smax, 0, n_lblk * sizeof(unsigned), s)) != cudaSuccess)
             return cuda_fail(e, "memset");
     }
-    rcx::PackArgs pa{chi, eta, n_phys, NI, NI > 1 ? p->d_incl : nullptr, ncell,
-                     (float)p->voxel, p->d_packed, f16 ? p->d_smax : nullptr};
+    rcx::PackArgs pa{chi, eta, n_phys, NI, NI > 1 ? p->d_incl : nullptr,
+                     p->sparse ? p->d_active : nullptr, ncell, (float)p->voxel, p->d_packed,
+                     f16 ? p->d_smax : nullptr};
+    if (p->sparse) {
+        // cells outside the active set get J = 0 (their lane groups do not run)
+        float* outs[4] = {Jv, alov, Jeffv, alocv};
+        for (float* o : outs)
+            if (o && (e = cudaMemsetAsync(o, 0, (size_t)n_lambda * ncell_ * sizeof(float), s)) != cudaSuccess)
+                return cuda_fail(e, "memset");
+    }
     if ((e = rcx::launch_pack(LB, n_lblk, pa, s)) != cudaSuccess) return cuda_fail(e, "pack launch");
     ++launches;
     mark("pack");
@@ -271,7 +279,14 @@ rcx::LevelArgs rcx::level_args(const rc_plan_s* p, int i, int n_lambda, float* J
     a.a = (float)g.a;
     a.b = std::isinf(g.b) ? INFINITY : (float)g.b;
     a.dirs = p->d_dirs + p->dir_off[i];
-    a.rays = g.rays();
+    // cascade 0 runs one lane group per cell (looping over its directions); sparse plans
+    // run the flagged probes only
+    if (p->sparse) {
+        a.probe_list = p->probe_list[i];
+        a.rays = i == 0 ? p->n_flagged[0] : p->n_flagged[i] * g.W;
+    } else {
+        a.rays = i == 0 ? (long long)p->nx * p->nz : g.rays();
+    }
     a.bilinear_fix = p->opt.bilinear_fix;
     if (i < p->C - 1) {
         const rcx::LevelGeom& u = p->lv[i + 1];
@@ -461,6 +476,8 @@ void rc_plan_destroy(rc_plan_t p) {
     cudaFree(p->d_dirs);
     cudaFree(p->d_incl);
     cudaFree(p->d_vout);
+    cudaFree(p->d_active);
+    cudaFree(p->d_sparse);
     cudaFree(p->d_stage);
     for (auto& s : p->s_io)
         if (s) cudaStreamDestroy(s);
@@ -497,6 +514,110 @@ rc_status rc_plan_cascade(rc_plan_t p, int i, int* px, int* pz, long long* dirs,
 }
 
 int rc_plan_last_launch_count(rc_plan_t p) { return p ? p->last_launches : 0; }
+
+rc_status rc_emergent(rc_plan_t p, const float* chi, const float* eta, int n_lambda,
+                      const float* rays, long long n_rays, float mu, float* I, float* contrib,
+                      void* stream) {
+    g_last_error.clear();
+    if (!p) return fail(RC_ERR_ARG, "rc_emergent: plan is NULL");
+    if (n_lambda < 0 || n_rays < 0 || !(mu >= 0.0f && mu < 1.0f))
+        return fail(RC_ERR_ARG, "rc_emergent: n_lambda, n_rays >= 0 and 0 <= mu < 1 required");
+    if (n_lambda == 0 || n_rays == 0) return RC_OK;
+    if (!chi || !eta || !rays || !I)
+        return fail(RC_ERR_ARG, "rc_emergent: chi, eta, rays and I must be non-NULL");
+    if ((reinterpret_cast<uintptr_t>(rays) & 15) != 0)
+        return fail(RC_ERR_ARG, "rc_emergent: rays must be 16-byte aligned");
+    if ((n_lambda + p->LB - 1) / p->LB > 65535 || n_rays > (1LL << 31))
+        return fail(RC_ERR_ARG, "rc_emergent: too many wavelengths or rays");
+    DeviceGuard dg(p->device);
+    const int NI = p->n_incl;
+    rc_status st = ensure_scratch(p, (n_lambda + NI - 1) / NI);   // room for n_lambda packed
+    if (st != RC_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int LB = p->LB;
+    const int n_lblk = (n_lambda + LB - 1) / LB;
+    const long long ncell = (long long)p->nx * p->nz;
+    // the inclination lengthens the path per projected length by 1/sqrt(1 - mu^2): fold it into
+    // the per-voxel opacity and emissivity (S unchanged)
+    const double r = 1.0 / std::sqrt(1.0 - (double)mu * mu);
+    rcx::PackArgs pa{chi, eta, n_lambda, 1, nullptr, p->sparse ? p->d_active : nullptr, ncell,
+                     (float)(p->voxel * r), p->d_packed, nullptr};
+    cudaError_t e = rcx::launch_pack(LB, n_lblk, pa, s);
+    if (e != cudaSuccess) return cuda_fail(e, "rc_emergent: pack launch");
+    rcx::EmergentArgs ea{p->d_packed, ncell, p->nx, p->nz, rays, n_rays, I, contrib, n_lambda,
+                         p->nx + p->nz + 2};
+    if ((e = rcx::launch_emergent(LB, n_lblk, ea, s)) != cudaSuccess)
+        return cuda_fail(e, "rc_emergent: launch");
+    p->last_launches = 2;
+    return RC_OK;
+}
+
+rc_status rc_plan_set_active(rc_plan_t p, const unsigned char* active, void* stream) {
+    g_last_error.clear();
+    if (!p) return fail(RC_ERR_ARG, "rc_plan_set_active: plan is NULL");
+    DeviceGuard dg(p->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaStreamSynchronize(s);
+    cudaFree(p->d_active);
+    cudaFree(p->d_sparse);
+    p->d_active = nullptr;
+    p->d_sparse = nullptr;
+    p->sparse = false;
+    p->probe_list.clear();
+    p->n_flagged.clear();
+    if (!active) return RC_OK;
+    const int C = p->C;
+    const long long ncell = (long long)p->nx * p->nz;
+    // layout: [flags of every cascade][lists of every cascade][counts]
+    std::vector<size_t> foff(C), loff(C);
+    size_t bytes = 0;
+    for (int i = 0; i < C; ++i) {
+        foff[i] = bytes;
+        bytes += ((size_t)p->lv[i].Px * p->lv[i].Pz + 255) & ~(size_t)255;
+    }
+    for (int i = 0; i < C; ++i) {
+        loff[i] = bytes;
+        bytes += (((size_t)p->lv[i].Px * p->lv[i].Pz * sizeof(int)) + 255) & ~(size_t)255;
+    }
+    const size_t coff = bytes;
+    bytes += 256;
+    cudaError_t e = cudaMalloc(&p->d_sparse, bytes);
+    if (e == cudaSuccess) e = cudaMalloc(&p->d_active, (size_t)ncell);
+    if (e != cudaSuccess) {
+        cudaFree(p->d_sparse);
+        p->d_sparse = nullptr;
+        cudaGetLastError();
+        return fail(RC_ERR_OOM, "rc_plan_set_active: allocation failed");
+    }
+    unsigned char* base = (unsigned char*)p->d_sparse;
+    int* counts = (int*)(base + coff);
+    e = cudaMemcpyAsync(p->d_active, active, (size_t)ncell, cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(base, 0, coff, s);
+    if (e == cudaSuccess) e = rcx::launch_flags_seed(p->d_active, base + foff[0], ncell, s);
+    for (int i = 0; i + 1 < C && e == cudaSuccess; ++i)
+        e = rcx::launch_flags_up(base + foff[i], p->lv[i].Px, p->lv[i].Pz, base + foff[i + 1],
+                                 p->lv[i + 1].Px, p->lv[i + 1].Pz, s);
+    for (int i = 0; i < C && e == cudaSuccess; ++i)
+        e = rcx::launch_compact(base + foff[i], (long long)p->lv[i].Px * p->lv[i].Pz,
+                                (int*)(base + loff[i]), counts + i, s);
+    std::vector<int> h(C);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h.data(), counts, C * sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "rc_plan_set_active");
+    for (int i = 0; i < C; ++i) {
+        p->probe_list.push_back((const int*)(base + loff[i]));
+        p->n_flagged.push_back(h[i]);
+    }
+    p->sparse = true;
+    return RC_OK;
+}
+
+rc_status rc_plan_active_probes(rc_plan_t p, long long* per_cascade) {
+    if (!p || !per_cascade) return fail(RC_ERR_ARG, "rc_plan_active_probes: NULL argument");
+    for (int i = 0; i < p->C; ++i)
+        per_cascade[i] = p->sparse ? p->n_flagged[i] : (long long)p->lv[i].Px * p->lv[i].Pz;
+    return RC_OK;
+}
 
 rc_status rc_plan_set_lane_layout(rc_plan_t p, int lambda_block, int lambda_per_lane) {
     g_last_error.clear();

@@ -32,7 +32,8 @@ EXPORTS = [
     "rc_batch_info", "rc_batch_destroy", "rc_formal_solve_batched", "rc_mlp_create",
     "rc_mlp_destroy", "rc_mlp_n_params", "rc_mlp_set_params", "rc_mlp_get_params",
     "rc_mlp_fit_normalization", "rc_mlp_forward", "rc_mlp_loss_grad", "rc_mlp_train",
-    "rc_surrogate_features", "rc_surrogate_targets", "rc_surrogate_seed",
+    "rc_surrogate_features", "rc_surrogate_targets", "rc_surrogate_seed", "rc_plan_set_active",
+    "rc_plan_active_probes", "rc_emergent", "rc_mlp_use_tensor_cores", "rc_mlp_tensor_core_status",
 ]
 
 
@@ -129,6 +130,13 @@ def load():
                                 ctypes.POINTER(ctypes.c_double), _vp]
     L.rc_nlte_solve.restype = ctypes.c_int
     _ip = ctypes.POINTER(ctypes.c_int)
+    L.rc_emergent.argtypes = [_vp, _vp, _vp, ctypes.c_int, _vp, ctypes.c_longlong, ctypes.c_float,
+                              _vp, _vp, _vp]
+    L.rc_emergent.restype = ctypes.c_int
+    L.rc_plan_set_active.argtypes = [_vp, _vp, _vp]
+    L.rc_plan_set_active.restype = ctypes.c_int
+    L.rc_plan_active_probes.argtypes = [_vp, ctypes.POINTER(ctypes.c_longlong)]
+    L.rc_plan_active_probes.restype = ctypes.c_int
     L.rc_plan_set_lane_layout.argtypes = [_vp, ctypes.c_int, ctypes.c_int]
     L.rc_plan_set_lane_layout.restype = ctypes.c_int
     L.rc_plan_get_lane_layout.argtypes = [_vp, _ip, _ip]
@@ -160,6 +168,10 @@ def load():
     L.rc_mlp_get_params.restype = ctypes.c_int
     L.rc_mlp_fit_normalization.argtypes = [_vp, _vp, ctypes.c_longlong, _vp]
     L.rc_mlp_fit_normalization.restype = ctypes.c_int
+    L.rc_mlp_use_tensor_cores.argtypes = [_vp, ctypes.c_int]
+    L.rc_mlp_use_tensor_cores.restype = ctypes.c_int
+    L.rc_mlp_tensor_core_status.argtypes = [_vp]
+    L.rc_mlp_tensor_core_status.restype = ctypes.c_int
     L.rc_mlp_forward.argtypes = [_vp, _vp, ctypes.c_longlong, _vp, _vp]
     L.rc_mlp_forward.restype = ctypes.c_int
     L.rc_mlp_loss_grad.argtypes = [_vp, _vp, _vp, ctypes.c_longlong, _vp, _vp, _vp]
@@ -276,6 +288,32 @@ class Plan:
         check(load().rc_plan_launch_times(self._h, buf, 64, ctypes.byref(n)))
         return [(load().rc_plan_launch_name(self._h, j).decode(), float(buf[j]))
                 for j in range(n.value)]
+
+    def emergent(self, chi, eta, rays, mu: float = 0.0, want_contrib: bool = False, stream=None):
+        """rc_emergent: I [n_lambda][n_rays] (and the contribution map) along device rays [n][4]."""
+        import torch
+        nl = chi.shape[0]
+        shape = (nl, self.nz, self.nx)
+        n = rays.shape[0]
+        I = torch.empty((nl, n), dtype=torch.float32, device=chi.device)
+        C = torch.zeros(shape, dtype=torch.float32, device=chi.device) if want_contrib else None
+        check(load().rc_emergent(self._h, _dev_ptr(chi, "chi", shape), _dev_ptr(eta, "eta", shape), nl,
+                                 _dev_ptr(rays, "rays", (n, 4)), n, mu, _dev_ptr(I, "I", I.shape),
+                                 _dev_ptr(C, "contrib", shape) if C is not None else None,
+                                 _stream_ptr(stream)))
+        return (I, C) if want_contrib else I
+
+    def set_active(self, active=None, stream=None):
+        """rc_plan_set_active: device uint8 [nz][nx] mask of the active cells, or None."""
+        ptr = None
+        if active is not None:
+            ptr = _dev_ptr(active, "active", (self.nz, self.nx), "uint8")
+        check(load().rc_plan_set_active(self._h, ptr, _stream_ptr(stream)))
+
+    def active_probes(self):
+        out = (ctypes.c_longlong * self.n_cascades)()
+        check(load().rc_plan_active_probes(self._h, out))
+        return list(out)
 
     def set_lane_layout(self, lambda_block: int, lambda_per_lane: int):
         check(load().rc_plan_set_lane_layout(self._h, lambda_block, lambda_per_lane))
@@ -468,7 +506,7 @@ def nlte_solve(plan: Plan, atom: Atom, T, ne, n_atom, pops, tol: float = 1e-3,
 
 
 class Batch:
-    """rc_batch_create: fixed batch of domains, one persistent launch per cascade, CUDA graph."""
+    """rc_batch_create: fixed batch of domains, one launch per cascade, CUDA graph."""
 
     def __init__(self, plans, chis, etas, Js, autotune: bool = False):
         L = load()
@@ -546,6 +584,13 @@ class MLP:
         check(load().rc_mlp_get_params(self._h, th.ctypes.data_as(fp), mu.ctypes.data_as(fp),
                                        sd.ctypes.data_as(fp)))
         return th, mu, sd
+
+    def use_tensor_cores(self, enable: bool = True):
+        """Inference with the 64 x 64 layer on tcgen05 tensor cores (bf16 in, FP32 out)."""
+        check(load().rc_mlp_use_tensor_cores(self._h, int(enable)))
+
+    def tensor_core_status(self):
+        check(load().rc_mlp_tensor_core_status(self._h))
 
     def fit_normalization(self, X, stream=None):
         check(load().rc_mlp_fit_normalization(self._h, _dev_ptr(X, "X", (X.shape[0], 6)), X.shape[0],

@@ -215,3 +215,86 @@ def test_inclinations_host_entry_and_mali():
                                               want_alo=True)
     _assert_close(J.cpu().numpy(), J_ref, 1e-3, "mali J")
     _assert_close(alo_c.cpu().numpy(), 1.0 - alo_ref, 1e-3, "mali 1-alo")
+
+
+def _mask(nx, nz, seed=0):
+    x = np.arange(nx) + 0.5
+    z = np.arange(nz) + 0.5
+    X, Z = np.meshgrid(x, z)
+    m = (np.abs(X - 0.3 * nx) < 0.08 * nx + 1) | (np.hypot(X - 0.7 * nx, Z - 0.6 * nz) < 0.12 * nx)
+    return m
+
+
+@pytest.mark.parametrize("nx,nz,C", [(64, 64, 5), (96, 70, 6)])
+def test_sparse_matches_oracle(nx, nz, C):
+    """Sec. 3.5: flagged probes only; active cells match the oracle, inactive cells are 0, and
+    the flagged-probe counts equal the oracle's interval counts per direction."""
+    rcx = _rcx()
+    chi, eta = W.grf_fields(nx, 3, nz=nz)
+    m = _mask(nx, nz)
+    p = rcx.Plan(nx, nz, C)
+    p.set_active(torch.from_numpy(m.astype(np.uint8)).cuda())
+    J = p.formal_solve(torch.from_numpy(chi).cuda(), torch.from_numpy(eta).cuda()).cpu().numpy()
+    counts = p.active_probes()
+    for lam in range(3):
+        J_ref, rays = oracle.rc_solve_sparse(chi[lam].astype(np.float64), eta[lam].astype(np.float64),
+                                             m, C)
+        _assert_close(J[lam][None], J_ref[None], 1e-3, f"sparse lambda {lam}")
+        assert np.all(J[lam][~m] == 0.0)
+    dirs = [oracle.dirs(4, 4, i) for i in range(C)]
+    assert counts[0] == m.sum()
+    assert [int(r) // w for r, w in zip(rays, dirs)] == counts
+
+
+def test_sparse_cleared_is_dense_again():
+    rcx = _rcx()
+    chi, eta = W.grf_fields(48, 2)
+    dchi, deta = torch.from_numpy(chi).cuda(), torch.from_numpy(eta).cuda()
+    p = rcx.Plan(48, 48, 5)
+    J0 = p.formal_solve(dchi, deta).cpu().numpy()
+    p.set_active(torch.from_numpy(_mask(48, 48).astype(np.uint8)).cuda())
+    p.formal_solve(dchi, deta)
+    p.set_active(None)
+    np.testing.assert_array_equal(p.formal_solve(dchi, deta).cpu().numpy(), J0)
+
+
+def test_sparse_nlte_keeps_inactive_populations():
+    rcx = _rcx()
+    T, nH, vox = W.prominence_slab(n=48, half_width=10, blend=3, wander=3)
+    atom = rcx.Atom(W.h3_atom())
+    dT, dnH = torch.from_numpy(T).cuda(), torch.from_numpy(nH).cuda()
+    ne, na, pops = atom.lte(dT, dnH)
+    lte = pops.clone()
+    plan = rcx.Plan(48, 48, 5, voxel_size=vox)
+    active = torch.from_numpy((T < 2.5e5).astype(np.uint8)).cuda()
+    plan.set_active(active)
+    conv, it, hist = rcx.nlte_solve(plan, atom, dT, ne, na, pops, tol=1e-3, max_iter=200)
+    assert conv
+    inactive = active.cpu().numpy().ravel() == 0
+    assert inactive.any()
+    np.testing.assert_array_equal(pops.cpu().numpy()[:, inactive], lte.cpu().numpy()[:, inactive])
+
+
+@pytest.mark.parametrize("mu", [0.0, 0.5])
+def test_emergent_intensity_and_contribution_function(mu):
+    """Sec. 3.9: front-to-back long characteristics along given rays, with the contribution
+    function summed per cell."""
+    rcx = _rcx()
+    chi, eta = W.grf_fields(64, 5, nz=48)
+    rng = np.random.default_rng(5)
+    th = 0.3
+    rays = [(x + 0.5, -0.5, np.sin(th), np.cos(th)) for x in range(-10, 64)]
+    for _ in range(40):
+        a = rng.uniform(0, 2 * np.pi)
+        rays.append((rng.uniform(-4, 68), rng.uniform(-4, 52), np.cos(a), np.sin(a)))
+    rays = np.array(rays, dtype=np.float32)
+    p = rcx.Plan(64, 48, 3)
+    I, C = p.emergent(torch.from_numpy(chi).cuda(), torch.from_numpy(eta).cuda(),
+                      torch.from_numpy(rays).cuda(), mu=mu, want_contrib=True)
+    I, C = I.cpu().numpy(), C.cpu().numpy()
+    for lam in range(5):
+        I_ref, C_ref = oracle.emergent(chi[lam].astype(np.float64), eta[lam].astype(np.float64),
+                                       rays.astype(np.float64), mu=mu, want_contrib=True)
+        _assert_close(I[lam][None, None], I_ref[None, None], 1e-3, f"I lambda {lam}")
+        _assert_close(C[lam][None], C_ref[None], 2e-3, f"contribution lambda {lam}")
+        assert C[lam].sum() == pytest.approx(I[lam].sum(), rel=1e-4)

@@ -82,8 +82,8 @@ def test_grf_256_seven_cascades():
     _assert_close(alo, alo_ref, 1e-5, "alo grf 256")
 
 
-@pytest.mark.parametrize("lb,vl", [(1, 1), (2, 2), (4, 1), (4, 4), (8, 4), (16, 2), (16, 4),
-                                   (32, 1), (32, 4)])
+@pytest.mark.parametrize("lb,vl", [(1, 1), (2, 2), (4, 1), (4, 4), (8, 4), (8, 8), (16, 2),
+                                   (16, 4), (16, 8), (32, 1), (32, 4), (32, 8)])
 def test_lane_layouts_agree(lb, vl):
     """Every lane layout (wavelengths per ray, per lane) computes each (ray, wavelength)
     with the same arithmetic, so the results are identical."""

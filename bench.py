@@ -88,17 +88,30 @@ def _kernel_hash():
     return h.hexdigest()[:16]
 
 
-def _ncu_traffic(kernel_hash):
-    """DRAM bytes per step of the march kernels from a committed ncu summary, if it was
-    taken on the current kernel source; else None."""
+def _ncu_summary(kernel_hash):
+    """The committed ncu summary of the march kernels, if it was taken on the current
+    kernel source; else {}."""
     p = os.path.join(ROOT, "profiles", "traffic_rc_march_1024.json")
     if not os.path.exists(p):
-        return None
+        return {}
     with open(p) as f:
         d = json.load(f)
-    if d.get("kernel_source_sha256_16") != kernel_hash:
-        return None
-    return d.get("dram_bytes_per_step_march")
+    return d if d.get("kernel_source_sha256_16") == kernel_hash else {}
+
+
+def _ncu_traffic(kernel_hash):
+    """DRAM bytes per step of the march kernels (ncu), or None."""
+    return _ncu_summary(kernel_hash).get("dram_bytes_per_step_march")
+
+
+def _issue_peak():
+    """Thread instructions per second with every issue slot busy: 4 warp instructions per
+    clock per SM x 32 lanes x SMs x the maximum SM clock.  Divided by the thread
+    instructions one wavelength-crossing takes (ncu), it bounds wavelength-crossings/s."""
+    import torch
+    props = torch.cuda.get_device_properties(torch.cuda.current_device())
+    clock_hz = 2032e6   # maximum SM clock of the B300 (nvidia-smi clocks.max.sm)
+    return props.multi_processor_count * 4 * 32 * clock_hz
 
 
 class ClockSampler:
@@ -275,6 +288,16 @@ def run_ours(args):
         levels.append({"cascade": i, "ms": round(ms, 4), "crossings_per_slice": cross["per_cascade"][i],
                        "alg_GBps": round(alg[i] / (ms / 1e3) / 1e9, 1) if ms > 0 else None})
     pack_ms = per_launch.get("pack", 0.0) / args.steps
+    # second bound: instruction issue (the march is not HBM-bound: see traffic)
+    summ = _ncu_summary(khash) if (n_side, n_lambda, n_casc) == (N_SIDE, N_LAMBDA, N_CASC) else {}
+    ipc = summ.get("issue", {}).get("thread_inst_per_lambda_crossing")
+    lam_cross = sum(cross["per_cascade"]) * n_lambda / (march_ms / 1e3)
+    roofline_issue = {"bound": "alu", "unit": "wavelength-crossings/s", "achieved": round(lam_cross, 1),
+                      "thread_inst_per_lambda_crossing": ipc,
+                      "peak": round(_issue_peak() / ipc, 1) if ipc else None,
+                      "frac": round(lam_cross * ipc / _issue_peak(), 4) if ipc else None,
+                      "peak_kind": "derived: SMs x 4 issue/clk x 32 lanes x 2032 MHz / ncu-counted "
+                                   "thread instructions per wavelength-crossing"}
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": traffic,
                 "kernel": f"cascade march (level_kernel + level0_kernel), all {n_casc} launches of a step",
@@ -307,7 +330,7 @@ def run_ours(args):
                    "parallelism": f"wavelength batches, {world} GPU(s)"},
         "probe_ray_intervals_per_s": round(value * intervals, 1),
         "voxel_crossings_per_s": round(value * cross["total"], 1),
-        "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+        "roofline": roofline, "roofline_issue": roofline_issue, "cpu_baseline": cpu, "e2e": e2e,
         "gpu_launches": launches, "clocks": clk,
     }
     print(json.dumps(line), flush=True)

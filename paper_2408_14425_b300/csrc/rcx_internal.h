@@ -182,7 +182,7 @@ struct rc_plan_s {
     size_t aux_count = 0;            // lambda blocks the smax/scale arrays hold
     int cap_lambda = 0;              // largest n_lambda the scratch holds
     // host-buffer pipeline
-    cudaStream_t s_io[2] = {nullptr, nullptr};
+    cudaStream_t s_io[3] = {nullptr, nullptr, nullptr};   // copies in, solves, copies out
     float* d_stage = nullptr;        // 2 chunks x (chi, eta, J, alo)
     size_t stage_bytes = 0;
     int last_launches = 0;

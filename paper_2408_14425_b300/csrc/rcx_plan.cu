@@ -814,11 +814,13 @@ rc_status rc_formal_solve_host(rc_plan_t p, const float* chi_h, const float* eta
     rc_status st = ensure_scratch(p, chunk);
     if (st != RC_OK) return st;
 
-    // s_io[0] carries copies in, s_io[1] the solves and copies out.  Buffer b = c % 2 is
-    // reused two chunks later, after its J has left (event done[b]).
-    cudaEvent_t loaded[2], done[2];
+    // s_io[0] carries copies in, s_io[1] the solves, s_io[2] copies out, so the copy of
+    // chunk c's J overlaps chunk c+1's solve.  Buffer b = c % 2 is reused two chunks
+    // later, after its J has left (event done[b]).
+    cudaEvent_t loaded[2], solved[2], done[2];
     for (int b = 0; b < 2; ++b) {
         cudaEventCreateWithFlags(&loaded[b], cudaEventDisableTiming);
+        cudaEventCreateWithFlags(&solved[b], cudaEventDisableTiming);
         cudaEventCreateWithFlags(&done[b], cudaEventDisableTiming);
     }
     int launches = 0;
@@ -840,15 +842,20 @@ rc_status rc_formal_solve_host(rc_plan_t p, const float* chi_h, const float* eta
         cudaStreamWaitEvent(p->s_io[1], loaded[b], 0);
         st = solve_device(p, dchi, deta, nl, dJ, dalo, p->s_io[1]);
         launches += p->last_launches;
-        cudaMemcpyAsync(J_h + (size_t)l0 * ncell, dJ, bytes, cudaMemcpyDeviceToHost, p->s_io[1]);
+        cudaEventRecord(solved[b], p->s_io[1]);
+        cudaStreamWaitEvent(p->s_io[2], solved[b], 0);
+        cudaMemcpyAsync(J_h + (size_t)l0 * ncell, dJ, bytes, cudaMemcpyDeviceToHost, p->s_io[2]);
         if (alo_h)
-            cudaMemcpyAsync(alo_h + (size_t)l0 * ncell, dalo, bytes, cudaMemcpyDeviceToHost, p->s_io[1]);
-        cudaEventRecord(done[b], p->s_io[1]);
+            cudaMemcpyAsync(alo_h + (size_t)l0 * ncell, dalo, bytes, cudaMemcpyDeviceToHost, p->s_io[2]);
+        cudaEventRecord(done[b], p->s_io[2]);
     }
-    e = cudaStreamSynchronize(p->s_io[1]);
-    cudaStreamSynchronize(p->s_io[0]);
+    e = cudaStreamSynchronize(p->s_io[2]);
+    cudaError_t e1 = cudaStreamSynchronize(p->s_io[1]);
+    cudaError_t e0 = cudaStreamSynchronize(p->s_io[0]);
+    if (e == cudaSuccess) e = e1 != cudaSuccess ? e1 : e0;
     for (int b = 0; b < 2; ++b) {
         cudaEventDestroy(loaded[b]);
+        cudaEventDestroy(solved[b]);
         cudaEventDestroy(done[b]);
     }
     p->last_launches = launches;

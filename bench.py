@@ -479,16 +479,32 @@ def run_nlte(args):
     T, nH, plan = slab(1024, 9999, 6)
     surrogate.solve(plan, atom, T, nH, max_iter=2)          # warm-up
     plain = surrogate.solve(plan, atom, T, nH, max_iter=args.nlte_max_iter)
+    net.use_tensor_cores(True)          # seed inference: 64 x 64 layer on tcgen05
     seeded = surrogate.solve(plan, atom, T, nH, net=net, max_iter=args.nlte_max_iter)
+    net.tensor_core_status()
+    # the same pair with the corona (T >= 250 kK) inactive (Sec. 3.5)
+    plan.set_active((T < 2.5e5).to(torch.uint8))
+    plain_sp = surrogate.solve(plan, atom, T, nH, max_iter=args.nlte_max_iter)
+    seeded_sp = surrogate.solve(plan, atom, T, nH, net=net, max_iter=args.nlte_max_iter)
+    act = float((T < 2.5e5).float().mean())
+    plan.set_active(None)
     diff = float(((seeded["pops"] - plain["pops"]).abs() / plain["pops"].abs()).max())
     out["heldout_1024"] = {
         "cascades": 6,
         "plain": {"iterations": plain["iterations"], "seconds": round(plain["seconds"], 3),
                   "converged": plain["converged"]},
         "seeded": {"iterations": seeded["iterations"], "seconds": round(seeded["seconds"], 3),
-                   "converged": seeded["converged"], "lte_fallback_cells": seeded["fallback"]},
+                   "converged": seeded["converged"], "lte_fallback_cells": seeded["fallback"],
+                   "inference": "tcgen05 (bf16 operands, FP32 accumulation in tensor memory)"},
         "speedup_wall": round(plain["seconds"] / seeded["seconds"], 3),
         "max_rel_population_difference": diff}
+    out["heldout_1024_sparse"] = {
+        "active_cells": round(act, 4),
+        "plain": {"iterations": plain_sp["iterations"], "seconds": round(plain_sp["seconds"], 3),
+                  "converged": plain_sp["converged"]},
+        "seeded": {"iterations": seeded_sp["iterations"], "seconds": round(seeded_sp["seconds"], 3),
+                   "converged": seeded_sp["converged"]},
+        "speedup_wall": round(plain_sp["seconds"] / seeded_sp["seconds"], 3)}
     out["training"] = {"atmospheres": args.train_atmospheres, "side": 256, "cascades": 5,
                        "data_seconds": round(t_data, 2), "mean_iterations": float(np.mean(its)),
                        "train_seconds": round(t_train, 2), "steps": args.train_steps,

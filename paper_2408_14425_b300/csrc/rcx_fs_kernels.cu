@@ -20,6 +20,8 @@
 //   * Cascade 0 folds the W_0 directions of its probe (a cell centre) into J
 //     (Eq. 1) and, optionally, the diagonal operator of Eq. 17.
 // No tensor cores: the march is a gather walk, not a contraction.
+#include <type_traits>
+
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -85,6 +87,67 @@ struct Store<__nv_bfloat16> {
         *p = __float2bfloat16_rn(v);
     }
 };
+
+// VL consecutive stored values (VL * sizeof(TS)-aligned) as floats, and back.
+template <typename TS, int VL>
+__device__ __forceinline__ void load_vec(const TS* __restrict__ p, float (&v)[VL]) {
+    if constexpr (std::is_same<TS, float>::value) {
+        if constexpr (VL == 1) {
+            v[0] = __ldg(p);
+        } else if constexpr (VL == 2) {
+            const float2 a = __ldg(reinterpret_cast<const float2*>(p));
+            v[0] = a.x;
+            v[1] = a.y;
+        } else {
+#pragma unroll
+            for (int j = 0; j < VL; j += 4) {
+                const float4 a = __ldg(reinterpret_cast<const float4*>(p + j));
+                v[j] = a.x;
+                v[j + 1] = a.y;
+                v[j + 2] = a.z;
+                v[j + 3] = a.w;
+            }
+        }
+    } else {
+        using T2 = typename std::conditional<std::is_same<TS, __half>::value, __half2,
+                                             __nv_bfloat162>::type;
+        if constexpr (VL == 1) {
+            v[0] = (float)p[0];
+        } else {
+            // VL / 2 pairs in one load of VL * 2 bytes
+            T2 h[VL / 2];
+            if constexpr (VL == 2) *reinterpret_cast<unsigned*>(h) = __ldg(reinterpret_cast<const unsigned*>(p));
+            if constexpr (VL == 4) *reinterpret_cast<uint2*>(h) = __ldg(reinterpret_cast<const uint2*>(p));
+            if constexpr (VL == 8) *reinterpret_cast<uint4*>(h) = __ldg(reinterpret_cast<const uint4*>(p));
+#pragma unroll
+            for (int j = 0; j < VL / 2; ++j) {
+                const float2 f = std::is_same<TS, __half>::value
+                                     ? __half22float2(*reinterpret_cast<__half2*>(&h[j]))
+                                     : __bfloat1622float2(*reinterpret_cast<__nv_bfloat162*>(&h[j]));
+                v[2 * j] = f.x;
+                v[2 * j + 1] = f.y;
+            }
+        }
+    }
+}
+
+template <typename TS, int VL>
+__device__ __forceinline__ void store_vec(TS* __restrict__ p, const float (&v)[VL]) {
+    if constexpr (std::is_same<TS, float>::value) {
+        if constexpr (VL == 1) {
+            p[0] = v[0];
+        } else if constexpr (VL == 2) {
+            *reinterpret_cast<float2*>(p) = make_float2(v[0], v[1]);
+        } else {
+#pragma unroll
+            for (int j = 0; j < VL; j += 4)
+                *reinterpret_cast<float4*>(p + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < VL; ++j) Store<TS>::store(p + j, v[j]);
+    }
+}
 
 // ---------------------------------------------------------------------------
 // one radiance interval
@@ -244,32 +307,30 @@ __device__ __forceinline__ void upper_coord(int m, int P_up, int& j0, int& j1, f
     f = u - (float)j0;
 }
 
-// Child-cone average of the four bracketing upper probes, bilinearly weighted,
-// for wavelength l of the block.
-template <int LB, typename TS>
-__device__ __forceinline__ float upper_radiance(const TS* __restrict__ Rup, long long b00,
-                                                long long b01, long long b10, long long b11,
-                                                float fx, float fz, int W, int k, int l) {
-    // children 4k..4k+3 of probe b sit at [(b W + k) LB + l][0..3]
-    const float4 c00 = Store<TS>::load4(Rup + ((size_t)(b00 * W + k) * LB + l) * 4);
-    const float4 c01 = Store<TS>::load4(Rup + ((size_t)(b01 * W + k) * LB + l) * 4);
-    const float4 c10 = Store<TS>::load4(Rup + ((size_t)(b10 * W + k) * LB + l) * 4);
-    const float4 c11 = Store<TS>::load4(Rup + ((size_t)(b11 * W + k) * LB + l) * 4);
-    const float s00 = (c00.x + c00.y) + (c00.z + c00.w);
-    const float s01 = (c01.x + c01.y) + (c01.z + c01.w);
-    const float s10 = (c10.x + c10.y) + (c10.z + c10.w);
-    const float s11 = (c11.x + c11.y) + (c11.z + c11.w);
-    const float r0 = fmaf(fx, s01 - s00, s00);
-    const float r1 = fmaf(fx, s11 - s10, s10);
-    return 0.25f * fmaf(fz, r1 - r0, r0);
-}
+// Merged intervals are stored as child-cone averages: for each probe b of a cascade and
+// each direction k of the cascade below, 1/4 sum of the probe's children 4k..4k+3 (Eq. 11
+// needs only that average), at [(b W + k) LB + l] with W the lower cascade's direction count.
+// Each stored value is read by the 16 lower probes around b, so averaging once at the
+// store saves three quarters of the merge's reads.
 
-// Child-cone average (1/4 sum of children 4k..4k+3) of one upper probe b.
-template <int LB, typename TS>
-__device__ __forceinline__ float child_average(const TS* __restrict__ Rup, long long b, int W,
-                                               int k, int l) {
-    const float4 c = Store<TS>::load4(Rup + ((size_t)(b * W + k) * LB + l) * 4);
-    return 0.25f * ((c.x + c.y) + (c.z + c.w));
+// Bilinearly weighted child averages of the four bracketing upper probes, for the lane's
+// VL wavelengths starting at l.
+template <int LB, int VL, typename TS>
+__device__ __forceinline__ void upper_radiance(const TS* __restrict__ Rup, long long b00,
+                                               long long b01, long long b10, long long b11,
+                                               float fx, float fz, int W, int k, int l,
+                                               float (&up)[VL]) {
+    float c00[VL], c01[VL], c10[VL], c11[VL];
+    load_vec<TS, VL>(Rup + (size_t)(b00 * W + k) * LB + l, c00);
+    load_vec<TS, VL>(Rup + (size_t)(b01 * W + k) * LB + l, c01);
+    load_vec<TS, VL>(Rup + (size_t)(b10 * W + k) * LB + l, c10);
+    load_vec<TS, VL>(Rup + (size_t)(b11 * W + k) * LB + l, c11);
+#pragma unroll
+    for (int j = 0; j < VL; ++j) {
+        const float r0 = fmaf(fx, c01[j] - c00[j], c00[j]);
+        const float r1 = fmaf(fx, c11[j] - c10[j], c10[j]);
+        up[j] = fmaf(fz, r1 - r0, r0);
+    }
 }
 
 // The bilinear fix (Sec. 2.5) for the ray of probe (px, pz) in direction d starting at
@@ -311,11 +372,10 @@ __device__ __forceinline__ void fixed_rays(const LevelArgs& A, const float2* __r
                 }
             }
             const long long b = (long long)jz[q] * A.Px_up + jx[r];
+            float up[VL];
+            load_vec<TS, VL>(Rup + (size_t)(b * A.W + k) * LB + lane_off, up);
 #pragma unroll
-            for (int j = 0; j < VL; ++j) {
-                const float up = child_average<LB, TS>(Rup, b, A.W, k, lane_off + j) * sc;
-                R[j] = fmaf(w, fmaf(T[j], up, I[j]), R[j]);
-            }
+            for (int j = 0; j < VL; ++j) R[j] = fmaf(w, fmaf(T[j], up[j] * sc, I[j]), R[j]);
         }
 }
 
@@ -336,7 +396,9 @@ struct Bilinear {
 // ---------------------------------------------------------------------------
 // cascades >= 1: march + merge, store the merged interval
 // ---------------------------------------------------------------------------
-// One CTA-sized chunk `cta` of the rays of lambda block `lb` of one cascade.
+// One CTA-sized chunk `cta` of the rays of lambda block `lb` of one cascade.  The four
+// rays 4m..4m+3 of a probe (consecutive directions: the children of direction m of the
+// cascade below) are summed across their lane groups and stored once as their average.
 template <int LB, int VL, typename TS, bool HAS_UP, bool FIX = false>
 __device__ __forceinline__ void level_body(const LevelArgs& A, int lb, long long cta) {
     constexpr int LPR = LB / VL;   // lanes per ray
@@ -345,55 +407,86 @@ __device__ __forceinline__ void level_body(const LevelArgs& A, int lb, long long
     const int g = lane / LPR, q = lane % LPR;
     const long long wid = cta * kWarpsPerCta + (threadIdx.x >> 5);
     const long long ray = wid * G + g;
-    if (ray >= A.rays) return;
-
-    int k;
-    long long probe;
-    if (A.Wshift >= 0) {
-        k = (int)(ray & (A.W - 1));
-        probe = ray >> A.Wshift;
-    } else {
-        k = (int)(ray % A.W);
-        probe = ray / A.W;
-    }
-    if (A.probe_list) probe = A.probe_list[probe];   // sparse: the flagged probes only
-    const long long sray = probe * A.W + k;           // the ray's slot in the merged storage
-    const int px = (int)(probe % A.Px), pz = (int)(probe / A.Px);
-    const float2 d = A.dirs[k];
-    const float ox = ((float)px + 0.5f) * A.spacing, oz = ((float)pz + 0.5f) * A.spacing;
-    const float2* F = A.field + (size_t)lb * A.ncell * LB;
     const int lane_off = q * VL;
-    const unsigned off_hi = (unsigned)((A.ncell - 1) * LB + lane_off);
+    // ray counts of cascades >= 1 are multiples of 4, so a group of four is valid or not as a
+    // whole; invalid lanes still take part in the group sum below
+    const bool valid = ray < A.rays;
 
     float R[VL];
-    if constexpr (FIX && HAS_UP) {
-        const TS* Rup = reinterpret_cast<const TS*>(A.R_up) + (size_t)lb * A.R_up_lstride;
-        fixed_rays<LB, VL, TS>(A, F, Rup, A.scale ? A.scale[lb] : 1.0f, px, pz, ox, oz, d, k,
-                               lane_off, off_hi, R);
-    } else {
-    float I[VL], T[VL], I0[VL];
-    march_interval<LB, VL>(F, A.nx, A.nz, ox, oz, d.x, d.y, A.a, A.b, lane_off, off_hi,
-                           A.max_steps, I, T, I0);
-    if (HAS_UP) {
-        const TS* Rup = reinterpret_cast<const TS*>(A.R_up) + (size_t)lb * A.R_up_lstride;
-        const Bilinear bl(px, pz, A.Px_up, A.Pz_up);
-        const float sc = A.scale ? A.scale[lb] : 1.0f;
+    long long sray = 0;            // the ray's slot in the merged storage
+#pragma unroll
+    for (int j = 0; j < VL; ++j) R[j] = 0.0f;
+    if (valid) {
+        int k;
+        long long probe;
+        if (A.Wshift >= 0) {
+            k = (int)(ray & (A.W - 1));
+            probe = ray >> A.Wshift;
+        } else {
+            k = (int)(ray % A.W);
+            probe = ray / A.W;
+        }
+        if (A.probe_list) probe = A.probe_list[probe];   // sparse: the flagged probes only
+        sray = probe * A.W + k;
+        const int px = (int)(probe % A.Px), pz = (int)(probe / A.Px);
+        const float2 d = A.dirs[k];
+        const float ox = ((float)px + 0.5f) * A.spacing, oz = ((float)pz + 0.5f) * A.spacing;
+        const float2* F = A.field + (size_t)lb * A.ncell * LB;
+        const unsigned off_hi = (unsigned)((A.ncell - 1) * LB + lane_off);
+
+        if constexpr (FIX && HAS_UP) {
+            const TS* Rup = reinterpret_cast<const TS*>(A.R_up) + (size_t)lb * A.R_up_lstride;
+            fixed_rays<LB, VL, TS>(A, F, Rup, A.scale ? A.scale[lb] : 1.0f, px, pz, ox, oz, d, k,
+                                   lane_off, off_hi, R);
+        } else {
+            float I[VL], T[VL], I0[VL];
+            march_interval<LB, VL>(F, A.nx, A.nz, ox, oz, d.x, d.y, A.a, A.b, lane_off, off_hi,
+                                   A.max_steps, I, T, I0);
+            if (HAS_UP) {
+                const TS* Rup = reinterpret_cast<const TS*>(A.R_up) + (size_t)lb * A.R_up_lstride;
+                const Bilinear bl(px, pz, A.Px_up, A.Pz_up);
+                const float sc = A.scale ? A.scale[lb] : 1.0f;
+                float up[VL];
+                upper_radiance<LB, VL, TS>(Rup, bl.b00, bl.b01, bl.b10, bl.b11, bl.fx, bl.fz, A.W,
+                                           k, lane_off, up);
+#pragma unroll
+                for (int j = 0; j < VL; ++j) R[j] = fmaf(T[j], up[j] * sc, I[j]);
+            } else {
+#pragma unroll
+                for (int j = 0; j < VL; ++j) R[j] = I[j];
+            }
+        }
+    }
+    // sum over the group of four rays: its lane groups are LPR lanes apart within a warp,
+    // or (more than 8 lanes per ray) spread over consecutive warps of the CTA
+    bool leader;
+    if constexpr (G >= 4) {
 #pragma unroll
         for (int j = 0; j < VL; ++j) {
-            const float up = upper_radiance<LB, TS>(Rup, bl.b00, bl.b01, bl.b10, bl.b11, bl.fx,
-                                                    bl.fz, A.W, k, lane_off + j);
-            R[j] = fmaf(T[j], up * sc, I[j]);
+            R[j] += __shfl_xor_sync(0xffffffffu, R[j], LPR);
+            R[j] += __shfl_xor_sync(0xffffffffu, R[j], 2 * LPR);
         }
+        leader = (g & 3) == 0;
     } else {
+        __shared__ float sR[kWarpsPerCta * 32 * VL];
 #pragma unroll
-        for (int j = 0; j < VL; ++j) R[j] = I[j];
-    }
-    }
-    TS* out = reinterpret_cast<TS*>(A.R_out) + (size_t)lb * A.R_out_lstride;
-    const float inv = A.scale ? 1.0f / A.scale[lb] : 1.0f;
+        for (int j = 0; j < VL; ++j) sR[threadIdx.x * VL + j] = R[j];
+        __syncthreads();
+        const int rc = (int)threadIdx.x / LPR;          // ray within the CTA
+        leader = (rc & 3) == 0;
+        if (leader)
 #pragma unroll
-    for (int j = 0; j < VL; ++j)
-        Store<TS>::store(out + ((size_t)(sray >> 2) * LB + lane_off + j) * 4 + (sray & 3), R[j] * inv);
+            for (int j = 0; j < VL; ++j)
+                R[j] = (sR[threadIdx.x * VL + j] + sR[(threadIdx.x + LPR) * VL + j]) +
+                       (sR[(threadIdx.x + 2 * LPR) * VL + j] + sR[(threadIdx.x + 3 * LPR) * VL + j]);
+    }
+    if (valid && leader) {
+        TS* out = reinterpret_cast<TS*>(A.R_out) + (size_t)lb * A.R_out_lstride;
+        const float inv = 0.25f * (A.scale ? 1.0f / A.scale[lb] : 1.0f);
+#pragma unroll
+        for (int j = 0; j < VL; ++j) R[j] *= inv;
+        store_vec<TS, VL>(out + (size_t)(sray >> 2) * LB + lane_off, R);
+    }
 }
 
 template <int LB, int VL, typename TS, bool HAS_UP, bool FIX>
@@ -451,14 +544,14 @@ __device__ __forceinline__ void level0_body(const LevelArgs& A, int lb, long lon
         march_interval<LB, VL, true>(F, A.nx, A.nz, ox, oz, d.x, d.y, A.a, A.b, lane_off,
                                      off_hi, A.max_steps, I, T, I0);
         const float dk = 0.5f / fmaxf(fabsf(d.x), fabsf(d.y));
+        float up[VL];
+        if (HAS_UP)
+            upper_radiance<LB, VL, TS>(Rup, bl.b00, bl.b01, bl.b10, bl.b11, bl.fx, bl.fz, A.W, k,
+                                       lane_off, up);
 #pragma unroll
         for (int j = 0; j < VL; ++j) {
             float Rnl = I[j];
-            if (HAS_UP) {
-                const float up = upper_radiance<LB, TS>(Rup, bl.b00, bl.b01, bl.b10, bl.b11, bl.fx,
-                                                        bl.fz, A.W, k, lane_off + j);
-                Rnl = fmaf(T[j], up * sc, I[j]);
-            }
+            if (HAS_UP) Rnl = fmaf(T[j], up[j] * sc, I[j]);
             Jsum[j] += Rnl + I0[j];
             Jeff[j] += Rnl;
             const float y = own.v[j].x * dk;

@@ -106,7 +106,7 @@ extern "C" rc_status rc_formal_solve_noalloc(const rc_grid* grid, int n_cascades
     }
     const size_t dirs_bytes = align256((size_t)n_dirs * sizeof(float2));
     const size_t packed_bytes = align256((size_t)n_lblk * ncell * LB * sizeof(float2));
-    const size_t R_bytes = align256((size_t)n_lblk * (size_t)max_rays * LB * sizeof(float));
+    const size_t R_bytes = align256((size_t)n_lblk * (size_t)(max_rays / 4) * LB * sizeof(float));
     const size_t need = dirs_bytes + packed_bytes + 2 * R_bytes;
     if (need > kNoallocScratchBytes)
         return nfail(RC_ERR_ARG, "rc_formal_solve_noalloc: this problem needs " +
@@ -163,11 +163,11 @@ extern "C" rc_status rc_formal_solve_noalloc(const rc_grid* grid, int n_cascades
             a.R_up = R[(i + 1) & 1];
             a.Px_up = lv[i + 1].Px;
             a.Pz_up = lv[i + 1].Pz;
-            a.R_up_lstride = lv[i + 1].rays() * LB;
+            a.R_up_lstride = lv[i + 1].rays() / 4 * LB;   // child averages
         }
         if (i > 0) {
             a.R_out = R[i & 1];
-            a.R_out_lstride = lv[i].rays() * LB;
+            a.R_out_lstride = lv[i].rays() / 4 * LB;
         }
         a.J = J;
         a.alo = alo;

@@ -131,7 +131,8 @@ rc_status ensure_scratch(rc_plan_s* p, int n_lambda) {
     long long max_rays = 0;
     for (size_t i = 1; i < p->lv.size(); ++i) max_rays = std::max(max_rays, p->lv[i].rays());
     const size_t packed = n_lblk * ncell * LB * sizeof(float2);
-    const size_t Rb = std::max<size_t>(1, n_lblk * (size_t)max_rays * LB *
+    // merged intervals hold one child average per 4 rays
+    const size_t Rb = std::max<size_t>(1, n_lblk * (size_t)(max_rays / 4) * LB *
                                               storage_bytes(p->opt.precision));
     cudaDeviceSynchronize();  // scratch may be in use by work still queued
     free_scratch(p);
@@ -154,6 +155,32 @@ rc_status ensure_scratch(rc_plan_s* p, int n_lambda) {
 }
 
 // The launch sequence of one solve on device buffers.
+// Cascades whose merged intervals are identically zero need no launch: an interval that
+// starts beyond the farthest box corner from every probe of its cascade lies entirely in
+// free space (I = 0, T = 1, nothing enters: Sec. 3.4), so its R is the merged R of the
+// cascade above, and the top cascade's is 0.  Returns the number of cascades from 0 up to
+// the highest one that can be non-zero (always >= 1: cascade-0 intervals start at the
+// probe).  The bilinear fix retraces to the upper probes, so it keeps every cascade.
+int live_cascades(const rc_plan_s* p) {
+    if (p->opt.bilinear_fix) return p->C;
+    int live = p->C;
+    while (live > 1) {
+        const rcx::LevelGeom& g = p->lv[live - 1];
+        const double sp = std::ldexp(1.0, live - 1);
+        double far2 = 0.0;   // squared distance from the extreme probes to the farthest corner
+        for (int kx : {0, g.Px - 1})
+            for (int kz : {0, g.Pz - 1}) {
+                const double x = (kx + 0.5) * sp, z = (kz + 0.5) * sp;
+                const double dx = std::max(x, p->nx - x), dz = std::max(z, p->nz - z);
+                far2 = std::max(far2, dx * dx + dz * dz);
+            }
+        const double far = std::sqrt(far2);
+        if (!(g.a > far * (1.0 + 1e-6) + 1e-3)) break;
+        --live;
+    }
+    return live;
+}
+
 rc_status solve_device(rc_plan_s* p, const float* chi, const float* eta, int n_lambda,
                        float* J, float* alo, cudaStream_t s, float* J_eff = nullptr,
                        float* alo_c = nullptr) {
@@ -233,10 +260,10 @@ rc_status solve_device(rc_plan_s* p, const float* chi, const float* eta, int n_l
         mark("scale");
     }
 
-    const int C = p->C;
-    for (int i = C - 1; i >= 0; --i) {
+    const int live = live_cascades(p);
+    for (int i = live - 1; i >= 0; --i) {
         const rcx::LevelArgs a = rcx::level_args(p, i, n_lambda, Jv, alov, Jeffv, alocv);
-        const bool has_up = i < C - 1;
+        const bool has_up = i < live - 1;
         if ((e = rcx::launch_level(LB, p->VL, p->opt.precision, i == 0, has_up, n_lblk, a, s)) !=
             cudaSuccess)
             return cuda_fail(e, "cascade launch");
@@ -294,11 +321,11 @@ rcx::LevelArgs rcx::level_args(const rc_plan_s* p, int i, int n_lambda, float* J
         a.R_up = p->d_R[(i + 1) & 1];
         a.Px_up = u.Px;
         a.Pz_up = u.Pz;
-        a.R_up_lstride = u.rays() * LB;
+        a.R_up_lstride = u.rays() / 4 * LB;       // child averages: one per 4 rays
     }
     if (i > 0) {
         a.R_out = p->d_R[i & 1];
-        a.R_out_lstride = g.rays() * LB;
+        a.R_out_lstride = g.rays() / 4 * LB;
     }
     a.scale = p->opt.precision != RC_STORE_F32 ? p->d_scale : nullptr;
     a.J = J;

@@ -298,3 +298,22 @@ def test_emergent_intensity_and_contribution_function(mu):
         _assert_close(I[lam][None, None], I_ref[None, None], 1e-3, f"I lambda {lam}")
         _assert_close(C[lam][None], C_ref[None], 2e-3, f"contribution lambda {lam}")
         assert C[lam].sum() == pytest.approx(I[lam].sum(), rel=1e-4)
+
+
+@pytest.mark.parametrize("n,C,launched", [(64, 5, 4), (64, 7, 4), (1024, 8, 7), (100, 4, 4)])
+def test_free_space_cascades_are_not_launched(n, C, launched):
+    """Sec. 3.4: an interval beyond the farthest box corner from every probe of its cascade
+    lies in free space, so top cascades whose intervals all do are identically zero and are
+    not launched; the results still match the oracle, which marches them.
+    64^2: cascade 4 starts at 85 > 79.2 (probe (8, 8) to corner (64, 64)), cascades 5-6
+    further out; cascade 3 starts at 21 < 84.9.  1024^2: cascade 7 starts at 5461 > 1357.6,
+    cascade 6 at 1365 < 1402.9.  100^2: cascade 3 starts at 21 < 135.8."""
+    rcx = _rcx()
+    p = rcx.Plan(n, n, C)
+    chi, eta = W.grf_fields(n, 1 if n > 100 else 2)
+    dchi, deta = torch.from_numpy(chi).cuda(), torch.from_numpy(eta).cuda()
+    J = p.formal_solve(dchi, deta)
+    torch.cuda.synchronize()
+    assert p.last_launch_count() == 1 + launched      # pack + live cascades
+    if n <= 100:
+        _assert_close(J.cpu().numpy(), _oracle(chi, eta, C), 1e-3, f"{n} C{C}")

@@ -71,7 +71,15 @@ typedef struct {
                             not the MALI outputs or batches); 0 = basic RC */
     int lambda_per_lane; /* wavelengths one GPU lane carries along its ray: 0 = default
                             (min(lambda_block, 4)); 1, 2, 4 or 8, at most lambda_block */
-    int reserved[2];     /* must be zero */
+    int strips;          /* strip-split march of long-ray cascades: 0 = automatic (a cascade
+                            whose intervals reach half the domain, when one wavelength block
+                            of the packed field exceeds 96 MiB, runs as one launch per
+                            vertical strip of about 64 MiB per wavelength block, so each
+                            launch gathers from a strip that stays in L2); 1 = never; 2..16 =
+                            that many strips on every cascade >= 1.  Results agree with the
+                            unsplit march to FP32 rounding.  Not with the bilinear fix; lane
+                            layouts with 4 wavelengths per lane and 8-32 per ray. */
+    int reserved;        /* must be zero */
 } rc_options;
 
 /* Fills *opt with the defaults (F32 storage, flatland, rule 0, automatic lane layout, basic RC). */
@@ -120,7 +128,9 @@ size_t rc_plan_scratch_bytes(rc_plan_t plan);
  * Each interval is marched through the voxels it crosses with Eq. 16 (FP32), merged with
  * the child-cone average of the bilinearly interpolated upper cascade (Sec. 2.3.1, Eq. 11,
  * the nearer interval attenuating the farther), with the lookup clamped at the edges
- * (Sec. 2.5); outside the domain there is free space (Sec. 3.4).
+ * (Sec. 2.5); outside the domain there is free space (Sec. 3.4).  Top cascades whose
+ * intervals all start beyond the farthest domain corner from each of their probes are
+ * identically zero and are not launched (without the bilinear fix).
  * Opacities below 1e-30 per voxel are raised to 1e-30 (the emission eta ds of such a cell is
  * kept).  Asynchronous on `stream`; may allocate scratch on first use (see rc_plan_reserve).
  * Errors: RC_ERR_ARG (NULL pointers, n_lambda < 0), RC_ERR_OOM, RC_ERR_CUDA.
@@ -131,7 +141,8 @@ rc_status rc_formal_solve(rc_plan_t plan, const float* chi, const float* eta, in
 /*
  * rc_formal_solve_host -- as rc_formal_solve, with chi, eta, J (and alo) in HOST memory.
  * The wavelengths are processed in chunks; each chunk's host-to-device copies, solve and
- * device-to-host copy of J are pipelined on two internal streams.  Pinned host buffers
+ * device-to-host copy of J run on three internal streams, so a chunk's copies overlap its
+ * neighbours' solves.  Pinned host buffers
  * copy fastest.  Synchronous: returns when J is in host memory.
  * Errors: as rc_formal_solve.
  */

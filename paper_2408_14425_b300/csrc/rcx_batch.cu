@@ -89,6 +89,7 @@ rc_status build(rc_batch_s* b, bool first_block_only = false) {
         for (int d = 0; d < n; ++d) {
             rc_plan_s* p = b->plans[d];
             args[(size_t)i * n + d] = rcx::level_args(p, i, b->nl[d], b->J[d], nullptr, nullptr, nullptr);
+            if (rcx::strips_for(p, i) > 1) continue;   // launched strip by strip after the batch
             const long long items = i == 0 ? (long long)p->nx * p->nz : p->lv[i].rays();
             const long long chunks = (items + G_rays - 1) / G_rays;
             const double diag = std::sqrt((double)p->nx * p->nx + (double)p->nz * p->nz);
@@ -181,9 +182,30 @@ rc_status build(rc_batch_s* b, bool first_block_only = false) {
             rc_plan_s* p = b->plans[d];
             le = rcx::launch_scales((b->nl[d] + LB - 1) / LB, p->d_smax, p->d_scale, b->cap);
         }
-    for (int i = C - 1; i >= 0 && le == cudaSuccess; --i, ++launches)
-        le = rcx::launch_batched_level(LB, b->VL, b->precision, i == 0, i < C - 1, b->level[i],
-                                       b->grid[i], b->cap, nullptr);
+    for (int i = C - 1; i >= 0 && le == cudaSuccess; --i) {
+        if (b->level[i].total > 0) {
+            le = rcx::launch_batched_level(LB, b->VL, b->precision, i == 0, i < C - 1, b->level[i],
+                                           b->grid[i], b->cap, nullptr);
+            ++launches;
+        }
+        // domains whose cascade i is strip-split (large fields, long intervals): one launch
+        // per wavelength block and strip, as in rc_formal_solve
+        for (int d = 0; d < n && le == cudaSuccess; ++d) {
+            rc_plan_s* p = b->plans[d];
+            const int S = rcx::strips_for(p, i);
+            if (S < 2) continue;
+            rcx::LevelArgs a = args[(size_t)i * n + d];
+            a.it_state = p->d_it;
+            a.n_strips = S;
+            const int n_lblk = first_block_only ? 1 : (b->nl[d] + LB - 1) / LB;
+            for (int lb = 0; lb < n_lblk && le == cudaSuccess; ++lb)
+                for (int ph = 0; ph < S && le == cudaSuccess; ++ph, ++launches) {
+                    a.split_lb = lb;
+                    a.phase = ph;
+                    le = rcx::launch_level_split(LB, b->VL, b->precision, i < C - 1, a, b->cap);
+                }
+        }
+    }
     e = cudaStreamEndCapture(b->cap, &b->graph);
     if (le != cudaSuccess) return bcuda(le, "rc_batch: launch during capture");
     if (e != cudaSuccess) return bcuda(e, "rc_batch: end capture");

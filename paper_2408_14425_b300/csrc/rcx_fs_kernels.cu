@@ -212,9 +212,11 @@ struct Voxel {
 // With SPLIT_FIRST the emission of the first piece (for a cascade-0 ray: the probe's
 // own cell from its centre to its edge) goes to I0 instead of I.  With CONTRIB every
 // piece's contribution T S (1 - e^{-dtau}) is also added to contrib[j * ncell + cell] for the
-// lane's first n_valid wavelengths (the contribution function of Sec. 3.9).
+// lane's first n_valid wavelengths (the contribution function of Sec. 3.9).  Returns false
+// when the interval misses the box (I = 0, T = 1).
 template <int LB, int VL, bool SPLIT_FIRST = false, bool CONTRIB = false>
-__device__ __forceinline__ void march_interval(const float2* __restrict__ F, int nx, int nz,
+__device__ __forceinline__ bool march_interval(const float2* __restrict__ F, int nx, int nz,
+                                               int x0, int x1,
                                                float ox, float oz, float wx, float wz,
                                                float a, float b, int lane_off,
                                                unsigned off_hi, int max_steps,
@@ -229,18 +231,19 @@ __device__ __forceinline__ void march_interval(const float2* __restrict__ F, int
     }
     const float invx = wx != 0.0f ? 1.0f / wx : 1e30f;
     const float invz = wz != 0.0f ? 1.0f / wz : 1e30f;
-    // entry into the domain box (free space outside, Sec. 3.4)
-    const float tx0 = (0.0f - ox) * invx, tx1 = ((float)nx - ox) * invx;
+    // entry into the box [x0, x1] x [0, nz] (the domain, or a strip of it; free space
+    // outside the domain, Sec. 3.4); nx is the row stride of the field
+    const float tx0 = ((float)x0 - ox) * invx, tx1 = ((float)x1 - ox) * invx;
     const float tz0 = (0.0f - oz) * invz, tz1 = ((float)nz - oz) * invz;
     const float tlo = fmaxf(a, fmaxf(fminf(tx0, tx1), fminf(tz0, tz1)));
-    if (!(tlo < fminf(b, fminf(fmaxf(tx0, tx1), fmaxf(tz0, tz1))))) return;
+    if (!(tlo < fminf(b, fminf(fmaxf(tx0, tx1), fmaxf(tz0, tz1))))) return false;
 
     const bool upx = wx > 0.0f, upz = wz > 0.0f;
     const float ex = ox + tlo * wx, ez = oz + tlo * wz;
     int ix = (int)floorf(ex), iz = (int)floorf(ez);
     if (!upx && (float)ix == ex) --ix;   // entering through a face while moving down
     if (!upz && (float)iz == ez) --iz;
-    ix = min(max(ix, 0), nx - 1);
+    ix = min(max(ix, x0), x1 - 1);
     iz = min(max(iz, 0), nz - 1);
 
     // face parameters: first face after entry and spacing between faces
@@ -248,7 +251,7 @@ __device__ __forceinline__ void march_interval(const float2* __restrict__ F, int
     const float tfx = (fx0 - ox) * invx, tfz = (fz0 - oz) * invz;
     const float dtx = fabsf(invx), dtz = fabsf(invz);
     // exit: last face inside the domain, with the same expression as the walk
-    const float kx_end = (float)(upx ? nx - 1 - ix : ix);
+    const float kx_end = (float)(upx ? x1 - 1 - ix : ix - x0);
     const float kz_end = (float)(upz ? nz - 1 - iz : iz);
     const float thi = fminf(b, fminf(fmaf(kx_end, dtx, tfx), fmaf(kz_end, dtz, tfz)));
 
@@ -295,6 +298,7 @@ __device__ __forceinline__ void march_interval(const float2* __restrict__ F, int
         cur = nxt;
         t = tn;
     }
+    return true;
 }
 
 // Clamped bilinear coordinate of a cascade-i probe index m in the index space
@@ -362,7 +366,7 @@ __device__ __forceinline__ void fixed_rays(const LevelArgs& A, const float2* __r
             float I[VL], T[VL], I0[VL];
             if (L > 0.0f) {
                 const float iL = 1.0f / L;
-                march_interval<LB, VL>(F, A.nx, A.nz, Ax, Az, dx * iL, dz * iL, 0.0f, L,
+                march_interval<LB, VL>(F, A.nx, A.nz, 0, A.nx, Ax, Az, dx * iL, dz * iL, 0.0f, L,
                                        lane_off, off_hi, A.max_steps, I, T, I0);
             } else {
 #pragma unroll
@@ -396,6 +400,10 @@ struct Bilinear {
 // ---------------------------------------------------------------------------
 // cascades >= 1: march + merge, store the merged interval
 // ---------------------------------------------------------------------------
+template <int LB, int VL, typename TS>
+__device__ __forceinline__ void store_child_average(const LevelArgs& A, int lb, bool valid,
+                                                    long long sray, int lane_off, float (&R)[VL]);
+
 // One CTA-sized chunk `cta` of the rays of lambda block `lb` of one cascade.  The four
 // rays 4m..4m+3 of a probe (consecutive directions: the children of direction m of the
 // cascade below) are summed across their lane groups and stored once as their average.
@@ -440,7 +448,7 @@ __device__ __forceinline__ void level_body(const LevelArgs& A, int lb, long long
                                    lane_off, off_hi, R);
         } else {
             float I[VL], T[VL], I0[VL];
-            march_interval<LB, VL>(F, A.nx, A.nz, ox, oz, d.x, d.y, A.a, A.b, lane_off, off_hi,
+            march_interval<LB, VL>(F, A.nx, A.nz, 0, A.nx, ox, oz, d.x, d.y, A.a, A.b, lane_off, off_hi,
                                    A.max_steps, I, T, I0);
             if (HAS_UP) {
                 const TS* Rup = reinterpret_cast<const TS*>(A.R_up) + (size_t)lb * A.R_up_lstride;
@@ -457,8 +465,19 @@ __device__ __forceinline__ void level_body(const LevelArgs& A, int lb, long long
             }
         }
     }
-    // sum over the group of four rays: its lane groups are LPR lanes apart within a warp,
-    // or (more than 8 lanes per ray) spread over consecutive warps of the CTA
+    store_child_average<LB, VL, TS>(A, lb, valid, sray, lane_off, R);
+}
+
+// The group of four sibling rays (consecutive directions of one probe) is summed across
+// its lane groups -- LPR lanes apart within a warp, or (more than 8 lanes per ray) spread
+// over consecutive warps of the CTA -- and its leader stores the average.  Every thread
+// of the CTA calls this.
+template <int LB, int VL, typename TS>
+__device__ __forceinline__ void store_child_average(const LevelArgs& A, int lb, bool valid,
+                                                    long long sray, int lane_off, float (&R)[VL]) {
+    constexpr int LPR = LB / VL;
+    constexpr int G = 32 / LPR;
+    const int g = (threadIdx.x & 31) / LPR;
     bool leader;
     if constexpr (G >= 4) {
 #pragma unroll
@@ -493,6 +512,87 @@ template <int LB, int VL, typename TS, bool HAS_UP, bool FIX>
 __global__ void __launch_bounds__(kWarpsPerCta * 32, min_ctas<VL>())
 level_kernel(const LevelArgs A) {
     level_body<LB, VL, TS, HAS_UP, FIX>(A, blockIdx.y, blockIdx.x);
+}
+
+// ---------------------------------------------------------------------------
+// strip-split cascade: when a cascade's rays are long and one lambda block of the field
+// does not fit in L2, the domain is cut into n_strips vertical strips and the cascade runs
+// as n_strips launches.  Launch p marches, for every ray, only its piece inside strip p, so
+// each launch gathers from one strip.  The pieces compose associatively (Eq. 11 applied to
+// adjacent pieces): a ray moving to +x meets the strips front to back, I <- I + T I_p,
+// T <- T T_p; a ray moving to -x meets them back to front, I <- I_p + T_p I, T <- T_p T.
+// The partial (I, T) is kept in it_state between launches; the last launch merges with the
+// upper cascade and stores the child averages.
+// ---------------------------------------------------------------------------
+template <int LB, int VL, typename TS, bool HAS_UP>
+__global__ void __launch_bounds__(kWarpsPerCta * 32, min_ctas<VL>())
+level_split_kernel(const LevelArgs A) {
+    constexpr int LPR = LB / VL;
+    constexpr int G = 32 / LPR;
+    const int lane = threadIdx.x & 31;
+    const int g = lane / LPR, q = lane % LPR;
+    const long long ray = ((long long)blockIdx.x * kWarpsPerCta + (threadIdx.x >> 5)) * G + g;
+    const int lane_off = q * VL;
+    const int lb = A.split_lb;
+    const bool valid = ray < A.rays;
+    const bool first = A.phase == 0, last = A.phase == A.n_strips - 1;
+    float R[VL];
+    long long sray = 0;
+#pragma unroll
+    for (int j = 0; j < VL; ++j) R[j] = 0.0f;
+    if (valid) {
+        int k;
+        long long probe;
+        if (A.Wshift >= 0) {
+            k = (int)(ray & (A.W - 1));
+            probe = ray >> A.Wshift;
+        } else {
+            k = (int)(ray % A.W);
+            probe = ray / A.W;
+        }
+        if (A.probe_list) probe = A.probe_list[probe];
+        sray = probe * A.W + k;
+        const int px = (int)(probe % A.Px), pz = (int)(probe / A.Px);
+        const float2 d = A.dirs[k];
+        const float ox = ((float)px + 0.5f) * A.spacing, oz = ((float)pz + 0.5f) * A.spacing;
+        const float2* F = A.field + (size_t)lb * A.ncell * LB;
+        const unsigned off_hi = (unsigned)((A.ncell - 1) * LB + lane_off);
+        const int x0 = (int)((long long)A.phase * A.nx / A.n_strips);
+        const int x1 = (int)((long long)(A.phase + 1) * A.nx / A.n_strips);
+        float I[VL], T[VL], I0[VL];
+        const bool hit = march_interval<LB, VL>(F, A.nx, A.nz, x0, x1, ox, oz, d.x, d.y, A.a,
+                                                A.b, lane_off, off_hi, A.max_steps, I, T, I0);
+        float2* st = A.it_state + (size_t)ray * LB + lane_off;
+        // a ray with no piece in a middle strip leaves its partial (I, T) as it is
+        if (hit || first || last) {
+            if (!first) {
+                const bool forward = d.x >= 0.0f;   // strips met front to back
+#pragma unroll
+                for (int j = 0; j < VL; ++j) {      // the partial (I, T) of the strips before
+                    const float2 acc = st[j];
+                    I[j] = forward ? fmaf(acc.y, I[j], acc.x) : fmaf(T[j], acc.x, I[j]);
+                    T[j] *= acc.y;
+                }
+            }
+            if (!last) {
+#pragma unroll
+                for (int j = 0; j < VL; ++j) st[j] = make_float2(I[j], T[j]);
+            } else if (HAS_UP) {
+                const TS* Rup = reinterpret_cast<const TS*>(A.R_up) + (size_t)lb * A.R_up_lstride;
+                const Bilinear bl(px, pz, A.Px_up, A.Pz_up);
+                const float sc = A.scale ? A.scale[lb] : 1.0f;
+                float up[VL];
+                upper_radiance<LB, VL, TS>(Rup, bl.b00, bl.b01, bl.b10, bl.b11, bl.fx, bl.fz,
+                                           A.W, k, lane_off, up);
+#pragma unroll
+                for (int j = 0; j < VL; ++j) R[j] = fmaf(T[j], up[j] * sc, I[j]);
+            } else {
+#pragma unroll
+                for (int j = 0; j < VL; ++j) R[j] = I[j];
+            }
+        }
+    }
+    if (last) store_child_average<LB, VL, TS>(A, lb, valid, sray, lane_off, R);
 }
 
 // ---------------------------------------------------------------------------
@@ -541,7 +641,7 @@ __device__ __forceinline__ void level0_body(const LevelArgs& A, int lb, long lon
             continue;
         }
         float I[VL], T[VL], I0[VL];
-        march_interval<LB, VL, true>(F, A.nx, A.nz, ox, oz, d.x, d.y, A.a, A.b, lane_off,
+        march_interval<LB, VL, true>(F, A.nx, A.nz, 0, A.nx, ox, oz, d.x, d.y, A.a, A.b, lane_off,
                                      off_hi, A.max_steps, I, T, I0);
         const float dk = 0.5f / fmaxf(fabsf(d.x), fabsf(d.y));
         float up[VL];
@@ -637,7 +737,7 @@ emergent_kernel(const EmergentArgs A) {
     const int lam0 = lb * LB + lane_off;
     const int n_valid = max(0, min(VL, A.n_lambda - lam0));
     float I[VL], T[VL], I0[VL];
-    march_interval<LB, VL, false, CONTRIB>(F, A.nx, A.nz, r.x, r.y, r.z, r.w, 0.0f, INFINITY,
+    march_interval<LB, VL, false, CONTRIB>(F, A.nx, A.nz, 0, A.nx, r.x, r.y, r.z, r.w, 0.0f, INFINITY,
                                            lane_off, off_hi, A.max_steps, I, T, I0,
                                            CONTRIB ? A.contrib + (size_t)lam0 * A.ncell : nullptr,
                                            n_valid, A.ncell);
@@ -1002,6 +1102,42 @@ cudaError_t launch_batched_pack(int LB, const BatchPackArgs& b, int grid, cudaSt
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
+}
+
+template <int LB, typename TS>
+static cudaError_t level_split_t(bool has_up, const LevelArgs& a, cudaStream_t s) {
+    constexpr int G = 32 / (LB / 4);
+    if (a.rays == 0) return cudaSuccess;
+    const long long per_cta = (long long)G * kWarpsPerCta;
+    const dim3 grid((unsigned)((a.rays + per_cta - 1) / per_cta));
+    if (has_up) level_split_kernel<LB, 4, TS, true><<<grid, kWarpsPerCta * 32, 0, s>>>(a);
+    else level_split_kernel<LB, 4, TS, false><<<grid, kWarpsPerCta * 32, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+template <int LB>
+static cudaError_t level_split_p(int precision, bool has_up, const LevelArgs& a, cudaStream_t s) {
+    switch (precision) {
+        case RC_STORE_F32: return level_split_t<LB, float>(has_up, a, s);
+        case RC_STORE_F16: return level_split_t<LB, __half>(has_up, a, s);
+        case RC_STORE_BF16: return level_split_t<LB, __nv_bfloat16>(has_up, a, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+// The split march is instantiated for 4 wavelengths per lane and 8-32 per ray.
+bool level_split_supported(int LB, int VL) { return VL == 4 && (LB == 8 || LB == 16 || LB == 32); }
+
+cudaError_t launch_level_split(int LB, int VL, int precision, bool has_up, const LevelArgs& a,
+                               cudaStream_t s) {
+    if (!level_split_supported(LB, VL) || a.n_strips < 2 || !a.it_state)
+        return cudaErrorInvalidValue;
+    switch (LB) {
+        case 8: return level_split_p<8>(precision, has_up, a, s);
+        case 16: return level_split_p<16>(precision, has_up, a, s);
+        case 32: return level_split_p<32>(precision, has_up, a, s);
+    }
+    return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_level(int LB, int VL, int precision, bool level0, bool has_up, int n_lblk,

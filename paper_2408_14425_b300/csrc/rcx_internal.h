@@ -59,6 +59,10 @@ struct LevelArgs {
     float* alo_c;            // 1 - alo, may be NULL
     int n_lambda;
     int max_steps;           // upper bound on cells crossed by one ray (nx + nz + 2)
+    // strip-split march (launch_level_split): partial (I, T) of every ray of one lambda
+    // block [ray][LB], the strip count, this launch's phase and lambda block
+    float2* it_state;
+    int n_strips, phase, split_lb;
 };
 
 struct PackArgs {
@@ -128,6 +132,11 @@ cudaError_t launch_batched_level(int LB, int VL, int precision, bool level0, boo
                                  const BatchLevelArgs& b, int grid, cudaStream_t s, int* occ);
 cudaError_t launch_batched_pack(int LB, const BatchPackArgs& b, int grid, cudaStream_t s);
 cudaError_t launch_pack(int LB, int n_lblk, const PackArgs& a, cudaStream_t s);
+// One phase of a strip-split cascade (cascades >= 1, no bilinear fix): lambda block
+// a.split_lb, the rays' pieces inside strip a.phase (or its mirror for rays moving to -x).
+cudaError_t launch_level_split(int LB, int VL, int precision, bool has_up, const LevelArgs& a,
+                               cudaStream_t s);
+bool level_split_supported(int LB, int VL);
 cudaError_t launch_level(int LB, int VL, int precision, bool level0, bool has_up, int n_lblk,
                          const LevelArgs& a, cudaStream_t s);
 cudaError_t launch_scales(int n_lblk, const unsigned int* smax_bits, float* scale,
@@ -144,6 +153,8 @@ namespace rcx {
 LevelArgs level_args(const rc_plan_s* p, int i, int n_lambda, float* J, float* alo,
                      float* J_eff, float* alo_c);
 rc_status plan_reserve(rc_plan_s* p, int n_lambda);
+// strips of the strip-split march of cascade i of a plan (1 = not split)
+int strips_for(const rc_plan_s* p, int i);
 rc_status plan_set_layout(rc_plan_s* p, int LB, int VL);
 // Device tables of an atom's levels: E/k [K] and g (rcx_nlte.cu).
 rc_status atom_levels(rc_atom_t a, const double** Ek, const double** g, int* nlev,
@@ -174,6 +185,8 @@ struct rc_plan_s {
     float2* d_dirs = nullptr;
     // scratch
     float2* d_packed = nullptr;
+    float2* d_it = nullptr;            // partial (I, T) of a strip-split cascade, one lambda block
+    size_t it_bytes = 0;
     size_t packed_bytes = 0;
     void* d_R[2] = {nullptr, nullptr};
     size_t R_bytes = 0;              // bytes of each of the two cascade buffers

@@ -108,6 +108,9 @@ void gauss_radau(int n, std::vector<double>& mu, std::vector<double>& w) {
 
 void free_scratch(rc_plan_s* p) {
     cudaFree(p->d_packed);
+    cudaFree(p->d_it);
+    p->d_it = nullptr;
+    p->it_bytes = 0;
     cudaFree(p->d_R[0]);
     cudaFree(p->d_R[1]);
     cudaFree(p->d_smax);
@@ -122,6 +125,42 @@ void free_scratch(rc_plan_s* p) {
 }
 
 // Grows the solve scratch to hold n_lambda wavelengths.
+// Largest distance from a probe of cascade i to a domain corner (the extreme probes decide).
+double far_corner(const rc_plan_s* p, int i) {
+    const rcx::LevelGeom& g = p->lv[i];
+    const double sp = std::ldexp(1.0, i);
+    double far2 = 0.0;
+    for (int kx : {0, g.Px - 1})
+        for (int kz : {0, g.Pz - 1}) {
+            const double x = (kx + 0.5) * sp, z = (kz + 0.5) * sp;
+            const double dx = std::max(x, p->nx - x), dz = std::max(z, p->nz - z);
+            far2 = std::max(far2, dx * dx + dz * dz);
+        }
+    return std::sqrt(far2);
+}
+
+// Strips of the strip-split march for cascade i (1 = one ordinary launch).  A cascade is
+// split when its intervals reach half the domain and one wavelength block of the packed
+// field exceeds 96 MiB: such rays cross the whole field within one launch, so with the
+// field larger than L2 every voxel is fetched from DRAM many times.  Strips of about 64 MiB
+// measured best on the B300 (cascade 5 of 16 wavelengths: 1024^2 10.2 -> 9.7 ms with 2
+// strips; 1408^2 42.0 -> 31.3 ms with 4; 1984^2 150 -> 90 ms with 8); shorter cascades lose
+// more to the extra launches and the (I, T) traffic than they gain.  rc_options.strips >= 2
+// forces a count on every cascade >= 1.
+int strips_for_impl(const rc_plan_s* p, int i) {
+    if (i == 0 || p->opt.bilinear_fix || p->opt.strips == 1 ||
+        !rcx::level_split_supported(p->LB, p->VL))
+        return 1;
+    if (p->opt.strips >= 2) return std::min(p->opt.strips, p->nx);
+    const rcx::LevelGeom& g = p->lv[i];
+    const double len = std::min(g.b, far_corner(p, i)) - g.a;   // longest piece in the domain
+    if (len < 0.5 * std::max(p->nx, p->nz)) return 1;
+    const double block = (double)p->nx * p->nz * p->LB * sizeof(float2);
+    constexpr double kSplitMin = 96.0 * (1 << 20), kStrip = 64.0 * (1 << 20);
+    if (block <= kSplitMin) return 1;
+    return std::min(std::min(16, p->nx), std::max(2, (int)std::lround(block / kStrip)));
+}
+
 rc_status ensure_scratch(rc_plan_s* p, int n_lambda) {
     n_lambda *= p->n_incl;                           // virtual wavelengths
     if (n_lambda <= p->cap_lambda) return RC_OK;
@@ -134,10 +173,16 @@ rc_status ensure_scratch(rc_plan_s* p, int n_lambda) {
     // merged intervals hold one child average per 4 rays
     const size_t Rb = std::max<size_t>(1, n_lblk * (size_t)(max_rays / 4) * LB *
                                               storage_bytes(p->opt.precision));
+    // strip-split cascades keep (I, T) per ray and wavelength of one block between launches
+    size_t itb = 0;
+    for (int i = 1; i < p->C; ++i)
+        if (strips_for_impl(p, i) > 1)
+            itb = std::max(itb, (size_t)p->lv[i].rays() * LB * sizeof(float2));
     cudaDeviceSynchronize();  // scratch may be in use by work still queued
     free_scratch(p);
-    cudaError_t e;
+    cudaError_t e = cudaSuccess;
     if ((e = cudaMalloc(&p->d_packed, packed)) != cudaSuccess ||
+        (itb && (e = cudaMalloc(&p->d_it, itb)) != cudaSuccess) ||
         (e = cudaMalloc(&p->d_R[0], Rb)) != cudaSuccess ||
         (e = cudaMalloc(&p->d_R[1], Rb)) != cudaSuccess ||
         (e = cudaMalloc(&p->d_smax, n_lblk * sizeof(unsigned))) != cudaSuccess ||
@@ -148,6 +193,7 @@ rc_status ensure_scratch(rc_plan_s* p, int n_lambda) {
                     std::string("scratch allocation failed: ") + cudaGetErrorString(e));
     }
     p->packed_bytes = packed;
+    p->it_bytes = itb;
     p->R_bytes = Rb;
     p->aux_count = n_lblk;
     p->cap_lambda = (int)(n_lblk * LB);
@@ -164,20 +210,7 @@ rc_status ensure_scratch(rc_plan_s* p, int n_lambda) {
 int live_cascades(const rc_plan_s* p) {
     if (p->opt.bilinear_fix) return p->C;
     int live = p->C;
-    while (live > 1) {
-        const rcx::LevelGeom& g = p->lv[live - 1];
-        const double sp = std::ldexp(1.0, live - 1);
-        double far2 = 0.0;   // squared distance from the extreme probes to the farthest corner
-        for (int kx : {0, g.Px - 1})
-            for (int kz : {0, g.Pz - 1}) {
-                const double x = (kx + 0.5) * sp, z = (kz + 0.5) * sp;
-                const double dx = std::max(x, p->nx - x), dz = std::max(z, p->nz - z);
-                far2 = std::max(far2, dx * dx + dz * dz);
-            }
-        const double far = std::sqrt(far2);
-        if (!(g.a > far * (1.0 + 1e-6) + 1e-3)) break;
-        --live;
-    }
+    while (live > 1 && p->lv[live - 1].a > far_corner(p, live - 1) * (1.0 + 1e-6) + 1e-3) --live;
     return live;
 }
 
@@ -222,17 +255,17 @@ rc_status solve_device(rc_plan_s* p, const float* chi, const float* eta, int n_l
     const int n_lblk = (n_lambda + LB - 1) / LB;
     const long long ncell = (long long)p->nx * p->nz;
     const bool f16 = p->opt.precision != RC_STORE_F32;
-    int launches = 0;
+    int launches = 0, marks = 0;
     cudaError_t e;
     const bool timing = p->timing && p->ev.size() >= (size_t)(p->C + 7);
     if (timing) {
         p->launch_names.clear();
         cudaEventRecord(p->ev[0], s);
     }
-    auto mark = [&](const std::string& name) {
+    auto mark = [&](const std::string& name) {   // closes the timed interval of `name`
         if (timing) {
             p->launch_names.push_back(name);
-            cudaEventRecord(p->ev[launches], s);
+            cudaEventRecord(p->ev[++marks], s);
         }
     };
 
@@ -262,12 +295,28 @@ rc_status solve_device(rc_plan_s* p, const float* chi, const float* eta, int n_l
 
     const int live = live_cascades(p);
     for (int i = live - 1; i >= 0; --i) {
-        const rcx::LevelArgs a = rcx::level_args(p, i, n_lambda, Jv, alov, Jeffv, alocv);
+        rcx::LevelArgs a = rcx::level_args(p, i, n_lambda, Jv, alov, Jeffv, alocv);
         const bool has_up = i < live - 1;
-        if ((e = rcx::launch_level(LB, p->VL, p->opt.precision, i == 0, has_up, n_lblk, a, s)) !=
-            cudaSuccess)
-            return cuda_fail(e, "cascade launch");
-        ++launches;
+        const int S = strips_for_impl(p, i);
+        if (S > 1) {
+            // one wavelength block at a time, one launch per strip
+            a.it_state = p->d_it;
+            a.n_strips = S;
+            for (int lb = 0; lb < n_lblk; ++lb)
+                for (int ph = 0; ph < S; ++ph) {
+                    a.split_lb = lb;
+                    a.phase = ph;
+                    if ((e = rcx::launch_level_split(LB, p->VL, p->opt.precision, has_up, a, s)) !=
+                        cudaSuccess)
+                        return cuda_fail(e, "cascade launch (strips)");
+                    ++launches;
+                }
+        } else {
+            if ((e = rcx::launch_level(LB, p->VL, p->opt.precision, i == 0, has_up, n_lblk, a,
+                                       s)) != cudaSuccess)
+                return cuda_fail(e, "cascade launch");
+            ++launches;
+        }
         mark("cascade " + std::to_string(i));
     }
     if (NI > 1) {
@@ -283,11 +332,13 @@ rc_status solve_device(rc_plan_s* p, const float* chi, const float* eta, int n_l
         }
     }
     p->last_launches = launches;
-    p->timed_launches = timing ? launches : 0;
+    p->timed_launches = timing ? marks : 0;
     return RC_OK;
 }
 
 }  // namespace
+
+int rcx::strips_for(const rc_plan_s* p, int i) { return strips_for_impl(p, i); }
 
 rcx::LevelArgs rcx::level_args(const rc_plan_s* p, int i, int n_lambda, float* J, float* alo,
                                float* J_eff, float* alo_c) {
@@ -414,8 +465,8 @@ rc_status rc_plan(const rc_grid* grid, int n_cascades, int dirs0, int branching,
     int VL = o.lambda_per_lane == 0 ? std::min(LB, kDefaultLambdaPerLane) : o.lambda_per_lane;
     if ((VL != 1 && VL != 2 && VL != 4 && VL != 8) || VL > LB)
         return fail(RC_ERR_ARG, "rc_plan: lambda_per_lane must be 0, 1, 2, 4 or 8 and <= lambda_block");
-    for (int r : o.reserved)
-        if (r != 0) return fail(RC_ERR_ARG, "rc_plan: reserved option fields must be zero");
+    if (o.strips < 0 || o.strips > 16) return fail(RC_ERR_ARG, "rc_plan: strips must be in [0, 16]");
+    if (o.reserved != 0) return fail(RC_ERR_ARG, "rc_plan: reserved option fields must be zero");
     if ((long long)grid->nx * grid->nz * LB >= (1LL << 31))
         return fail(RC_ERR_ARG, "rc_plan: nx * nz * lambda_block must stay below 2^31");
 

@@ -51,7 +51,7 @@ class rc_options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("n_incl", ctypes.c_int),
                 ("interval_rule", ctypes.c_int), ("lambda_block", ctypes.c_int),
                 ("bilinear_fix", ctypes.c_int), ("lambda_per_lane", ctypes.c_int),
-                ("reserved", ctypes.c_int * 2)]
+                ("strips", ctypes.c_int), ("reserved", ctypes.c_int)]
 
 
 class rc_atom_desc(ctypes.Structure):
@@ -237,7 +237,7 @@ class Plan:
     def __init__(self, nx: int, nz: int, n_cascades: int, dirs0: int = 4, branching: int = 4,
                  interval0: float = 1.0, voxel_size: float = 1.0, precision: str = "f32",
                  interval_rule: int = 0, lambda_block: int = 0, n_incl: int = 1,
-                 bilinear_fix: bool = False, lambda_per_lane: int = 0):
+                 bilinear_fix: bool = False, lambda_per_lane: int = 0, strips: int = 0):
         L = load()
         self.nx, self.nz, self.n_cascades = nx, nz, n_cascades
         g = rc_grid(nx, nz, voxel_size)
@@ -249,6 +249,7 @@ class Plan:
         o.n_incl = n_incl
         o.bilinear_fix = int(bilinear_fix)
         o.lambda_per_lane = lambda_per_lane
+        o.strips = strips
         h = _vp()
         check(L.rc_plan(ctypes.byref(g), n_cascades, dirs0, branching, interval0, ctypes.byref(o),
                         ctypes.byref(h)))

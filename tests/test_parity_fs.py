@@ -309,7 +309,7 @@ def test_free_space_cascades_are_not_launched(n, C, launched):
     further out; cascade 3 starts at 21 < 84.9.  1024^2: cascade 7 starts at 5461 > 1357.6,
     cascade 6 at 1365 < 1402.9.  100^2: cascade 3 starts at 21 < 135.8."""
     rcx = _rcx()
-    p = rcx.Plan(n, n, C)
+    p = rcx.Plan(n, n, C, strips=1)                   # one launch per live cascade
     chi, eta = W.grf_fields(n, 1 if n > 100 else 2)
     dchi, deta = torch.from_numpy(chi).cuda(), torch.from_numpy(eta).cuda()
     J = p.formal_solve(dchi, deta)
@@ -317,3 +317,58 @@ def test_free_space_cascades_are_not_launched(n, C, launched):
     assert p.last_launch_count() == 1 + launched      # pack + live cascades
     if n <= 100:
         _assert_close(J.cpu().numpy(), _oracle(chi, eta, C), 1e-3, f"{n} C{C}")
+
+
+@pytest.mark.parametrize("nx,nz,C,strips,prec", [(96, 80, 5, 3, "f32"), (130, 67, 6, 4, "f32"),
+                                                 (64, 64, 5, 16, "f32"), (96, 80, 5, 2, "bf16")])
+def test_strip_split_march_matches_unsplit_and_oracle(nx, nz, C, strips, prec):
+    """Every cascade >= 1 marched strip by strip (one launch per vertical strip, partial
+    (I, T) composed front to back or back to front by the ray's x direction) gives the
+    unsplit result up to FP32 rounding, and the oracle's."""
+    rcx = _rcx()
+    chi, eta = W.grf_fields(nx, 5, nz=nz)
+    dchi, deta = torch.from_numpy(chi).cuda(), torch.from_numpy(eta).cuda()
+    whole = rcx.Plan(nx, nz, C, precision=prec, strips=1)
+    split = rcx.Plan(nx, nz, C, precision=prec, strips=strips)
+    J1, A1 = whole.formal_solve(dchi, deta, want_alo=True)
+    J2, A2 = split.formal_solve(dchi, deta, want_alo=True)
+    torch.cuda.synchronize()
+    J1, J2 = J1.cpu().numpy(), J2.cpu().numpy()
+    # the strip faces are entered at t computed from the face itself and left at t from the
+    # DDA's face count: the two differ by an ulp of t, so one piece per face moves by it
+    _assert_close(J2, J1, 1e-4 if prec == "f32" else 2e-3, "split vs whole")
+    np.testing.assert_array_equal(A2.cpu().numpy(), A1.cpu().numpy())   # cascade 0 is not split
+    _assert_close(J2, _oracle(chi, eta, C), 1e-3 if prec == "f32" else 5e-3, "split vs oracle")
+
+
+def test_strip_split_with_sparsity_and_mali():
+    rcx = _rcx()
+    chi, eta = W.grf_fields(96, 4, nz=72)
+    dchi, deta = torch.from_numpy(chi).cuda(), torch.from_numpy(eta).cuda()
+    active = np.zeros((72, 96), dtype=np.uint8)
+    active[10:50, 20:70] = 1
+    out = []
+    for strips in (1, 3):
+        p = rcx.Plan(96, 72, 5, strips=strips)
+        p.set_active(torch.from_numpy(active).cuda())
+        out.append([t.cpu().numpy() for t in p.formal_solve_mali(dchi, deta)])
+    for a, b in zip(*out):
+        _assert_close(b, a, 1e-4, "sparse split vs whole")
+
+
+def test_strip_split_automatic_at_1024():
+    """At 1024^2 with 16 wavelengths per block (128 MiB of packed field) cascade 5 (intervals
+    from 341 to the far corner) runs in 2 strips; cascade 4 (256 voxels long) and cascade 6
+    (38 voxels inside the domain) do not."""
+    rcx = _rcx()
+    chi, eta = W.grf_fields(1024, 16, lambdas=range(16))
+    dchi, deta = torch.from_numpy(chi).cuda(), torch.from_numpy(eta).cuda()
+    auto = rcx.Plan(1024, 1024, 8)
+    whole = rcx.Plan(1024, 1024, 8, strips=1)
+    Ja = auto.formal_solve(dchi, deta)
+    n_auto = auto.last_launch_count()
+    Jw = whole.formal_solve(dchi, deta)
+    n_whole = whole.last_launch_count()
+    torch.cuda.synchronize()
+    assert n_whole == 1 + 7 and n_auto == n_whole + 1     # pack + cascades 6..0; c5 in 2 strips
+    _assert_close(Ja.cpu().numpy(), Jw.cpu().numpy(), 5e-4, "auto strips vs whole")

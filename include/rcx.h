@@ -388,6 +388,13 @@ rc_status rc_mlp_forward(rc_mlp_t net, const float* X, long long B, float* Y, vo
  * kernel then skipped its outputs).  Training always uses the FMA path. */
 rc_status rc_mlp_use_tensor_cores(rc_mlp_t net, int enable);
 rc_status rc_mlp_tensor_core_status(rc_mlp_t net);
+
+/* Self-test of the library's bounded device-side wait (no counterpart in the paper): one CTA
+ * waits on an mbarrier that nobody completes, through the same bounded poll the tensor-core
+ * kernel uses, gives up after ~0.3 ms and reports it.  Returns RC_ERR_TIMEOUT when the wait
+ * gave up as designed (the expected result; the CUDA context stays usable), RC_ERR_CUDA on a
+ * launch/copy failure or if the wait did not give up.  Synchronous on `stream`. */
+rc_status rc_selftest_bounded_wait(void* stream);
 /* Mean-squared-error loss over B samples and its gradient (device outputs, either may be NULL). */
 rc_status rc_mlp_loss_grad(rc_mlp_t net, const float* X, const float* Y_target, long long B,
                            float* grad, float* loss, void* stream);

@@ -262,6 +262,33 @@ __device__ __forceinline__ int core_offset(int r, int k) {
     return (r >> 3) * 1024 + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2;
 }
 
+// Waits for phase `parity` of the mbarrier at shared address `mbar` with non-blocking polls
+// and a short sleep between them, at most `limit` polls (about limit x 64 ns); false if it
+// gave up.  Every device-side wait of this library goes through here.
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned mbar, unsigned parity, unsigned limit) {
+    for (unsigned it = 0; it < limit; ++it) {
+        unsigned done;
+        asm volatile("{\n\t.reg .pred q;\n\t"
+                     "mbarrier.test_wait.parity.shared::cta.b64 q, [%1], %2;\n\t"
+                     "selp.u32 %0, 1, 0, q;\n\t}"
+                     : "=r"(done) : "r"(mbar), "r"(parity) : "memory");
+        if (done) return true;
+        __nanosleep(64);
+    }
+    return false;
+}
+
+// Self-test of the bounded wait: an mbarrier that expects one arrival nobody makes.  The
+// wait must give up after `limit` polls and report it; the context stays usable.
+__global__ void wait_timeout_probe_kernel(unsigned limit, int* __restrict__ timed_out) {
+    __shared__ __align__(8) unsigned long long bar;
+    const unsigned mb = (unsigned)__cvta_generic_to_shared(&bar);
+    if (threadIdx.x == 0) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb));
+    __syncthreads();
+    const bool ok = mbar_wait_bounded(mb, 0, limit);
+    if (threadIdx.x == 0) *timed_out = ok ? 0 : 1;
+}
+
 __device__ __forceinline__ unsigned long long smem_desc(const void* p) {
     const unsigned addr = (unsigned)__cvta_generic_to_shared(p);
     unsigned long long d = 0;
@@ -352,17 +379,9 @@ mlp_forward_tc_kernel(const float* __restrict__ wbf, const float* __restrict__ n
         asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
                      ::"r"(mb) : "memory");
     }
-    // bounded wait for the MMAs (phase 0): non-blocking polls with a short sleep, so the
-    // limit bounds the wall time (about kTcWaitLimit x 64 ns)
-    unsigned done = 0;
-    for (unsigned it = 0; it < kTcWaitLimit && !done; ++it) {
-        asm volatile("{\n\t.reg .pred q;\n\t"
-                     "mbarrier.test_wait.parity.shared::cta.b64 q, [%1], 0;\n\t"
-                     "selp.u32 %0, 1, 0, q;\n\t}"
-                     : "=r"(done) : "r"(mb) : "memory");
-        if (!done) __nanosleep(64);
-    }
-    // block-uniform outcome: the epilogue's .sync.aligned loads need whole warps
+    // bounded wait for the MMAs (phase 0); block-uniform outcome: the epilogue's
+    // .sync.aligned loads need whole warps
+    unsigned done = mbar_wait_bounded(mb, 0, kTcWaitLimit) ? 1u : 0u;
     done = __syncthreads_and(done);
     if (!done && tid == 0) atomicExch(err, 1);
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -661,6 +680,25 @@ rc_status rc_mlp_use_tensor_cores(rc_mlp_t n, int enable) {
     }
     n->tensor_cores = enable != 0;
     return RC_OK;
+}
+
+rc_status rc_selftest_bounded_wait(void* stream) {
+    rcx::set_last_error("");
+    cudaStream_t s = (cudaStream_t)stream;
+    int* d = nullptr;
+    cudaError_t e = cudaMalloc(&d, sizeof(int));
+    if (e != cudaSuccess) return mcuda(e, "rc_selftest_bounded_wait");
+    int h = -1;
+    if ((e = cudaMemsetAsync(d, 0xff, sizeof(int), s)) == cudaSuccess) {
+        wait_timeout_probe_kernel<<<1, 32, 0, s>>>(1u << 12, d);   // ~0.3 ms of polling
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h, d, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(d);
+    if (e != cudaSuccess) return mcuda(e, "rc_selftest_bounded_wait");
+    if (h == 1) return mfail(RC_ERR_TIMEOUT, "bounded device wait gave up (as the self-test expects)");
+    return mfail(RC_ERR_CUDA, "rc_selftest_bounded_wait: the probe's wait did not give up");
 }
 
 rc_status rc_mlp_tensor_core_status(rc_mlp_t n) {

@@ -575,7 +575,7 @@ rc_status rc_plan_reserve(rc_plan_t p, int n_lambda) {
 size_t rc_plan_scratch_bytes(rc_plan_t p) {
     if (!p) return 0;
     return p->packed_bytes + 2 * p->R_bytes + p->aux_count * (sizeof(unsigned) + sizeof(float)) +
-           p->stage_bytes;
+           p->it_bytes + p->stage_bytes;
 }
 
 rc_status rc_plan_cascade(rc_plan_t p, int i, int* px, int* pz, long long* dirs, double* a,

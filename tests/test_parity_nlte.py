@@ -140,3 +140,24 @@ def test_nlte_converges_on_a_slab():
     p = pops.cpu().numpy()
     np.testing.assert_allclose(p.sum(axis=0), na.cpu().numpy(), rtol=1e-12)
     assert np.all(p > 0)
+
+
+def test_resume_from_checkpoint_equals_straight_run(tmp_path):
+    """Populations are the whole state of the iteration: 3 iterations, a checkpoint written
+    and read back, 2 more iterations give bit for bit the populations of 5 straight ones."""
+    from paper_2408_14425_b300 import checkpoint
+    rcx = _rcx()
+    T, nH, vox = _slab(48)
+    atom = rcx.Atom(ATOM)
+    plan = rcx.Plan(48, 48, 5, voxel_size=vox)
+    Td = _dev(T)
+    ne, na, straight = atom.lte(Td, _dev(nH))
+    rcx.nlte_solve(plan, atom, Td, ne, na, straight, tol=1e-30, max_iter=5)
+    _, _, pops = atom.lte(Td, _dev(nH))
+    _, it, hist = rcx.nlte_solve(plan, atom, Td, ne, na, pops, tol=1e-30, max_iter=3)
+    f = str(tmp_path / "nlte.npz")
+    checkpoint.save(f, pops, it, hist)
+    resumed, it0, _ = checkpoint.load(f, device="cuda")
+    assert it0 == 3
+    rcx.nlte_solve(plan, atom, Td, ne, na, resumed, tol=1e-30, max_iter=2)
+    np.testing.assert_array_equal(resumed.cpu().numpy(), straight.cpu().numpy())

@@ -192,11 +192,12 @@ def test_bilinear_fix_rejects_the_operator_outputs():
         p.formal_solve_mali(x, x)
 
 
-@pytest.mark.parametrize("n_incl,C", [(8, 5), (3, 4)])
-def test_inclinations_match_oracle(n_incl, C):
-    """2D invariance (Sec. 3.1): Gauss-Radau inclinations, J and the diagonal operator."""
+@pytest.mark.parametrize("n_incl,C,strips", [(8, 5, 0), (3, 4, 0), (3, 5, 3)])
+def test_inclinations_match_oracle(n_incl, C, strips):
+    """2D invariance (Sec. 3.1): Gauss-Radau inclinations, J and the diagonal operator (also
+    with the cascades strip-split)."""
     chi, eta = W.grf_fields(80, 6, nz=72)
-    J, alo = _solve(chi, eta, C, want_alo=True, n_incl=n_incl)
+    J, alo = _solve(chi, eta, C, want_alo=True, n_incl=n_incl, strips=strips)
     J_ref, alo_ref = oracle.rc_solve_inclined(chi.astype(np.float64), eta.astype(np.float64), C,
                                               n_incl, want_alo=True)
     _assert_close(J, J_ref, 1e-3, f"J n_incl={n_incl}")

@@ -602,15 +602,93 @@ def run_batched(args):
     print(json.dumps(line), flush=True)
 
 
+def emergent_rays(n_side: int, n_view: int = 16, per_view: int = 2048):
+    """Lines of sight for emergent spectra: n_view viewing directions theta = pi (v + 1/2) /
+    n_view, each with per_view parallel rays spread evenly across the domain's projected
+    width, starting outside the domain on the observer's side.  Returns rays [n][4] (float32)
+    and each ray's cell count inside the domain (x and z faces crossed + 1; 0 if it misses)."""
+    import numpy as np
+    c = n_side / 2.0
+    rays, cells = [], []
+    for v in range(n_view):
+        th = np.pi * (v + 0.5) / n_view
+        w = np.array([np.cos(th), np.sin(th)])
+        nrm = np.array([-w[1], w[0]])
+        width = n_side * (abs(w[0]) + abs(w[1]))
+        u = (np.arange(per_view) + 0.5) / per_view * width - width / 2
+        o = c - (n_side * 0.75) * w + u[:, None] * nrm[None, :]
+        rays.append(np.column_stack([o, np.broadcast_to(w, (per_view, 2))]))
+        # exact box clip, then faces crossed between the entry and exit points
+        with np.errstate(divide="ignore", invalid="ignore"):
+            inv = 1.0 / w
+            t0 = (0.0 - o) * inv
+            t1 = (n_side - o) * inv
+        tlo = np.maximum(np.minimum(t0, t1).max(axis=1), 0.0)
+        thi = np.maximum(t0, t1).min(axis=1)
+        hit = tlo < thi
+        eps = 1e-9
+        a = o + (tlo + eps)[:, None] * w
+        b = o + (thi - eps)[:, None] * w
+        n = (np.abs(np.floor(b) - np.floor(a)).sum(axis=1) + 1) * hit
+        cells.append(n)
+    return np.concatenate(rays).astype(np.float32), np.concatenate(cells)
+
+
+def run_emergent(args):
+    """Emergent intensity along lines of sight (Sec. 3.9): the 1024^2 x 64-wavelength field of
+    the headline, 16 viewing directions x 2048 parallel rays, front-to-back long
+    characteristics per ray and wavelength; timed without and with the contribution
+    function (one atomic add per piece)."""
+    import torch
+
+    from paper_2408_14425_b300 import build as rbuild
+    from paper_2408_14425_b300 import rcx, workloads
+    torch.cuda.set_device(_env_int("LOCAL_RANK", 0))
+    if _env_int("RANK", 0) != 0:
+        return
+    rbuild.build()
+    n, nl = args.n_side, args.n_lambda
+    chi, eta = workloads.grf_fields(n, nl)
+    dchi, deta = torch.from_numpy(chi).cuda(), torch.from_numpy(eta).cuda()
+    rays_h, cells = emergent_rays(n)
+    rays = torch.from_numpy(rays_h).cuda()
+    plan = rcx.Plan(n, n, 1)
+    out = {"metric": "emergent intensity, ray-wavelengths/s", "unit": "ray-wavelengths/s",
+           "higher_is_better": True, "data": "synthetic", "dtype": "f32",
+           "config": {"workload": f"{n}x{n} GRF field (headline recipe), {nl} wavelengths, "
+                      f"16 viewing directions x 2048 parallel rays from outside the domain",
+                      "rays": int(len(rays_h)), "cells_per_ray_mean": float(cells.mean())}}
+    stream = torch.cuda.current_stream()
+    for contrib in (False, True):
+        for _ in range(args.warmup):
+            plan.emergent(dchi, deta, rays, want_contrib=contrib)
+        torch.cuda.synchronize()
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for _ in range(args.steps):
+            plan.emergent(dchi, deta, rays, want_contrib=contrib)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        ms = ev0.elapsed_time(ev1) / args.steps
+        key = "with_contribution" if contrib else "intensity"
+        out[key] = {"ms_per_call": round(ms, 3),
+                    "ray_wavelengths_per_s": round(len(rays_h) * nl / (ms / 1e3), 1),
+                    "wavelength_crossings_per_s": round(float(cells.sum()) * nl / (ms / 1e3), 1)}
+    out["value"] = out["intensity"]["ray_wavelengths_per_s"]
+    print(json.dumps(out), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["formal", "nlte", "batched"], default="formal",
+    ap.add_argument("--workload", choices=["formal", "nlte", "batched", "emergent"],
+                    default="formal",
                     help="formal: the RC formal solution (headline); nlte: time-to-1e-3; "
-                         "batched: 16 uneven domains in one graph")
+                         "batched: 16 uneven domains in one graph; emergent: lines of sight")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--n-incl", type=int, default=1,
                     help="inclinations per in-plane ray (2D invariance; not the headline)")
@@ -634,6 +712,8 @@ def main():
         run_reference(args)
     elif args.workload == "nlte":
         run_nlte(args)
+    elif args.workload == "emergent":
+        run_emergent(args)
     elif args.workload == "batched":
         if args.precision == "f32" and "--precision" not in sys.argv:
             args.precision = "bf16"

@@ -404,6 +404,14 @@ rc_status rc_mlp_loss_grad(rc_mlp_t net, const float* X, const float* Y_target, 
  * receives each minibatch loss. */
 rc_status rc_mlp_train(rc_mlp_t net, const float* X, const float* Y_target, long long N, int batch,
                        int steps, float lr, float* loss_history, void* stream);
+/* The surrogate's life cycle under the names of the method's interface (no counterpart in the
+ * paper): rc_surrogate_init = rc_mlp_create; rc_surrogate_train_step = one Adam step of
+ * rc_mlp_train (loss: host float or NULL; NULL does not synchronise); rc_surrogate_predict =
+ * rc_mlp_forward (log10 departure coefficients [B][3] from features [B][6]). */
+rc_status rc_surrogate_init(unsigned long long seed, rc_mlp_t* out);
+rc_status rc_surrogate_train_step(rc_mlp_t net, const float* X, const float* Y_target, long long N,
+                                  int batch, float lr, float* loss, void* stream);
+rc_status rc_surrogate_predict(rc_mlp_t net, const float* X, long long B, float* Y, void* stream);
 /* Features X [ncell][6] from device T, n_e, n_H (FP64) and J [n_lambda][ncell] (FP32). */
 rc_status rc_surrogate_features(rc_atom_t atom, const double* T, const double* ne, const double* nH,
                                 const float* J, long long ncell, float* X, void* stream);

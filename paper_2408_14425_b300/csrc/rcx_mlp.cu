@@ -682,6 +682,17 @@ rc_status rc_mlp_use_tensor_cores(rc_mlp_t n, int enable) {
     return RC_OK;
 }
 
+rc_status rc_surrogate_init(unsigned long long seed, rc_mlp_t* out) { return rc_mlp_create(seed, out); }
+
+rc_status rc_surrogate_train_step(rc_mlp_t net, const float* X, const float* Y_target, long long N,
+                                  int batch, float lr, float* loss, void* stream) {
+    return rc_mlp_train(net, X, Y_target, N, batch, 1, lr, loss, stream);
+}
+
+rc_status rc_surrogate_predict(rc_mlp_t net, const float* X, long long B, float* Y, void* stream) {
+    return rc_mlp_forward(net, X, B, Y, stream);
+}
+
 rc_status rc_selftest_bounded_wait(void* stream) {
     rcx::set_last_error("");
     cudaStream_t s = (cudaStream_t)stream;

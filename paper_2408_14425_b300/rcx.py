@@ -34,7 +34,8 @@ EXPORTS = [
     "rc_mlp_fit_normalization", "rc_mlp_forward", "rc_mlp_loss_grad", "rc_mlp_train",
     "rc_surrogate_features", "rc_surrogate_targets", "rc_surrogate_seed", "rc_plan_set_active",
     "rc_plan_active_probes", "rc_emergent", "rc_mlp_use_tensor_cores", "rc_mlp_tensor_core_status",
-    "rc_selftest_bounded_wait",
+    "rc_selftest_bounded_wait", "rc_surrogate_init", "rc_surrogate_train_step",
+    "rc_surrogate_predict",
 ]
 
 
@@ -174,6 +175,13 @@ def load():
     L.rc_mlp_tensor_core_status.argtypes = [_vp]
     L.rc_selftest_bounded_wait.argtypes = [_vp]
     L.rc_selftest_bounded_wait.restype = ctypes.c_int
+    L.rc_surrogate_init.argtypes = [ctypes.c_ulonglong, ctypes.POINTER(_vp)]
+    L.rc_surrogate_init.restype = ctypes.c_int
+    L.rc_surrogate_train_step.argtypes = [_vp, _vp, _vp, ctypes.c_longlong, ctypes.c_int,
+                                          ctypes.c_float, ctypes.POINTER(ctypes.c_float), _vp]
+    L.rc_surrogate_train_step.restype = ctypes.c_int
+    L.rc_surrogate_predict.argtypes = [_vp, _vp, ctypes.c_longlong, _vp, _vp]
+    L.rc_surrogate_predict.restype = ctypes.c_int
     L.rc_mlp_tensor_core_status.restype = ctypes.c_int
     L.rc_mlp_forward.argtypes = [_vp, _vp, ctypes.c_longlong, _vp, _vp]
     L.rc_mlp_forward.restype = ctypes.c_int

@@ -151,3 +151,40 @@ def test_trained_network_saves_iterations():
     assert seeded["iterations"] < plain["iterations"]
     rel = (seeded["pops"] - plain["pops"]).abs() / plain["pops"].abs()
     assert float(rel.max()) < 5e-3
+
+
+def test_surrogate_interface_names():
+    """rc_surrogate_init / _train_step / _predict are rc_mlp_create, one step of
+    rc_mlp_train and rc_mlp_forward: five single steps equal one five-step call (up to the
+    summation order of the gradient atomics), and predict equals forward."""
+    import ctypes
+    from paper_2408_14425_b300 import build, rcx
+    build.build()
+    L = rcx.load()
+    rng = np.random.default_rng(2)
+    X = torch.from_numpy(rng.normal(size=(3000, 6)).astype(np.float32)).cuda()
+    Y = torch.from_numpy(rng.normal(size=(3000, 3)).astype(np.float32)).cuda()
+    a = rcx.MLP(seed=5)
+    a.fit_normalization(X)
+    a.train(X, Y, batch=512, steps=5, lr=1e-3, record=False)
+    h = ctypes.c_void_p()
+    assert L.rc_surrogate_init(5, ctypes.byref(h)) == 0
+    fp = ctypes.POINTER(ctypes.c_float)
+    mean = np.ascontiguousarray(a.get_params()[1])
+    std = np.ascontiguousarray(a.get_params()[2])
+    assert L.rc_mlp_set_params(h, None, mean.ctypes.data_as(fp), std.ctypes.data_as(fp)) == 0
+    loss = ctypes.c_float()
+    for _ in range(5):
+        assert L.rc_surrogate_train_step(h, X.data_ptr(), Y.data_ptr(), 3000, 512, 1e-3,
+                                         ctypes.byref(loss), None) == 0
+    th = np.empty(a.n_params, np.float32)
+    assert L.rc_mlp_get_params(h, th.ctypes.data_as(fp), None, None) == 0
+    np.testing.assert_allclose(th, a.get_params()[0], rtol=1e-4, atol=1e-6)
+    assert np.isfinite(loss.value) and loss.value > 0
+    y1 = torch.empty((3000, 3), device="cuda")
+    assert L.rc_surrogate_predict(h, X.data_ptr(), 3000, y1.data_ptr(), None) == 0
+    y2 = torch.empty((3000, 3), device="cuda")
+    assert L.rc_mlp_forward(h, X.data_ptr(), 3000, y2.data_ptr(), None) == 0
+    torch.cuda.synchronize()
+    assert torch.equal(y1, y2)
+    L.rc_mlp_destroy(h)

@@ -61,6 +61,8 @@ def _plan(lib, nx=8, nz=8, C=3, W0=4, B=4, L0=1.0, voxel=1.0, **kw):
     (dict(L0=0.0), -1), (dict(L0=float("inf")), -1), (dict(voxel=0.0), -1),
     (dict(B=2), -6), (dict(precision=3), -1), (dict(interval_rule=2), -1),
     (dict(lambda_block=3), -1), (dict(n_incl=0), -1), (dict(n_incl=17), -1),
+    (dict(strips=17), -1), (dict(strips=-1), -1),
+    (dict(nx=16384, nz=16384), -1),          # nx * nz * lambda_block must stay below 2^31
 ])
 def test_plan_rejects_bad_arguments(lib, kw, expect):
     st, h = _plan(lib, **kw)

@@ -373,3 +373,23 @@ def test_strip_split_automatic_at_1024():
     torch.cuda.synchronize()
     assert n_whole == 1 + 7 and n_auto == n_whole + 1     # pack + cascades 6..0; c5 in 2 strips
     _assert_close(Ja.cpu().numpy(), Jw.cpu().numpy(), 5e-4, "auto strips vs whole")
+
+
+def test_large_thick_uniform_domain():
+    """4096^2, 16 wavelengths, 9 cascades (a 2 GiB field block, so the long cascades run in
+    16 strips; cascade 8 lies in free space): in a uniform medium of optical depth 1 per
+    voxel, J equals S wherever every ray has crossed 40 voxels before leaving the domain
+    (exp(-40) below FP32 resolution)."""
+    rcx = _rcx()
+    n, nl = 4096, 16
+    S = np.linspace(0.5, 2.0, nl, dtype=np.float32)
+    chi = torch.ones((nl, n, n), device="cuda")
+    eta = chi * torch.from_numpy(S).cuda()[:, None, None]
+    p = rcx.Plan(n, n, 9)
+    J = p.formal_solve(chi, eta)
+    torch.cuda.synchronize()
+    inner = J[:, 40:-40, 40:-40]
+    rel = (inner / torch.from_numpy(S).cuda()[:, None, None] - 1.0).abs().max().item()
+    assert rel < 1e-5, rel
+    assert p.last_launch_count() > 1 + 8     # strips on the long cascades
+    del chi, eta, J

@@ -263,15 +263,18 @@ __device__ __forceinline__ bool march_interval(const float2* __restrict__ F, int
     float t = tlo;
     // The walk does not depend on the field, so the next voxel is fetched one step
     // ahead: two loads per lane are in flight while the current voxel is integrated.
+    // After the last step that fetch is one voxel past the exit face (up to a row outside
+    // the block); the packed field is allocated with a guard band of a row of voxels on
+    // both sides, so it reads allocated memory, and the value is never used.
     Voxel<VL> cur;
-    cur.load(F + min((unsigned)off, off_hi));
+    cur.load(F + off);
     for (int step = 0; step < max_steps; ++step) {
         const bool stepx = tnx <= tnz;
         const float tn = fminf(fminf(tnx, tnz), thi);
         const float ds = tn - t;
         const int off_next = off + (stepx ? dox : doz);
         Voxel<VL> nxt;
-        nxt.load(F + min((unsigned)off_next, off_hi));
+        nxt.load(F + off_next);
 #pragma unroll
         for (int j = 0; j < VL; ++j) {
             const float y = cur.v[j].x * ds;

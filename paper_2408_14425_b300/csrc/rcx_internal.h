@@ -153,6 +153,12 @@ namespace rcx {
 LevelArgs level_args(const rc_plan_s* p, int i, int n_lambda, float* J, float* alo,
                      float* J_eff, float* alo_c);
 rc_status plan_reserve(rc_plan_s* p, int n_lambda);
+// Guard band on each side of a packed field of nx-wide rows and LB wavelengths per voxel:
+// one row plus one voxel, so the march's one-step-ahead fetch past the exit face stays in
+// the allocation.  Rounded to 256 bytes.
+inline size_t packed_guard_bytes(int nx, int LB) {
+    return (((size_t)(nx + 1) * LB * 2 * sizeof(float)) + 255) & ~(size_t)255;
+}
 // strips of the strip-split march of cascade i of a plan (1 = not split)
 int strips_for(const rc_plan_s* p, int i);
 rc_status plan_set_layout(rc_plan_s* p, int LB, int VL);
@@ -184,7 +190,9 @@ struct rc_plan_s {
     std::vector<size_t> dir_off;     // offset of each cascade's table in d_dirs
     float2* d_dirs = nullptr;
     // scratch
-    float2* d_packed = nullptr;
+    float2* d_packed = nullptr;        // inside d_packed_raw, after a guard band
+    float2* d_packed_raw = nullptr;
+    size_t packed_guard = 0;           // bytes of guard band on each side of the field
     float2* d_it = nullptr;            // partial (I, T) of a strip-split cascade, one lambda block
     size_t it_bytes = 0;
     size_t packed_bytes = 0;

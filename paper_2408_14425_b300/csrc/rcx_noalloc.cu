@@ -106,8 +106,9 @@ extern "C" rc_status rc_formal_solve_noalloc(const rc_grid* grid, int n_cascades
     }
     const size_t dirs_bytes = align256((size_t)n_dirs * sizeof(float2));
     const size_t packed_bytes = align256((size_t)n_lblk * ncell * LB * sizeof(float2));
+    const size_t guard = rcx::packed_guard_bytes(nx, LB);   // around the field (march prefetch)
     const size_t R_bytes = align256((size_t)n_lblk * (size_t)(max_rays / 4) * LB * sizeof(float));
-    const size_t need = dirs_bytes + packed_bytes + 2 * R_bytes;
+    const size_t need = dirs_bytes + guard + packed_bytes + guard + 2 * R_bytes;
     if (need > kNoallocScratchBytes)
         return nfail(RC_ERR_ARG, "rc_formal_solve_noalloc: this problem needs " +
                                      std::to_string(need) + " bytes of scratch, more than the " +
@@ -124,9 +125,9 @@ extern "C" rc_status rc_formal_solve_noalloc(const rc_grid* grid, int n_cascades
     rc_status st = scratch_address(dev, &base);
     if (st != RC_OK) return st;
     float2* dirs = reinterpret_cast<float2*>(base);
-    float2* packed = reinterpret_cast<float2*>(base + dirs_bytes);
-    float* R[2] = {reinterpret_cast<float*>(base + dirs_bytes + packed_bytes),
-                   reinterpret_cast<float*>(base + dirs_bytes + packed_bytes + R_bytes)};
+    float2* packed = reinterpret_cast<float2*>(base + dirs_bytes + guard);
+    unsigned char* after = base + dirs_bytes + guard + packed_bytes + guard;
+    float* R[2] = {reinterpret_cast<float*>(after), reinterpret_cast<float*>(after + R_bytes)};
     cudaStream_t s = (cudaStream_t)stream;
 
     // Everything below overwrites what it later reads; nothing has to start at zero.

@@ -107,7 +107,9 @@ void gauss_radau(int n, std::vector<double>& mu, std::vector<double>& w) {
 }
 
 void free_scratch(rc_plan_s* p) {
-    cudaFree(p->d_packed);
+    cudaFree(p->d_packed_raw);
+    p->d_packed_raw = nullptr;
+    p->packed_guard = 0;
     cudaFree(p->d_it);
     p->d_it = nullptr;
     p->it_bytes = 0;
@@ -181,7 +183,8 @@ rc_status ensure_scratch(rc_plan_s* p, int n_lambda) {
     cudaDeviceSynchronize();  // scratch may be in use by work still queued
     free_scratch(p);
     cudaError_t e = cudaSuccess;
-    if ((e = cudaMalloc(&p->d_packed, packed)) != cudaSuccess ||
+    const size_t guard = rcx::packed_guard_bytes(p->nx, LB);
+    if ((e = cudaMalloc(&p->d_packed_raw, packed + 2 * guard)) != cudaSuccess ||
         (itb && (e = cudaMalloc(&p->d_it, itb)) != cudaSuccess) ||
         (e = cudaMalloc(&p->d_R[0], Rb)) != cudaSuccess ||
         (e = cudaMalloc(&p->d_R[1], Rb)) != cudaSuccess ||
@@ -192,6 +195,8 @@ rc_status ensure_scratch(rc_plan_s* p, int n_lambda) {
         return fail(e == cudaErrorMemoryAllocation ? RC_ERR_OOM : RC_ERR_CUDA,
                     std::string("scratch allocation failed: ") + cudaGetErrorString(e));
     }
+    p->d_packed = reinterpret_cast<float2*>(reinterpret_cast<char*>(p->d_packed_raw) + guard);
+    p->packed_guard = guard;
     p->packed_bytes = packed;
     p->it_bytes = itb;
     p->R_bytes = Rb;
@@ -574,8 +579,8 @@ rc_status rc_plan_reserve(rc_plan_t p, int n_lambda) {
 
 size_t rc_plan_scratch_bytes(rc_plan_t p) {
     if (!p) return 0;
-    return p->packed_bytes + 2 * p->R_bytes + p->aux_count * (sizeof(unsigned) + sizeof(float)) +
-           p->it_bytes + p->stage_bytes;
+    return p->packed_bytes + 2 * p->packed_guard + 2 * p->R_bytes +
+           p->aux_count * (sizeof(unsigned) + sizeof(float)) + p->it_bytes + p->stage_bytes;
 }
 
 rc_status rc_plan_cascade(rc_plan_t p, int i, int* px, int* pz, long long* dirs, double* a,

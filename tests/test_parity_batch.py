@@ -114,7 +114,8 @@ def test_batch_rejects_mismatched_plans():
 
 def test_uneven_domain_workload_full_size_sampled():
     """The 16-domain workload (sides 256..2048, 32..128 wavelengths, seed 7) in one batch
-    with BF16 interval storage; one wavelength of the two smallest domains against the oracle."""
+    with BF16 interval storage; one wavelength of the two smallest domains against the oracle,
+    and the largest domain against its own single-domain solve."""
     rcx = _rcx()
     doms = W.batched_domains()
     plans, chis, etas, Js, host = [], [], [], [], []
@@ -136,4 +137,10 @@ def test_uneven_domain_workload_full_size_sampled():
         _close(Js[d][0].cpu().numpy(), J_ref, 5e-3, f"domain {d} ({doms[d][0]}^2)")
     for j in Js:
         assert bool(torch.isfinite(j).all())
+    # the largest domain (its long cascades strip-split inside the graph) equals the same
+    # plan solved on its own
+    big = int(np.argmax([s for s, _, _ in doms]))
+    J_single = plans[big].formal_solve(chis[big], etas[big])
+    torch.cuda.synchronize()
+    assert torch.equal(J_single, Js[big]), float((J_single - Js[big]).abs().max())
     batch.close()

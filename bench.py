@@ -308,6 +308,16 @@ def run_ours(args):
                 "march_ms_per_step": round(march_ms, 3), "pack_ms_per_step": round(pack_ms, 3),
                 "per_cascade": levels, "kernel_source_sha256_16": khash}
 
+    # the compulsory-traffic floor: chi, eta read and J written once (12 B per cell), every
+    # cascade's merged intervals written and read back once (4 B per ray each way)
+    comp = n_lambda * (12 * n_side * n_side + sum(8 * r for r in rays[1:]))
+    comp_gbps = comp / (ms_step / 1e3) / 1e9
+    roofline_compulsory = {"bound": "hbm", "unit": "GB/s", "bytes_per_step": comp,
+                           "achieved": round(comp_gbps, 1), "peak": peak,
+                           "frac": round(comp_gbps / peak, 4),
+                           "note": "floor only: a ray march re-gathers every voxel ~1000x, "
+                                   "see roofline (algorithmic gathers) and traffic (ncu)"}
+
     # CPU baseline: the FP64 oracle on a bounded sample (one wavelength of this workload)
     cpu = None
     if not args.no_cpu_baseline:
@@ -330,7 +340,8 @@ def run_ours(args):
                    "parallelism": f"wavelength batches, {world} GPU(s)"},
         "probe_ray_intervals_per_s": round(value * intervals, 1),
         "voxel_crossings_per_s": round(value * cross["total"], 1),
-        "roofline": roofline, "roofline_issue": roofline_issue, "cpu_baseline": cpu, "e2e": e2e,
+        "roofline": roofline, "roofline_issue": roofline_issue,
+        "roofline_compulsory": roofline_compulsory, "cpu_baseline": cpu, "e2e": e2e,
         "gpu_launches": launches, "clocks": clk,
     }
     print(json.dumps(line), flush=True)

@@ -731,7 +731,7 @@ def main():
     ap.add_argument("--bilinear-fix", action="store_true",
                     help="the bilinear fix of Sec. 2.5 (J only; not the headline workload)")
     ap.add_argument("--train-atmospheres", type=int, default=200)
-    ap.add_argument("--train-steps", type=int, default=4000)
+    ap.add_argument("--train-steps", type=int, default=16000)
     ap.add_argument("--nlte-max-iter", type=int, default=3000)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")

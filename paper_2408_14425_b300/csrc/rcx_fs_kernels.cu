@@ -208,7 +208,7 @@ struct Voxel {
 // is evaluated with the same expression, so the walk ends exactly on it and never
 // leaves the grid.  The advance is predicated (no divergent branch between rays
 // of a warp that step along different axes), and the voxel address is a running
-// 32-bit offset.
+// 32-bit offset (cell * LB + lane_off).
 // With SPLIT_FIRST the emission of the first piece (for a cascade-0 ray: the probe's
 // own cell from its centre to its edge) goes to I0 instead of I.  With CONTRIB every
 // piece's contribution T S (1 - e^{-dtau}) is also added to contrib[j * ncell + cell] for the
@@ -218,8 +218,7 @@ template <int LB, int VL, bool SPLIT_FIRST = false, bool CONTRIB = false>
 __device__ __forceinline__ bool march_interval(const float2* __restrict__ F, int nx, int nz,
                                                int x0, int x1,
                                                float ox, float oz, float wx, float wz,
-                                               float a, float b, int lane_off,
-                                               unsigned off_hi, int max_steps,
+                                               float a, float b, int lane_off, int max_steps,
                                                float (&I)[VL], float (&T)[VL], float (&I0)[VL],
                                                float* contrib = nullptr, int n_valid = 0,
                                                long long ncell = 0) {
@@ -285,7 +284,7 @@ __device__ __forceinline__ bool march_interval(const float2* __restrict__ F, int
             else
                 I[j] = fmaf(T[j] * cur.v[j].y, om, I[j]);
             if (CONTRIB && j < n_valid)
-                atomicAdd(contrib + (size_t)j * ncell + (min((unsigned)off, off_hi) - lane_off) / LB,
+                atomicAdd(contrib + (size_t)j * ncell + (off - lane_off) / LB,
                           T[j] * cur.v[j].y * om);
             T[j] *= e;
         }
@@ -348,7 +347,7 @@ template <int LB, int VL, typename TS>
 __device__ __forceinline__ void fixed_rays(const LevelArgs& A, const float2* __restrict__ F,
                                            const TS* __restrict__ Rup, float sc, int px, int pz,
                                            float ox, float oz, float2 d, int k, int lane_off,
-                                           unsigned off_hi, float (&R)[VL]) {
+                                           float (&R)[VL]) {
     int jx[2], jz[2];
     float fx, fz;
     upper_coord(px, A.Px_up, jx[0], jx[1], fx);
@@ -370,7 +369,7 @@ __device__ __forceinline__ void fixed_rays(const LevelArgs& A, const float2* __r
             if (L > 0.0f) {
                 const float iL = 1.0f / L;
                 march_interval<LB, VL>(F, A.nx, A.nz, 0, A.nx, Ax, Az, dx * iL, dz * iL, 0.0f, L,
-                                       lane_off, off_hi, A.max_steps, I, T, I0);
+                                       lane_off, A.max_steps, I, T, I0);
             } else {
 #pragma unroll
                 for (int j = 0; j < VL; ++j) {
@@ -443,15 +442,14 @@ __device__ __forceinline__ void level_body(const LevelArgs& A, int lb, long long
         const float2 d = A.dirs[k];
         const float ox = ((float)px + 0.5f) * A.spacing, oz = ((float)pz + 0.5f) * A.spacing;
         const float2* F = A.field + (size_t)lb * A.ncell * LB;
-        const unsigned off_hi = (unsigned)((A.ncell - 1) * LB + lane_off);
 
         if constexpr (FIX && HAS_UP) {
             const TS* Rup = reinterpret_cast<const TS*>(A.R_up) + (size_t)lb * A.R_up_lstride;
             fixed_rays<LB, VL, TS>(A, F, Rup, A.scale ? A.scale[lb] : 1.0f, px, pz, ox, oz, d, k,
-                                   lane_off, off_hi, R);
+                                   lane_off, R);
         } else {
             float I[VL], T[VL], I0[VL];
-            march_interval<LB, VL>(F, A.nx, A.nz, 0, A.nx, ox, oz, d.x, d.y, A.a, A.b, lane_off, off_hi,
+            march_interval<LB, VL>(F, A.nx, A.nz, 0, A.nx, ox, oz, d.x, d.y, A.a, A.b, lane_off,
                                    A.max_steps, I, T, I0);
             if (HAS_UP) {
                 const TS* Rup = reinterpret_cast<const TS*>(A.R_up) + (size_t)lb * A.R_up_lstride;
@@ -559,12 +557,11 @@ level_split_kernel(const LevelArgs A) {
         const float2 d = A.dirs[k];
         const float ox = ((float)px + 0.5f) * A.spacing, oz = ((float)pz + 0.5f) * A.spacing;
         const float2* F = A.field + (size_t)lb * A.ncell * LB;
-        const unsigned off_hi = (unsigned)((A.ncell - 1) * LB + lane_off);
         const int x0 = (int)((long long)A.phase * A.nx / A.n_strips);
         const int x1 = (int)((long long)(A.phase + 1) * A.nx / A.n_strips);
         float I[VL], T[VL], I0[VL];
         const bool hit = march_interval<LB, VL>(F, A.nx, A.nz, x0, x1, ox, oz, d.x, d.y, A.a,
-                                                A.b, lane_off, off_hi, A.max_steps, I, T, I0);
+                                                A.b, lane_off, A.max_steps, I, T, I0);
         float2* st = A.it_state + (size_t)ray * LB + lane_off;
         // a ray with no piece in a middle strip leaves its partial (I, T) as it is
         if (hit || first || last) {
@@ -616,7 +613,6 @@ __device__ __forceinline__ void level0_body(const LevelArgs& A, int lb, long lon
     const float ox = (float)px + 0.5f, oz = (float)pz + 0.5f;
     const float2* F = A.field + (size_t)lb * A.ncell * LB;
     const int lane_off = q * VL;
-    const unsigned off_hi = (unsigned)((A.ncell - 1) * LB + lane_off);
     const TS* Rup = nullptr;
     float sc = 1.0f;
     if (HAS_UP) {
@@ -638,14 +634,14 @@ __device__ __forceinline__ void level0_body(const LevelArgs& A, int lb, long lon
         if constexpr (FIX && HAS_UP) {
             // the bilinear fix serves J only (no diagonal operator, no J_eff)
             float R[VL];
-            fixed_rays<LB, VL, TS>(A, F, Rup, sc, px, pz, ox, oz, d, k, lane_off, off_hi, R);
+            fixed_rays<LB, VL, TS>(A, F, Rup, sc, px, pz, ox, oz, d, k, lane_off, R);
 #pragma unroll
             for (int j = 0; j < VL; ++j) Jsum[j] += R[j];
             continue;
         }
         float I[VL], T[VL], I0[VL];
         march_interval<LB, VL, true>(F, A.nx, A.nz, 0, A.nx, ox, oz, d.x, d.y, A.a, A.b, lane_off,
-                                     off_hi, A.max_steps, I, T, I0);
+                                     A.max_steps, I, T, I0);
         const float dk = 0.5f / fmaxf(fabsf(d.x), fabsf(d.y));
         float up[VL];
         if (HAS_UP)
@@ -736,12 +732,11 @@ emergent_kernel(const EmergentArgs A) {
     const float4 r = __ldg(reinterpret_cast<const float4*>(A.rays) + ray);
     const float2* F = A.field + (size_t)lb * A.ncell * LB;
     const int lane_off = q * VL;
-    const unsigned off_hi = (unsigned)((A.ncell - 1) * LB + lane_off);
     const int lam0 = lb * LB + lane_off;
     const int n_valid = max(0, min(VL, A.n_lambda - lam0));
     float I[VL], T[VL], I0[VL];
     march_interval<LB, VL, false, CONTRIB>(F, A.nx, A.nz, 0, A.nx, r.x, r.y, r.z, r.w, 0.0f, INFINITY,
-                                           lane_off, off_hi, A.max_steps, I, T, I0,
+                                           lane_off, A.max_steps, I, T, I0,
                                            CONTRIB ? A.contrib + (size_t)lam0 * A.ncell : nullptr,
                                            n_valid, A.ncell);
 #pragma unroll

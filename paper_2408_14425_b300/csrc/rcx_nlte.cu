@@ -42,6 +42,8 @@ struct LineConst {
     double coll;         // n_e-independent van Regemorter factor: beta Omega/(g_l P) = beta (8pi/sqrt3)(E_Ryd/dE) f_lu
     double y_T;          // dE / k: y = y_T / T
     double glo_gup;      // g_l / g_u
+    double ddnu;         // frequency step of the line's grid (Hz); the grid is uniform and
+                         // symmetric about nu0
 };
 
 struct AtomDev {
@@ -84,10 +86,25 @@ __device__ double van_regemorter_p(double y) {
     return fmax(0.2, 0.276 * exp_e1_small(y));
 }
 
-// Gaussian profile value at offset dnu for Doppler width dD (not yet renormalised).
-__device__ __forceinline__ double gauss(double dnu, double dD) {
-    const double u = dnu / dD;
-    return exp(-u * u);
+// The Gaussian exp(-(dnu_k / dD)^2) on a line's uniform grid symmetric about nu0, walked
+// from the centre outwards: with offsets u_j = (j + d) h (h = step / dD, d = 0 for an odd
+// point count, 1/2 for an even one), e_{j+1} = e_j r_j and r_{j+1} = r_j exp(-2 h^2), so
+// three exponentials per line replace one per point (FP64 exponentials are the cost of
+// these kernels); after j products the relative error is a few j ulps.  Calls f(k, e_k)
+// for every grid index k.
+template <class F>
+__device__ __forceinline__ void for_each_gauss(int n, double h, F&& f) {
+    const bool odd = n & 1;
+    double e = odd ? 1.0 : exp(-0.25 * h * h);           // e_0 = exp(-(d h)^2)
+    double r = exp(-(odd ? 1.0 : 2.0) * h * h);           // e_1 / e_0 = exp(-(2d + 1) h^2)
+    const double q = exp(-2.0 * h * h);
+    const int hi = n / 2, lo = odd ? n / 2 : n / 2 - 1;    // the centre point(s)
+    for (int j = 0; hi + j < n; ++j) {
+        f(hi + j, e);
+        if (lo - j != hi + j) f(lo - j, e);
+        e *= r;
+        r *= q;
+    }
 }
 
 __global__ void lte_kernel(AtomDev A, const double* __restrict__ T, const double* __restrict__ nH,
@@ -119,21 +136,19 @@ __global__ void emis_opac_kernel(AtomDev A, const double* __restrict__ T,
     const double sqT = sqrt(T[c]);
     for (int li = 0; li < A.n_lines; ++li) {
         const LineConst& L = A.line[li];
-        const double dD = L.dop * sqT;
-        const double* dnu = A.dnu + (size_t)li * A.n_per_line;
+        const double h = L.ddnu / (L.dop * sqT);
         const double* w = A.w + (size_t)li * A.n_per_line;
         double norm = 0.0;
-        for (int k = 0; k < A.n_per_line; ++k) norm += w[k] * gauss(dnu[k], dD);
+        for_each_gauss(A.n_per_line, h, [&](int k, double g) { norm += w[k] * g; });
         const double nl = pops[(size_t)L.lo * ncell + c], nu = pops[(size_t)L.up * ncell + c];
         // phi_k = gauss / (sqrt(pi) dD) renormalised: the sqrt(pi) dD cancels
         const double kchi = L.hnu_4pi * (nl * L.Blu - nu * L.Bul) / norm;
         const double keta = L.hnu_4pi * nu * L.A / norm;
-        for (int k = 0; k < A.n_per_line; ++k) {
-            const double ph = gauss(dnu[k], dD);
+        for_each_gauss(A.n_per_line, h, [&](int k, double g) {
             const size_t o = (size_t)(L.lam0 + k) * ncell + c;
-            chi[o] = (float)(kchi * ph);
-            eta[o] = (float)(keta * ph);
-        }
+            chi[o] = (float)(kchi * g);
+            eta[o] = (float)(keta * g);
+        });
     }
 }
 
@@ -155,17 +170,16 @@ __global__ void stat_eq_kernel(AtomDev A, const double* __restrict__ T,
             for (int j = 0; j < n; ++j) G[i][j] = 0.0;
         for (int li = 0; li < A.n_lines; ++li) {
             const LineConst& L = A.line[li];
-            const double dD = L.dop * sqT;
-            const double* dnu = A.dnu + (size_t)li * A.n_per_line;
+            const double h = L.ddnu / (L.dop * sqT);
             const double* w = A.w + (size_t)li * A.n_per_line;
             double norm = 0.0, sj = 0.0, sl = 0.0;
-            for (int k = 0; k < A.n_per_line; ++k) {
-                const double wp = w[k] * gauss(dnu[k], dD);
+            for_each_gauss(A.n_per_line, h, [&](int k, double g) {
+                const double wp = w[k] * g;
                 const size_t o = (size_t)(L.lam0 + k) * ncell + c;
                 norm += wp;
                 sj += wp * (double)Jeff[o];
                 if (aloc) sl += wp * (double)aloc[o];
-            }
+            });
             const double Jb = sj / norm;                 // sum_k w phi J_eff
             const double Lc = aloc ? sl / norm : 1.0;    // sum_k w phi (1 - Lambda*)
             const double Rlu = L.Blu * Jb;
@@ -337,6 +351,7 @@ rc_status rc_atom_create(const rc_atom_desc* d, rc_atom_t* out) {
         L.glo_gup = d->g[lo] / d->g[up];
         const double dref = nu0 / kC * std::sqrt(2.0 * kK * d->T_ref / m);
         const double step = 2.0 * d->x_max / (double)(d->n_per_line - 1) * dref;
+        L.ddnu = step;
         for (int k = 0; k < d->n_per_line; ++k) {
             hdnu[(size_t)li * d->n_per_line + k] = (-d->x_max + 2.0 * d->x_max * k / (d->n_per_line - 1)) * dref;
             hw[(size_t)li * d->n_per_line + k] = (k == 0 || k == d->n_per_line - 1) ? 0.5 * step : step;

@@ -44,15 +44,19 @@ def test_lte_start_matches_oracle():
     np.testing.assert_allclose(pops.cpu().numpy(), pops_r, rtol=1e-12)
 
 
-def test_emis_opac_matches_oracle():
+@pytest.mark.parametrize("n_per_line", [21, 20, 7])
+def test_emis_opac_matches_oracle(n_per_line):
+    """Gaussian profiles on the line grids (odd and even point counts: the kernel walks the
+    symmetric grid from its centre) and the emissivity/opacity against the FP64 oracle."""
+    atom_d = dict(ATOM, n_per_line=n_per_line)
     rcx = _rcx()
-    atom = rcx.Atom(ATOM)
+    atom = rcx.Atom(atom_d)
     T, nH, _ = _slab(64)
     ne_r, na_r = nlte.saha_hydrogen(T.ravel(), nH.ravel())
     rng = np.random.default_rng(2)
-    pops = nlte.lte_populations(ATOM, T, na_r) * rng.uniform(0.5, 2.0, (3, T.size))
+    pops = nlte.lte_populations(atom_d, T, na_r) * rng.uniform(0.5, 2.0, (3, T.size))
     chi, eta = atom.emis_opac(_dev(T), _dev(pops))
-    chi_r, eta_r = nlte.emis_opac(ATOM, T, pops)
+    chi_r, eta_r = nlte.emis_opac(atom_d, T, pops)
     np.testing.assert_allclose(chi.cpu().numpy(), chi_r.astype(np.float32), rtol=2e-6)
     np.testing.assert_allclose(eta.cpu().numpy(), eta_r.astype(np.float32), rtol=2e-6)
 

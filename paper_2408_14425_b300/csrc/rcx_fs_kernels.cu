@@ -11,12 +11,14 @@
 //   * Each lane marches front to back (Sec. 3.2 allows either order) with the
 //     piecewise-constant update of Eq. 16 in FP32, keeping the running
 //     transmittance T:  I += T S (1 - e^{-dtau}),  T *= e^{-dtau}.
-//   * The merge of Sec. 2.3.1 is fused into the same kernel: the lane reads the
-//     four child rays of its direction on each of the four bracketing upper
-//     probes (one 16-byte vector per probe and wavelength thanks to the
-//     [ray/4][LB][4] layout of the merged intervals), averages them,
-//     interpolates bilinearly with the edge clamp of Sec. 2.5 and forms
-//     R = I + T * upper (Eq. 11, the nearer interval attenuating the farther one).
+//   * The merge of Sec. 2.3.1 is fused into the same kernel: the lane reads, on each
+//     of the four bracketing upper probes, the average of the four child rays of its
+//     direction (stored once by the upper cascade, one vector per probe), interpolates
+//     bilinearly with the edge clamp of Sec. 2.5 and forms R = I + T * upper (Eq. 11,
+//     the nearer interval attenuating the farther one).  The four sibling rays of a
+//     probe then sum their R across lane groups and store the average for the cascade
+//     below.
+//   * Long cascades over fields larger than L2 run strip by strip (level_split_kernel).
 //   * Cascade 0 folds the W_0 directions of its probe (a cell centre) into J
 //     (Eq. 1) and, optionally, the diagonal operator of Eq. 17.
 // No tensor cores: the march is a gather walk, not a contraction.
@@ -28,9 +30,9 @@
 #include "rcx_internal.h"
 
 // Resident CTAs per SM the cascade kernels are compiled for (register budget
-// 65536 / (256 threads x this)).  6 (40 registers, an 8-byte spill) measured 7% faster
-// than 5 (48 registers) on the 1024^2 x 64 x 8-cascade workload: the march is latency
-// bound on its L2 gathers and the extra resident warps hide more of it.
+// 65536 / (256 threads x this)).  6 (40 registers) measured 7% faster than 5 (48
+// registers) on the 1024^2 x 64 x 8-cascade workload: the extra resident warps hide more
+// of the gather latency.
 #ifndef RCX_MIN_CTAS
 #define RCX_MIN_CTAS 6
 #endif
@@ -49,40 +51,23 @@ template <int VL>
 constexpr int min_ctas() { return VL >= 8 ? RCX_MIN_CTAS_VL8 : RCX_MIN_CTAS; }
 
 // ---------------------------------------------------------------------------
-// storage of merged intervals
+// storage of merged intervals: FP32, or FP16/BF16 with a per-block scale
 // ---------------------------------------------------------------------------
 template <typename TS>
 struct Store;
 
 template <>
 struct Store<float> {
-    static __device__ __forceinline__ float4 load4(const float* p) {
-        return __ldg(reinterpret_cast<const float4*>(p));
-    }
     static __device__ __forceinline__ void store(float* p, float v) { *p = v; }
 };
 
 template <>
 struct Store<__half> {
-    static __device__ __forceinline__ float4 load4(const __half* p) {
-        uint2 u = __ldg(reinterpret_cast<const uint2*>(p));
-        __half2 h0 = *reinterpret_cast<__half2*>(&u.x);
-        __half2 h1 = *reinterpret_cast<__half2*>(&u.y);
-        float2 f0 = __half22float2(h0), f1 = __half22float2(h1);
-        return make_float4(f0.x, f0.y, f1.x, f1.y);
-    }
     static __device__ __forceinline__ void store(__half* p, float v) { *p = __float2half_rn(v); }
 };
 
 template <>
 struct Store<__nv_bfloat16> {
-    static __device__ __forceinline__ float4 load4(const __nv_bfloat16* p) {
-        uint2 u = __ldg(reinterpret_cast<const uint2*>(p));
-        __nv_bfloat162 h0 = *reinterpret_cast<__nv_bfloat162*>(&u.x);
-        __nv_bfloat162 h1 = *reinterpret_cast<__nv_bfloat162*>(&u.y);
-        float2 f0 = __bfloat1622float2(h0), f1 = __bfloat1622float2(h1);
-        return make_float4(f0.x, f0.y, f1.x, f1.y);
-    }
     static __device__ __forceinline__ void store(__nv_bfloat16* p, float v) {
         *p = __float2bfloat16_rn(v);
     }

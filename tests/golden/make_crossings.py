@@ -21,6 +21,8 @@ PLANS = [
 # the 16 domains of the uneven multi-domain workload (sides of batched_domains(), 8 cascades)
 BATCH_SIDES = [256, 320, 640, 768, 1152, 1280, 1408, 1472, 1664, 1728, 1792, 1856, 1920, 1984]
 PLANS += [(s, s, 8, 4, 4, 1.0, 0) for s in BATCH_SIDES if s != 1024]
+# the headline recipe at other sizes (8 cascades), for the size sweep of the benchmark
+PLANS += [(512, 512, 8, 4, 4, 1.0, 0), (2048, 2048, 8, 4, 4, 1.0, 0)]
 
 
 def key(p):

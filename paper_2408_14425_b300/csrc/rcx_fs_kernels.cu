@@ -288,6 +288,14 @@ __device__ __forceinline__ bool march_interval(const float2* __restrict__ F, int
     return true;
 }
 
+// Column and row of a probe (or cell) index on a grid P wide.  Probe and cell counts are
+// below 2^31 (rc_plan keeps nx nz LB below it), so the division runs in 32 bits.
+__device__ __forceinline__ void grid_xy(long long idx, int P, int& x, int& z) {
+    const unsigned u = (unsigned)idx, zz = u / (unsigned)P;
+    z = (int)zz;
+    x = (int)(u - zz * (unsigned)P);
+}
+
 // Clamped bilinear coordinate of a cascade-i probe index m in the index space
 // of cascade i+1 (probe positions (m+1/2) 2^i and (j+1/2) 2^(i+1)).
 __device__ __forceinline__ void upper_coord(int m, int P_up, int& j0, int& j1, float& f) {
@@ -538,14 +546,14 @@ level_split_kernel(const LevelArgs A) {
         }
         if (A.probe_list) probe = A.probe_list[probe];
         sray = probe * A.W + k;
-        const int px = (int)(probe % A.Px), pz = (int)(probe / A.Px);
+        int px, pz;
+        grid_xy(probe, A.Px, px, pz);
         const float2 d = A.dirs[k];
         const float ox = ((float)px + 0.5f) * A.spacing, oz = ((float)pz + 0.5f) * A.spacing;
         const float2* F = A.field + (size_t)lb * A.ncell * LB;
-        const int x0 = (int)((long long)A.phase * A.nx / A.n_strips);
-        const int x1 = (int)((long long)(A.phase + 1) * A.nx / A.n_strips);
         float I[VL], T[VL], I0[VL];
-        const bool hit = march_interval<LB, VL>(F, A.nx, A.nz, x0, x1, ox, oz, d.x, d.y, A.a,
+        const bool hit = march_interval<LB, VL>(F, A.nx, A.nz, A.strip_x0, A.strip_x1, ox, oz,
+                                                d.x, d.y, A.a,
                                                 A.b, lane_off, A.max_steps, I, T, I0);
         float2* st = A.it_state + (size_t)ray * LB + lane_off;
         // a ray with no piece in a middle strip leaves its partial (I, T) as it is
@@ -594,7 +602,8 @@ __device__ __forceinline__ void level0_body(const LevelArgs& A, int lb, long lon
     long long cell = wid * G + g;
     if (cell >= A.rays) return;                       // rays = cells (or flagged cells) here
     if (A.probe_list) cell = A.probe_list[cell];
-    const int px = (int)(cell % A.nx), pz = (int)(cell / A.nx);
+    int px, pz;
+    grid_xy(cell, A.nx, px, pz);
     const float ox = (float)px + 0.5f, oz = (float)pz + 0.5f;
     const float2* F = A.field + (size_t)lb * A.ncell * LB;
     const int lane_off = q * VL;
@@ -1113,12 +1122,16 @@ bool level_split_supported(int LB, int VL) { return VL == 4 && (LB == 8 || LB ==
 
 cudaError_t launch_level_split(int LB, int VL, int precision, bool has_up, const LevelArgs& a,
                                cudaStream_t s) {
-    if (!level_split_supported(LB, VL) || a.n_strips < 2 || !a.it_state)
+    if (!level_split_supported(LB, VL) || a.n_strips < 2 || !a.it_state || a.phase < 0 ||
+        a.phase >= a.n_strips)
         return cudaErrorInvalidValue;
+    LevelArgs b = a;
+    b.strip_x0 = (int)((long long)a.phase * a.nx / a.n_strips);
+    b.strip_x1 = (int)((long long)(a.phase + 1) * a.nx / a.n_strips);
     switch (LB) {
-        case 8: return level_split_p<8>(precision, has_up, a, s);
-        case 16: return level_split_p<16>(precision, has_up, a, s);
-        case 32: return level_split_p<32>(precision, has_up, a, s);
+        case 8: return level_split_p<8>(precision, has_up, b, s);
+        case 16: return level_split_p<16>(precision, has_up, b, s);
+        case 32: return level_split_p<32>(precision, has_up, b, s);
     }
     return cudaErrorInvalidValue;
 }

@@ -527,7 +527,7 @@ level_split_kernel(const LevelArgs A) {
     const int g = lane / LPR, q = lane % LPR;
     const long long ray = ((long long)blockIdx.x * kWarpsPerCta + (threadIdx.x >> 5)) * G + g;
     const int lane_off = q * VL;
-    const int lb = A.split_lb;
+    const int lb = A.split_lb + (int)blockIdx.y;
     const bool valid = ray < A.rays;
     const bool first = A.phase == 0, last = A.phase == A.n_strips - 1;
     float R[VL];
@@ -555,7 +555,7 @@ level_split_kernel(const LevelArgs A) {
         const bool hit = march_interval<LB, VL>(F, A.nx, A.nz, A.strip_x0, A.strip_x1, ox, oz,
                                                 d.x, d.y, A.a,
                                                 A.b, lane_off, A.max_steps, I, T, I0);
-        float2* st = A.it_state + (size_t)ray * LB + lane_off;
+        float2* st = A.it_state + ((size_t)blockIdx.y * A.rays + ray) * LB + lane_off;
         // a ray with no piece in a middle strip leaves its partial (I, T) as it is
         if (hit || first || last) {
             if (!first) {
@@ -1101,7 +1101,7 @@ static cudaError_t level_split_t(bool has_up, const LevelArgs& a, cudaStream_t s
     constexpr int G = 32 / (LB / 4);
     if (a.rays == 0) return cudaSuccess;
     const long long per_cta = (long long)G * kWarpsPerCta;
-    const dim3 grid((unsigned)((a.rays + per_cta - 1) / per_cta));
+    const dim3 grid((unsigned)((a.rays + per_cta - 1) / per_cta), (unsigned)a.split_nblk);
     if (has_up) level_split_kernel<LB, 4, TS, true><<<grid, kWarpsPerCta * 32, 0, s>>>(a);
     else level_split_kernel<LB, 4, TS, false><<<grid, kWarpsPerCta * 32, 0, s>>>(a);
     return cudaGetLastError();
@@ -1123,9 +1123,10 @@ bool level_split_supported(int LB, int VL) { return VL == 4 && (LB == 8 || LB ==
 cudaError_t launch_level_split(int LB, int VL, int precision, bool has_up, const LevelArgs& a,
                                cudaStream_t s) {
     if (!level_split_supported(LB, VL) || a.n_strips < 2 || !a.it_state || a.phase < 0 ||
-        a.phase >= a.n_strips)
+        a.phase >= a.n_strips || a.split_nblk < 0 || a.split_nblk > 65535)
         return cudaErrorInvalidValue;
     LevelArgs b = a;
+    b.split_nblk = std::max(1, a.split_nblk);
     b.strip_x0 = (int)((long long)a.phase * a.nx / a.n_strips);
     b.strip_x1 = (int)((long long)(a.phase + 1) * a.nx / a.n_strips);
     switch (LB) {

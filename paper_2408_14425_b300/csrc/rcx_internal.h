@@ -60,10 +60,11 @@ struct LevelArgs {
     int n_lambda;
     int max_steps;           // upper bound on cells crossed by one ray (nx + nz + 2)
     // strip-split march (launch_level_split): partial (I, T) of every ray of one lambda
-    // block [ray][LB], the strip count, this launch's phase and lambda block, and the
-    // strip's columns [strip_x0, strip_x1) (set by launch_level_split)
+    // block [block][ray][LB], the strip count, this launch's phase, its first lambda block
+    // and block count (0 counts as 1), and the strip's columns [strip_x0, strip_x1) (set by
+    // launch_level_split)
     float2* it_state;
-    int n_strips, phase, split_lb;
+    int n_strips, phase, split_lb, split_nblk;
     int strip_x0, strip_x1;
 };
 

@@ -163,6 +163,15 @@ int strips_for_impl(const rc_plan_s* p, int i) {
     return std::min(std::min(16, p->nx), std::max(2, (int)std::lround(block / kStrip)));
 }
 
+// Lambda blocks that one strip launch covers: all of them while their partial (I, T) fits in
+// 2 GiB.  The hardware hands out CTAs in index order, block after block, so the gathers in
+// flight still come from one block's strip; one launch per strip instead of one per block
+// and strip leaves one launch tail per strip.
+int split_blocks(size_t per_blk, int n_lblk) {
+    constexpr size_t kItBudget = size_t(2) << 30;
+    return (int)std::max<size_t>(1, std::min<size_t>((size_t)n_lblk, kItBudget / per_blk));
+}
+
 rc_status ensure_scratch(rc_plan_s* p, int n_lambda) {
     n_lambda *= p->n_incl;                           // virtual wavelengths
     if (n_lambda <= p->cap_lambda) return RC_OK;
@@ -175,11 +184,14 @@ rc_status ensure_scratch(rc_plan_s* p, int n_lambda) {
     // merged intervals hold one child average per 4 rays
     const size_t Rb = std::max<size_t>(1, n_lblk * (size_t)(max_rays / 4) * LB *
                                               storage_bytes(p->opt.precision));
-    // strip-split cascades keep (I, T) per ray and wavelength of one block between launches
+    // strip-split cascades keep (I, T) per ray and wavelength between launches, for as many
+    // lambda blocks as one launch covers (split_blocks)
     size_t itb = 0;
     for (int i = 1; i < p->C; ++i)
-        if (strips_for_impl(p, i) > 1)
-            itb = std::max(itb, (size_t)p->lv[i].rays() * LB * sizeof(float2));
+        if (strips_for_impl(p, i) > 1) {
+            const size_t per_blk = (size_t)p->lv[i].rays() * LB * sizeof(float2);
+            itb = std::max(itb, per_blk * split_blocks(per_blk, (int)n_lblk));
+        }
     cudaDeviceSynchronize();  // scratch may be in use by work still queued
     free_scratch(p);
     cudaError_t e = cudaSuccess;
@@ -304,12 +316,15 @@ rc_status solve_device(rc_plan_s* p, const float* chi, const float* eta, int n_l
         const bool has_up = i < live - 1;
         const int S = strips_for_impl(p, i);
         if (S > 1) {
-            // one wavelength block at a time, one launch per strip
+            // one launch per strip, over as many wavelength blocks as it_state holds
+            const size_t per_blk = (size_t)a.rays * LB * sizeof(float2);
+            const int G = std::max(1, std::min(n_lblk, (int)(p->it_bytes / per_blk)));
             a.it_state = p->d_it;
             a.n_strips = S;
-            for (int lb = 0; lb < n_lblk; ++lb)
+            for (int lb = 0; lb < n_lblk; lb += G)
                 for (int ph = 0; ph < S; ++ph) {
                     a.split_lb = lb;
+                    a.split_nblk = std::min(G, n_lblk - lb);
                     a.phase = ph;
                     if ((e = rcx::launch_level_split(LB, p->VL, p->opt.precision, has_up, a, s)) !=
                         cudaSuccess)

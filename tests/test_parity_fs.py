@@ -320,14 +320,16 @@ def test_free_space_cascades_are_not_launched(n, C, launched):
         _assert_close(J.cpu().numpy(), _oracle(chi, eta, C), 1e-3, f"{n} C{C}")
 
 
-@pytest.mark.parametrize("nx,nz,C,strips,prec", [(96, 80, 5, 3, "f32"), (130, 67, 6, 4, "f32"),
-                                                 (64, 64, 5, 16, "f32"), (96, 80, 5, 2, "bf16")])
-def test_strip_split_march_matches_unsplit_and_oracle(nx, nz, C, strips, prec):
+@pytest.mark.parametrize("nx,nz,C,strips,prec,nl", [(96, 80, 5, 3, "f32", 5), (130, 67, 6, 4, "f32", 5),
+                                                    (64, 64, 5, 16, "f32", 5), (96, 80, 5, 2, "bf16", 5),
+                                                    (96, 80, 5, 3, "f32", 40)])
+def test_strip_split_march_matches_unsplit_and_oracle(nx, nz, C, strips, prec, nl):
     """Every cascade >= 1 marched strip by strip (one launch per vertical strip, partial
     (I, T) composed front to back or back to front by the ray's x direction) gives the
-    unsplit result up to FP32 rounding, and the oracle's."""
+    unsplit result up to FP32 rounding, and the oracle's.  With 40 wavelengths one strip
+    launch covers three wavelength blocks, the last one ragged."""
     rcx = _rcx()
-    chi, eta = W.grf_fields(nx, 5, nz=nz)
+    chi, eta = W.grf_fields(nx, nl, nz=nz)
     dchi, deta = torch.from_numpy(chi).cuda(), torch.from_numpy(eta).cuda()
     whole = rcx.Plan(nx, nz, C, precision=prec, strips=1)
     split = rcx.Plan(nx, nz, C, precision=prec, strips=strips)
@@ -360,9 +362,10 @@ def test_strip_split_with_sparsity_and_mali():
 def test_strip_split_automatic_at_1024():
     """At 1024^2 with 16 wavelengths per block (128 MiB of packed field) cascade 5 (intervals
     from 341 to the far corner) runs in 2 strips; cascade 4 (256 voxels long) and cascade 6
-    (38 voxels inside the domain) do not."""
+    (38 voxels inside the domain) do not.  Each strip launch covers all three wavelength
+    blocks (their partial (I, T), 3 x 512 MiB, fits the 2 GiB it keeps for them)."""
     rcx = _rcx()
-    chi, eta = W.grf_fields(1024, 16, lambdas=range(16))
+    chi, eta = W.grf_fields(1024, 48, lambdas=range(48))
     dchi, deta = torch.from_numpy(chi).cuda(), torch.from_numpy(eta).cuda()
     auto = rcx.Plan(1024, 1024, 8)
     whole = rcx.Plan(1024, 1024, 8, strips=1)
@@ -372,6 +375,7 @@ def test_strip_split_automatic_at_1024():
     n_whole = whole.last_launch_count()
     torch.cuda.synchronize()
     assert n_whole == 1 + 7 and n_auto == n_whole + 1     # pack + cascades 6..0; c5 in 2 strips
+    assert auto.scratch_bytes() - whole.scratch_bytes() == 3 * 4194304 * 16 * 8
     _assert_close(Ja.cpu().numpy(), Jw.cpu().numpy(), 5e-4, "auto strips vs whole")
 
 

@@ -198,9 +198,13 @@ rc_status build(rc_batch_s* b, bool first_block_only = false) {
             a.it_state = p->d_it;
             a.n_strips = S;
             const int n_lblk = first_block_only ? 1 : (b->nl[d] + LB - 1) / LB;
-            for (int lb = 0; lb < n_lblk && le == cudaSuccess; ++lb)
+            // as many wavelength blocks per launch as the plan's it_state holds
+            const size_t per_blk = (size_t)a.rays * LB * sizeof(float2);
+            const int G = std::max(1, std::min(n_lblk, (int)(p->it_bytes / per_blk)));
+            for (int lb = 0; lb < n_lblk && le == cudaSuccess; lb += G)
                 for (int ph = 0; ph < S && le == cudaSuccess; ++ph, ++launches) {
                     a.split_lb = lb;
+                    a.split_nblk = std::min(G, n_lblk - lb);
                     a.phase = ph;
                     le = rcx::launch_level_split(LB, b->VL, b->precision, i < C - 1, a, b->cap);
                 }

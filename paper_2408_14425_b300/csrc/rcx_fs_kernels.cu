@@ -687,26 +687,30 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, min_ctas<VL>())
 batched_level_kernel(const BatchLevelArgs B) {
     static_assert(sizeof(LevelArgs) % sizeof(int) == 0, "LevelArgs is copied word by word");
     __shared__ __align__(16) int sargs[sizeof(LevelArgs) / sizeof(int)];
-    __shared__ int sseg;
+    __shared__ int s_dom, s_lblk;
+    __shared__ long long s_first;
     const long long t = blockIdx.x;
-    if (threadIdx.x == 0) {
-        int lo = 0, hi = B.n_seg - 1;
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (B.prefix[mid] <= t) lo = mid;
-            else hi = mid - 1;
+    // The segment holding chunk t is the one non-empty j with prefix[j] <= t < prefix[j+1]:
+    // the threads test one segment each, all loads in flight at once (one memory round trip
+    // instead of a serial binary search), and the match publishes its segment.
+    for (int j = threadIdx.x; j < B.n_seg; j += blockDim.x) {
+        const long long lo = B.prefix[j];
+        const long long hi = j + 1 < B.n_seg ? B.prefix[j + 1] : B.total;
+        const int dom = B.seg_domain[j], lblk = B.seg_lblk[j];
+        if (lo <= t && t < hi) {
+            s_dom = dom;
+            s_lblk = lblk;
+            s_first = lo;
         }
-        sseg = lo;
     }
     __syncthreads();
-    const int seg = sseg;
-    const int* src = reinterpret_cast<const int*>(B.args + B.seg_domain[seg]);
+    const int* src = reinterpret_cast<const int*>(B.args + s_dom);
     for (int w = threadIdx.x; w < (int)(sizeof(LevelArgs) / sizeof(int)); w += blockDim.x)
         sargs[w] = src[w];
     __syncthreads();
     const LevelArgs& A = *reinterpret_cast<const LevelArgs*>(sargs);
-    if (LEVEL0) level0_body<LB, VL, TS, HAS_UP>(A, B.seg_lblk[seg], t - B.prefix[seg]);
-    else level_body<LB, VL, TS, HAS_UP>(A, B.seg_lblk[seg], t - B.prefix[seg]);
+    if (LEVEL0) level0_body<LB, VL, TS, HAS_UP>(A, s_lblk, t - s_first);
+    else level_body<LB, VL, TS, HAS_UP>(A, s_lblk, t - s_first);
 }
 
 // ---------------------------------------------------------------------------

@@ -231,10 +231,13 @@ rc_status rc_plan_autotune(rc_plan_t plan, const float* chi, const float* eta, i
  * Batched formal solutions (independent problems solved together, Sec. 3.6: wavelengths and
  * domains are independent).  A batch binds n plans (same n_cascades, storage precision and
  * device; every plan is switched to the first plan's lane layout) to fixed device buffers
- * chi[d], eta[d], J[d] ([n_lambda[d]][nz_d][nx_d]).  Each cascade is ONE launch over a work
- * list of CTA-sized chunks of every (domain, wavelength block), sorted by estimated cost
- * (interval length a ray can march, longest first), one chunk per CTA; packing is one launch
- * for all domains.  The whole sequence is captured once into a CUDA graph; rc_batch_run
+ * chi[d], eta[d], J[d] ([n_lambda[d]][nz_d][nx_d]).  A domain large enough to fill the GPU
+ * on its own (at least 4 waves of CTAs, counted at 6 per SM, in every cascade that is not in
+ * free space) keeps its own launch sequence, that of rc_formal_solve.  For the other
+ * domains each cascade is ONE launch over a work list of CTA-sized chunks of every (domain,
+ * wavelength block), sorted by estimated cost (interval length a ray can march, longest
+ * first), one chunk per CTA; packing is one launch for all of them.  The whole sequence is
+ * captured once into a CUDA graph; rc_batch_run
  * replays it on `stream` (asynchronous).  With autotune != 0 creation times graph replays of
  * the candidate lane layouts (16/4, 8/4, 32/4, 8/2, 4/4) on the first wavelength block of
  * every bound domain, ranks them by time per wavelength slice and keeps the fastest.
@@ -249,6 +252,8 @@ rc_status rc_batch_create(int n, const rc_plan_t* plans, const float* const* chi
 rc_status rc_batch_run(rc_batch_t batch, void* stream);
 rc_status rc_batch_info(rc_batch_t batch, int* launches_per_run, int* lambda_block,
                         int* lambda_per_lane);
+/* Number of bound domains that keep their own launch sequence (-1 if batch is NULL). */
+int rc_batch_solo_domains(rc_batch_t batch);
 void rc_batch_destroy(rc_batch_t batch);
 
 /* One-shot batched solve: rc_batch_create + rc_batch_run + synchronise + rc_batch_destroy. */

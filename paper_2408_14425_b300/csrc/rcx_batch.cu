@@ -1,8 +1,12 @@
 // rcx_batch.cu -- many independent formal solutions (domains of uneven sizes, each with
-// its own wavelength count) run as one launch per cascade over a work list of CTA-sized
-// chunks, segments sorted by estimated cost, and the whole sequence captured once in a
-// CUDA graph.  An optional native autotuner picks the lane layout by timing graph replays
-// of the candidates on a sample of the batch (the first wavelength block of each domain).
+// its own wavelength count) captured once in a CUDA graph.  A domain that fills the GPU on
+// its own (at least kSoloWaves waves of CTAs in every live cascade) runs its own launch
+// sequence, as rc_formal_solve would: its cascades follow one another while the merged
+// intervals they pass on are still in L2, and its free-space cascades are skipped.  The
+// smaller domains share one launch per cascade over a work list of CTA-sized chunks,
+// segments sorted by estimated cost.  An optional native autotuner picks the lane layout by
+// timing graph replays of the candidates on a sample of the batch (the first wavelength
+// block of each domain).
 #include <algorithm>
 #include <cmath>
 #include <new>
@@ -47,6 +51,7 @@ struct rc_batch_s {
     cudaStream_t cap = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
+    std::vector<char> solo;                    // per domain: runs its own launch sequence
     int launches = 0;
     int LB = 0, VL = 0, precision = 0;
 };
@@ -77,18 +82,37 @@ rc_status build(rc_batch_s* b, bool first_block_only = false) {
         rc_status st = rcx::plan_reserve(b->plans[d], b->nl[d]);
         if (st != RC_OK) return st;
     }
-    // per-cascade segment tables, chunks sorted by estimated cost (the interval length
-    // a ray can actually march: min(b - a, domain diagonal) per chunk of rays)
+    // domains that fill the GPU alone: every live cascade has kSoloWaves waves of CTAs (the
+    // march kernels keep up to 6 CTAs on an SM)
+    constexpr int kSoloWaves = 4, kCtasPerSm = 6;
+    const int G_rays = 32 / (LB / b->VL) * rcx::kWarpsPerCta;
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device);
+    const long long resident = (long long)sms * kCtasPerSm;
+    b->solo.assign(n, 0);
+    for (int d = 0; d < n; ++d) {
+        rc_plan_s* p = b->plans[d];
+        const int n_lblk = first_block_only ? 1 : (b->nl[d] + LB - 1) / LB;
+        long long least = -1;
+        for (int i = 0; i < rcx::live_cascade_count(p); ++i) {
+            const long long items = i == 0 ? (long long)p->nx * p->nz : p->lv[i].rays();
+            const long long chunks = (items + G_rays - 1) / G_rays * n_lblk;
+            least = least < 0 ? chunks : std::min(least, chunks);
+        }
+        b->solo[d] = least >= kSoloWaves * resident;
+    }
+    // per-cascade segment tables of the shared launches, chunks sorted by estimated cost (the
+    // interval length a ray can actually march: min(b - a, domain diagonal) per chunk of rays)
     std::vector<LevelTables> T(C + 1);
     std::vector<rcx::LevelArgs> args((size_t)C * n);
     std::vector<rcx::PackArgs> pargs(n);
-    const int G_rays = 32 / (LB / b->VL) * rcx::kWarpsPerCta;
     for (int i = 0; i < C; ++i) {
         struct Seg { double cost; int d, lb; long long chunks; };
         std::vector<Seg> segs;
         for (int d = 0; d < n; ++d) {
             rc_plan_s* p = b->plans[d];
             args[(size_t)i * n + d] = rcx::level_args(p, i, b->nl[d], b->J[d], nullptr, nullptr, nullptr);
+            if (b->solo[d]) continue;
             if (rcx::strips_for(p, i) > 1) continue;   // launched strip by strip after the batch
             const long long items = i == 0 ? (long long)p->nx * p->nz : p->lv[i].rays();
             const long long chunks = (items + G_rays - 1) / G_rays;
@@ -107,6 +131,7 @@ rc_status build(rc_batch_s* b, bool first_block_only = false) {
     }
     for (int d = 0; d < n; ++d) {
         rc_plan_s* p = b->plans[d];
+        if (b->solo[d]) continue;
         pargs[d] = rcx::PackArgs{b->chi[d], b->eta[d], b->nl[d], 1, nullptr, nullptr,
                                  (long long)p->nx * p->nz, (float)p->voxel, p->d_packed,
                                  p->opt.precision != RC_STORE_F32 ? p->d_smax : nullptr};
@@ -148,8 +173,6 @@ rc_status build(rc_batch_s* b, bool first_block_only = false) {
         return bcuda(e, "rc_batch: table upload");
 
     // cascade launches: one CTA per chunk, handed out in index order by the hardware
-    int sms = 0;
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device);
     b->grid.assign(C, 0);
     for (int i = 0; i < C; ++i) {
         int occ = 0;
@@ -170,19 +193,35 @@ rc_status build(rc_batch_s* b, bool first_block_only = false) {
     int launches = 0;
     const bool f16 = b->precision != RC_STORE_F32;
     cudaError_t le = cudaSuccess;
-    if (f16)
+    rc_status sst = RC_OK;
+    // the domains that fill the GPU alone, one after another, each with its own sequence
+    for (int d = 0; d < n && sst == RC_OK; ++d) {
+        if (!b->solo[d]) continue;
+        rc_plan_s* p = b->plans[d];
+        sst = rcx::solve_sequence(p, b->chi[d], b->eta[d],
+                                  first_block_only ? std::min(b->nl[d], LB) : b->nl[d], b->J[d], b->cap);
+        launches += p->last_launches;
+    }
+    if (sst != RC_OK) le = cudaErrorUnknown;
+    const bool shared = b->pack.total > 0;
+    if (f16 && shared)
         for (int d = 0; d < n && le == cudaSuccess; ++d) {
+            if (b->solo[d]) continue;
             rc_plan_s* p = b->plans[d];
             le = cudaMemsetAsync(p->d_smax, 0, p->aux_count * sizeof(unsigned), b->cap);
         }
-    if (le == cudaSuccess) le = rcx::launch_batched_pack(LB, b->pack, b->pack_grid, b->cap);
-    ++launches;
-    if (f16)
-        for (int d = 0; d < n && le == cudaSuccess; ++d, ++launches) {
+    if (le == cudaSuccess && shared) {
+        le = rcx::launch_batched_pack(LB, b->pack, b->pack_grid, b->cap);
+        ++launches;
+    }
+    if (f16 && shared)
+        for (int d = 0; d < n && le == cudaSuccess; ++d) {
+            if (b->solo[d]) continue;
             rc_plan_s* p = b->plans[d];
             le = rcx::launch_scales((b->nl[d] + LB - 1) / LB, p->d_smax, p->d_scale, b->cap);
+            ++launches;
         }
-    for (int i = C - 1; i >= 0 && le == cudaSuccess; --i) {
+    for (int i = C - 1; i >= 0 && le == cudaSuccess && shared; --i) {
         if (b->level[i].total > 0) {
             le = rcx::launch_batched_level(LB, b->VL, b->precision, i == 0, i < C - 1, b->level[i],
                                            b->grid[i], b->cap, nullptr);
@@ -193,7 +232,7 @@ rc_status build(rc_batch_s* b, bool first_block_only = false) {
         for (int d = 0; d < n && le == cudaSuccess; ++d) {
             rc_plan_s* p = b->plans[d];
             const int S = rcx::strips_for(p, i);
-            if (S < 2) continue;
+            if (S < 2 || b->solo[d]) continue;
             rcx::LevelArgs a = args[(size_t)i * n + d];
             a.it_state = p->d_it;
             a.n_strips = S;
@@ -211,6 +250,7 @@ rc_status build(rc_batch_s* b, bool first_block_only = false) {
         }
     }
     e = cudaStreamEndCapture(b->cap, &b->graph);
+    if (sst != RC_OK) return sst;
     if (le != cudaSuccess) return bcuda(le, "rc_batch: launch during capture");
     if (e != cudaSuccess) return bcuda(e, "rc_batch: end capture");
     if ((e = cudaGraphInstantiate(&b->exec, b->graph, 0)) != cudaSuccess)
@@ -330,6 +370,11 @@ rc_status rc_batch_info(rc_batch_t b, int* launches_per_run, int* lambda_block,
     if (lambda_block) *lambda_block = b->LB;
     if (lambda_per_lane) *lambda_per_lane = b->VL;
     return RC_OK;
+}
+
+int rc_batch_solo_domains(rc_batch_t b) {
+    if (!b) return -1;
+    return (int)std::count(b->solo.begin(), b->solo.end(), 1);
 }
 
 void rc_batch_destroy(rc_batch_t b) {

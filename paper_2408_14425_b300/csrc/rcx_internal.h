@@ -164,6 +164,12 @@ inline size_t packed_guard_bytes(int nx, int LB) {
 }
 // strips of the strip-split march of cascade i of a plan (1 = not split)
 int strips_for(const rc_plan_s* p, int i);
+// cascades 0 .. live-1 of a plan can be non-zero (the rest lie in free space)
+int live_cascade_count(const rc_plan_s* p);
+// the launch sequence of rc_formal_solve (J only) on stream s, without its timing events;
+// the plan's scratch must already hold n_lambda (nothing is allocated, so it may be captured)
+rc_status solve_sequence(rc_plan_s* p, const float* chi, const float* eta, int n_lambda, float* J,
+                         cudaStream_t s);
 rc_status plan_set_layout(rc_plan_s* p, int LB, int VL);
 // Device tables of an atom's levels: E/k [K] and g (rcx_nlte.cu).
 rc_status atom_levels(rc_atom_t a, const double** Ek, const double** g, int* nlev,

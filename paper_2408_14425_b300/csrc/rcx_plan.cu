@@ -360,6 +360,19 @@ rc_status solve_device(rc_plan_s* p, const float* chi, const float* eta, int n_l
 
 int rcx::strips_for(const rc_plan_s* p, int i) { return strips_for_impl(p, i); }
 
+int rcx::live_cascade_count(const rc_plan_s* p) { return live_cascades(p); }
+
+rc_status rcx::solve_sequence(rc_plan_s* p, const float* chi, const float* eta, int n_lambda,
+                              float* J, cudaStream_t s) {
+    if (n_lambda * p->n_incl > p->cap_lambda)
+        return fail(RC_ERR_ARG, "solve_sequence: the plan's scratch is too small");
+    const bool timing_was = p->timing;
+    p->timing = false;
+    const rc_status st = solve_device(p, chi, eta, n_lambda, J, nullptr, s);
+    p->timing = timing_was;
+    return st;
+}
+
 rcx::LevelArgs rcx::level_args(const rc_plan_s* p, int i, int n_lambda, float* J, float* alo,
                                float* J_eff, float* alo_c) {
     const rcx::LevelGeom& g = p->lv[i];

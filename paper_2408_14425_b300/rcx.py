@@ -35,7 +35,7 @@ EXPORTS = [
     "rc_surrogate_features", "rc_surrogate_targets", "rc_surrogate_seed", "rc_plan_set_active",
     "rc_plan_active_probes", "rc_emergent", "rc_mlp_use_tensor_cores", "rc_mlp_tensor_core_status",
     "rc_selftest_bounded_wait", "rc_surrogate_init", "rc_surrogate_train_step",
-    "rc_surrogate_predict",
+    "rc_surrogate_predict", "rc_batch_solo_domains",
 ]
 
 
@@ -153,6 +153,8 @@ def load():
     L.rc_batch_run.restype = ctypes.c_int
     L.rc_batch_info.argtypes = [_vp, _ip, _ip, _ip]
     L.rc_batch_info.restype = ctypes.c_int
+    L.rc_batch_solo_domains.argtypes = [_vp]
+    L.rc_batch_solo_domains.restype = ctypes.c_int
     L.rc_batch_destroy.argtypes = [_vp]
     L.rc_batch_destroy.restype = None
     L.rc_formal_solve_batched.argtypes = [ctypes.c_int, _pp, _pp, _pp, _ip, _pp, _vp]
@@ -543,7 +545,8 @@ class Batch:
     def info(self):
         a, b, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
         check(load().rc_batch_info(self._h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
-        return dict(launches=a.value, lambda_block=b.value, lambda_per_lane=c.value)
+        return dict(launches=a.value, lambda_block=b.value, lambda_per_lane=c.value,
+                    solo_domains=load().rc_batch_solo_domains(self._h))
 
     def close(self):
         if getattr(self, "_h", None):

@@ -1,4 +1,5 @@
-"""Batched formal solutions (persistent launch per cascade over a cost-sorted work list,
+"""Batched formal solutions (one launch per cascade over a cost-sorted work list, or a
+domain's own launch sequence when it fills the GPU alone,
 captured in a CUDA graph) against the per-domain path and the FP64 oracle, with FP32,
 FP16 and BF16 interval storage, and the lane-layout autotuners."""
 import numpy as np
@@ -56,6 +57,25 @@ def test_batch_matches_single_domain_path_and_oracle(prec):
         J_ref, _, _ = oracle.rc_solve(chi[lam].astype(np.float64), eta[lam].astype(np.float64), 6)
         _close(Js[d][lam].cpu().numpy(), J_ref, 1e-3 if prec == "f32" else 5e-3,
                f"{prec} domain {d}")
+    batch.close()
+
+
+def test_solo_and_shared_domains_in_one_graph():
+    """A 384^2 domain with 48 wavelengths fills the GPU alone in every cascade (2304 to 9216
+    CTAs per wavelength block), so it keeps its own launch sequence inside the graph; the
+    three small domains share the per-cascade launches.  Every domain equals its single
+    solve bit for bit, and the solo domain matches the oracle."""
+    doms = [(384, 384, 48), (64, 64, 5), (96, 80, 9), (40, 72, 3)]
+    rcx, plans, chis, etas, Js, host = _batch_inputs(doms, 6)
+    batch = rcx.Batch(plans, chis, etas, Js)
+    batch.run()
+    torch.cuda.synchronize()
+    assert batch.info()["solo_domains"] == 1
+    for d, p in enumerate(plans):
+        np.testing.assert_array_equal(Js[d].cpu().numpy(), p.formal_solve(chis[d], etas[d]).cpu().numpy())
+    chi, eta = host[0]
+    J_ref, _, _ = oracle.rc_solve(chi[47].astype(np.float64), eta[47].astype(np.float64), 6)
+    _close(Js[0][47].cpu().numpy(), J_ref, 1e-3, "solo domain")
     batch.close()
 
 

@@ -7,7 +7,8 @@
 // Work layout: one CTA of 256 threads per tile of 128 samples holds the weights and the
 // tile's activations in shared memory (about 150 KB) and runs the forward pass, the loss
 // and (for training) the whole backward pass; weight gradients are summed over the tile
-// and added to the global gradient with one atomic per weight per tile.
+// and stored as the tile's partial gradient, which a second kernel sums over the tiles in
+// a fixed order, so training is bit-for-bit reproducible.
 #include <cuda_bf16.h>
 
 #include <cmath>
@@ -58,8 +59,10 @@ template <bool TRAIN>
 __global__ void __launch_bounds__(THREADS)
 mlp_tile_kernel(const float* __restrict__ wbf, const float* __restrict__ norm,
                 const float* __restrict__ X, const float* __restrict__ Yt, long long B,
-                float* __restrict__ Y, float* __restrict__ grad, float* __restrict__ loss) {
+                float* __restrict__ Y, float* __restrict__ part) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    // this tile's partial gradient [NPARAM] and loss (training only)
+    float* const grad = TRAIN ? part + (size_t)blockIdx.x * (NPARAM + 1) : nullptr;
     Smem& S = *reinterpret_cast<Smem*>(smem_raw);
     const int tid = threadIdx.x;
     const long long s0 = (long long)blockIdx.x * TILE;
@@ -133,7 +136,7 @@ mlp_tile_kernel(const float* __restrict__ wbf, const float* __restrict__ norm,
         }
     }
     if constexpr (TRAIN) {
-    // loss: block sum, one atomic
+    // loss: block sum
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) lsum += __shfl_xor_sync(0xffffffffu, lsum, o);
     if ((tid & 31) == 0) S.red[tid >> 5] = lsum;
@@ -141,19 +144,19 @@ mlp_tile_kernel(const float* __restrict__ wbf, const float* __restrict__ norm,
     if (tid == 0) {
         float t = 0.0f;
         for (int w = 0; w < THREADS / 32; ++w) t += S.red[w];
-        atomicAdd(loss, t / (float)(B * NO));
+        grad[NPARAM] = t / (float)(B * NO);
     }
     // dW3, db3
     if (tid < NO * NH) {
         const int o = tid / NH, k = tid % NH;
         float g = 0.0f;
         for (int s = 0; s < TILE; ++s) g = fmaf(S.dy[s * NO + o], S.h2[s * LD + k], g);
-        atomicAdd(grad + OFF_W3 + tid, g);
+        grad[OFF_W3 + tid] = g;
     } else if (tid < NO * NH + NO) {
         const int o = tid - NO * NH;
         float g = 0.0f;
         for (int s = 0; s < TILE; ++s) g += S.dy[s * NO + o];
-        atomicAdd(grad + OFF_B3 + o, g);
+        grad[OFF_B3 + o] = g;
     }
     // dh2 = (W3^T dy) * (1 - h2^2)
     for (int i = tid; i < TILE * NH; i += THREADS) {
@@ -183,11 +186,11 @@ mlp_tile_kernel(const float* __restrict__ wbf, const float* __restrict__ norm,
 #pragma unroll
         for (int r = 0; r < 4; ++r)
 #pragma unroll
-            for (int c = 0; c < 4; ++c) atomicAdd(grad + OFF_W2 + (ob + r) * NH + kb + c, g[r][c]);
+            for (int c = 0; c < 4; ++c) grad[OFF_W2 + (ob + r) * NH + kb + c] = g[r][c];
         if (tid < NH) {
             float gb = 0.0f;
             for (int s = 0; s < TILE; ++s) gb += S.d[s * LD + tid];
-            atomicAdd(grad + OFF_B2 + tid, gb);
+            grad[OFF_B2 + tid] = gb;
         }
     }
     __syncthreads();
@@ -222,12 +225,12 @@ mlp_tile_kernel(const float* __restrict__ wbf, const float* __restrict__ norm,
             const int o = i / NI, f = i % NI;
             float g = 0.0f;
             for (int s = 0; s < TILE; ++s) g = fmaf(S.h2[s * LD + o], S.xn[s * NI + f], g);
-            atomicAdd(grad + OFF_W1 + i, g);
+            grad[OFF_W1 + i] = g;
         } else {
             const int o = i - NH * NI;
             float g = 0.0f;
             for (int s = 0; s < TILE; ++s) g += S.h2[s * LD + o];
-            atomicAdd(grad + OFF_B1 + o, g);
+            grad[OFF_B1 + o] = g;
         }
     }
     }  // TRAIN
@@ -424,6 +427,16 @@ mlp_forward_tc_kernel(const float* __restrict__ wbf, const float* __restrict__ n
 }
 
 // Adam (Kingma & Ba 2015) on the FP32 master weights; also refreshes the bf16-rounded copy.
+// grad[i] = sum over tiles t of part[t][i], t ascending (i = NPARAM: the loss)
+__global__ void grad_sum_kernel(const float* __restrict__ part, long long tiles,
+                                float* __restrict__ grad) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i > NPARAM) return;
+    float g = 0.0f;
+    for (long long t = 0; t < tiles; ++t) g += part[(size_t)t * (NPARAM + 1) + i];
+    grad[i] = g;
+}
+
 __global__ void adam_kernel(float* __restrict__ theta, float* __restrict__ wbf,
                             float* __restrict__ m, float* __restrict__ v,
                             const float* __restrict__ g, float lr, float b1, float b2, float c1,
@@ -510,6 +523,8 @@ struct rc_mlp_s {
     float* h_loss = nullptr;       // pinned
     bool tensor_cores = false;     // inference through mlp_forward_tc_kernel
     int* d_err = nullptr;          // set if a tensor-core wait ran out
+    float* part = nullptr;         // per-tile partial gradients and losses [tiles][NPARAM + 1]
+    long long part_tiles = 0;
 };
 
 namespace {
@@ -536,11 +551,22 @@ rc_status ensure_configured() {
 rc_status loss_grad(rc_mlp_t n, const float* X, const float* Yt, long long B, cudaStream_t s) {
     rc_status st = ensure_configured();
     if (st != RC_OK) return st;
-    cudaMemsetAsync(n->grad, 0, (NPARAM + 1) * sizeof(float), s);   // grad and the loss after it
-    const unsigned grid = (unsigned)((B + TILE - 1) / TILE);
-    mlp_tile_kernel<true><<<grid, THREADS, smem_bytes(), s>>>(n->wbf, n->norm, X, Yt, B, nullptr,
-                                                             n->grad, n->loss);
-    cudaError_t e = cudaGetLastError();
+    const long long tiles = (B + TILE - 1) / TILE;
+    cudaError_t e;
+    if (n->part_tiles < tiles) {
+        cudaStreamSynchronize(s);
+        cudaFree(n->part);
+        n->part = nullptr;
+        n->part_tiles = 0;
+        if ((e = cudaMalloc(&n->part, (size_t)tiles * (NPARAM + 1) * sizeof(float))) != cudaSuccess)
+            return mcuda(e, "mlp: partial-gradient buffer");
+        n->part_tiles = tiles;
+    }
+    mlp_tile_kernel<true><<<(unsigned)tiles, THREADS, smem_bytes(), s>>>(n->wbf, n->norm, X, Yt, B,
+                                                                        nullptr, n->part);
+    // grad and the loss after it: the tiles' partials summed in tile order
+    grad_sum_kernel<<<(NPARAM + 1 + 255) / 256, 256, 0, s>>>(n->part, tiles, n->grad);
+    e = cudaGetLastError();
     return e == cudaSuccess ? RC_OK : mcuda(e, "mlp_tile_kernel");
 }
 
@@ -609,6 +635,7 @@ void rc_mlp_destroy(rc_mlp_t n) {
     cudaFree(n->Xb);
     cudaFree(n->Ysc);
     cudaFree(n->d_err);
+    cudaFree(n->part);
     cudaFreeHost(n->h_loss);
     delete n;
 }
@@ -663,8 +690,7 @@ rc_status rc_mlp_forward(rc_mlp_t n, const float* X, long long B, float* Y, void
                                 (cudaStream_t)stream>>>(n->wbf, n->norm, X, B, Y, n->d_err);
     } else {
         mlp_tile_kernel<false><<<(unsigned)((B + TILE - 1) / TILE), THREADS, smem_bytes(),
-                                 (cudaStream_t)stream>>>(n->wbf, n->norm, X, nullptr, B, Y, nullptr,
-                                                         nullptr);
+                                 (cudaStream_t)stream>>>(n->wbf, n->norm, X, nullptr, B, Y, nullptr);
     }
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? RC_OK : mcuda(e, "rc_mlp_forward");

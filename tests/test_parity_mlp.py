@@ -83,6 +83,24 @@ def test_training_reduces_the_loss():
     assert l1 < 0.15 * l0
 
 
+def test_training_is_reproducible():
+    """The tiles' partial gradients are summed in a fixed order (no atomics), so two nets
+    with the same seed trained on the same data end with identical parameters."""
+    rcx = _rcx()
+    rng = np.random.default_rng(4)
+    X = rng.normal(0, 1, (9000, 6)).astype(np.float32)
+    Y = np.stack([np.cos(X[:, 0]), X[:, 1] * X[:, 2], np.tanh(X[:, 5])], axis=1).astype(np.float32)
+    dX, dY = torch.from_numpy(X).cuda(), torch.from_numpy(Y).cuda()
+    out = []
+    for _ in range(2):
+        net = rcx.MLP(seed=11)
+        net.fit_normalization(dX)
+        net.train(dX, dY, batch=2000, steps=200, lr=3e-3, record=False)
+        torch.cuda.synchronize()
+        out.append(net.get_params()[0])
+    np.testing.assert_array_equal(out[0], out[1])
+
+
 def test_features_targets_and_seed_closed_forms():
     rcx = _rcx()
     atom = rcx.Atom(ATOM)

@@ -30,15 +30,30 @@ def up_to_date() -> bool:
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
+    """Compiles every CUDA source to an object in parallel (one nvcc per file), then links
+    librcx.so; the library is replaced atomically."""
     if not force and up_to_date():
         return LIB
-    tmp = LIB + f".tmp{os.getpid()}"
+    from concurrent.futures import ThreadPoolExecutor
     extra = os.environ.get("RCX_NVCC_FLAGS", "").split()   # e.g. -DRCX_MIN_CTAS=6
-    cmd = [NVCC, *ARCH, "-O3", "-lineinfo", "-std=c++17", "--shared", "-Xcompiler", "-fPIC",
-           "-Xptxas", "-v" if verbose else "-O3", "-I", os.path.join(ROOT, "include"), *extra,
-           *sources(), "-o", tmp]
-    subprocess.check_call(cmd)
+    obj_dir = os.path.join(HERE, "_build", f"p{os.getpid()}")
+    os.makedirs(obj_dir, exist_ok=True)
+    common = [NVCC, *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
+              "-Xptxas", "-v" if verbose else "-O3", "-I", os.path.join(ROOT, "include"), *extra]
+    objs = [os.path.join(obj_dir, os.path.basename(src)[:-3] + ".o") for src in sources()]
+
+    def compile_one(pair):
+        src, obj = pair
+        subprocess.check_call([*common, "-c", src, "-o", obj])
+
+    with ThreadPoolExecutor(max_workers=max(1, min(len(objs), os.cpu_count() or 1))) as ex:
+        list(ex.map(compile_one, zip(sources(), objs)))
+    tmp = LIB + f".tmp{os.getpid()}"
+    subprocess.check_call([NVCC, *ARCH, "--shared", *objs, "-o", tmp])
     os.replace(tmp, LIB)
+    for o in objs:
+        os.remove(o)
+    os.rmdir(obj_dir)
     return LIB
 
 

@@ -518,7 +518,8 @@ level_kernel(const LevelArgs A) {
 // The partial (I, T) is kept in it_state between launches; the last launch merges with the
 // upper cascade and stores the child averages.
 // ---------------------------------------------------------------------------
-template <int LB, int VL, typename TS, bool HAS_UP>
+// FIRST / LAST: this launch is the first / last strip (never both: at least 2 strips).
+template <int LB, int VL, typename TS, bool HAS_UP, bool FIRST, bool LAST>
 __global__ void __launch_bounds__(kWarpsPerCta * 32, min_ctas<VL>())
 level_split_kernel(const LevelArgs A) {
     constexpr int LPR = LB / VL;
@@ -529,7 +530,7 @@ level_split_kernel(const LevelArgs A) {
     const int lane_off = q * VL;
     const int lb = A.split_lb + (int)blockIdx.y;
     const bool valid = ray < A.rays;
-    const bool first = A.phase == 0, last = A.phase == A.n_strips - 1;
+    constexpr bool first = FIRST, last = LAST;
     float R[VL];
     long long sray = 0;
 #pragma unroll
@@ -1106,8 +1107,17 @@ static cudaError_t level_split_t(bool has_up, const LevelArgs& a, cudaStream_t s
     if (a.rays == 0) return cudaSuccess;
     const long long per_cta = (long long)G * kWarpsPerCta;
     const dim3 grid((unsigned)((a.rays + per_cta - 1) / per_cta), (unsigned)a.split_nblk);
-    if (has_up) level_split_kernel<LB, 4, TS, true><<<grid, kWarpsPerCta * 32, 0, s>>>(a);
-    else level_split_kernel<LB, 4, TS, false><<<grid, kWarpsPerCta * 32, 0, s>>>(a);
+    const dim3 block(kWarpsPerCta * 32);
+    const bool first = a.phase == 0, last = a.phase == a.n_strips - 1;
+    if (has_up) {
+        if (first) level_split_kernel<LB, 4, TS, true, true, false><<<grid, block, 0, s>>>(a);
+        else if (last) level_split_kernel<LB, 4, TS, true, false, true><<<grid, block, 0, s>>>(a);
+        else level_split_kernel<LB, 4, TS, true, false, false><<<grid, block, 0, s>>>(a);
+    } else {
+        if (first) level_split_kernel<LB, 4, TS, false, true, false><<<grid, block, 0, s>>>(a);
+        else if (last) level_split_kernel<LB, 4, TS, false, false, true><<<grid, block, 0, s>>>(a);
+        else level_split_kernel<LB, 4, TS, false, false, false><<<grid, block, 0, s>>>(a);
+    }
     return cudaGetLastError();
 }
 

@@ -288,6 +288,14 @@ __device__ __forceinline__ bool march_interval(const float2* __restrict__ F, int
     return true;
 }
 
+// Storage scale of lambda block lb: 16-bit merged intervals are stored divided by a
+// per-block scale; FP32 storage has none (known at compile time).
+template <typename TS>
+__device__ __forceinline__ float storage_scale(const LevelArgs& A, int lb) {
+    if constexpr (std::is_same<TS, float>::value) return 1.0f;
+    else return A.scale ? A.scale[lb] : 1.0f;
+}
+
 // Column and row of a probe (or cell) index on a grid P wide.  Probe and cell counts are
 // below 2^31 (rc_plan keeps nx nz LB below it), so the division runs in 32 bits.
 __device__ __forceinline__ void grid_xy(long long idx, int P, int& x, int& z) {
@@ -402,7 +410,9 @@ __device__ __forceinline__ void store_child_average(const LevelArgs& A, int lb, 
 // One CTA-sized chunk `cta` of the rays of lambda block `lb` of one cascade.  The four
 // rays 4m..4m+3 of a probe (consecutive directions: the children of direction m of the
 // cascade below) are summed across their lane groups and stored once as their average.
-template <int LB, int VL, typename TS, bool HAS_UP, bool FIX = false>
+// FAST: the direction count is a power of two and every probe is marched (no sparse list),
+// both known at compile time.
+template <int LB, int VL, typename TS, bool HAS_UP, bool FIX = false, bool FAST = false>
 __device__ __forceinline__ void level_body(const LevelArgs& A, int lb, long long cta) {
     constexpr int LPR = LB / VL;   // lanes per ray
     constexpr int G = 32 / LPR;    // rays per warp
@@ -422,14 +432,14 @@ __device__ __forceinline__ void level_body(const LevelArgs& A, int lb, long long
     if (valid) {
         int k;
         long long probe;
-        if (A.Wshift >= 0) {
+        if (FAST || A.Wshift >= 0) {
             k = (int)(ray & (A.W - 1));
             probe = ray >> A.Wshift;
         } else {
             k = (int)(ray % A.W);
             probe = ray / A.W;
         }
-        if (A.probe_list) probe = A.probe_list[probe];   // sparse: the flagged probes only
+        if (!FAST && A.probe_list) probe = A.probe_list[probe];   // sparse: the flagged probes only
         sray = probe * A.W + k;
         const int px = (int)(probe % A.Px), pz = (int)(probe / A.Px);
         const float2 d = A.dirs[k];
@@ -438,7 +448,7 @@ __device__ __forceinline__ void level_body(const LevelArgs& A, int lb, long long
 
         if constexpr (FIX && HAS_UP) {
             const TS* Rup = reinterpret_cast<const TS*>(A.R_up) + (size_t)lb * A.R_up_lstride;
-            fixed_rays<LB, VL, TS>(A, F, Rup, A.scale ? A.scale[lb] : 1.0f, px, pz, ox, oz, d, k,
+            fixed_rays<LB, VL, TS>(A, F, Rup, storage_scale<TS>(A, lb), px, pz, ox, oz, d, k,
                                    lane_off, R);
         } else {
             float I[VL], T[VL], I0[VL];
@@ -447,7 +457,7 @@ __device__ __forceinline__ void level_body(const LevelArgs& A, int lb, long long
             if (HAS_UP) {
                 const TS* Rup = reinterpret_cast<const TS*>(A.R_up) + (size_t)lb * A.R_up_lstride;
                 const Bilinear bl(px, pz, A.Px_up, A.Pz_up);
-                const float sc = A.scale ? A.scale[lb] : 1.0f;
+                const float sc = storage_scale<TS>(A, lb);
                 float up[VL];
                 upper_radiance<LB, VL, TS>(Rup, bl.b00, bl.b01, bl.b10, bl.b11, bl.fx, bl.fz, A.W,
                                            k, lane_off, up);
@@ -495,17 +505,17 @@ __device__ __forceinline__ void store_child_average(const LevelArgs& A, int lb, 
     }
     if (valid && leader) {
         TS* out = reinterpret_cast<TS*>(A.R_out) + (size_t)lb * A.R_out_lstride;
-        const float inv = 0.25f * (A.scale ? 1.0f / A.scale[lb] : 1.0f);
+        const float inv = 0.25f / storage_scale<TS>(A, lb);
 #pragma unroll
         for (int j = 0; j < VL; ++j) R[j] *= inv;
         store_vec<TS, VL>(out + (size_t)(sray >> 2) * LB + lane_off, R);
     }
 }
 
-template <int LB, int VL, typename TS, bool HAS_UP, bool FIX>
+template <int LB, int VL, typename TS, bool HAS_UP, bool FIX, bool FAST>
 __global__ void __launch_bounds__(kWarpsPerCta * 32, min_ctas<VL>())
 level_kernel(const LevelArgs A) {
-    level_body<LB, VL, TS, HAS_UP, FIX>(A, blockIdx.y, blockIdx.x);
+    level_body<LB, VL, TS, HAS_UP, FIX, FAST>(A, blockIdx.y, blockIdx.x);
 }
 
 // ---------------------------------------------------------------------------
@@ -574,7 +584,7 @@ level_split_kernel(const LevelArgs A) {
             } else if (HAS_UP) {
                 const TS* Rup = reinterpret_cast<const TS*>(A.R_up) + (size_t)lb * A.R_up_lstride;
                 const Bilinear bl(px, pz, A.Px_up, A.Pz_up);
-                const float sc = A.scale ? A.scale[lb] : 1.0f;
+                const float sc = storage_scale<TS>(A, lb);
                 float up[VL];
                 upper_radiance<LB, VL, TS>(Rup, bl.b00, bl.b01, bl.b10, bl.b11, bl.fx, bl.fz,
                                            A.W, k, lane_off, up);
@@ -612,7 +622,7 @@ __device__ __forceinline__ void level0_body(const LevelArgs& A, int lb, long lon
     float sc = 1.0f;
     if (HAS_UP) {
         Rup = reinterpret_cast<const TS*>(A.R_up) + (size_t)lb * A.R_up_lstride;
-        if (A.scale) sc = A.scale[lb];
+        sc = storage_scale<TS>(A, lb);
     }
     Voxel<VL> own;
     own.load(F + (size_t)cell * LB + lane_off);
@@ -1006,9 +1016,12 @@ static cudaError_t level_t(bool level0, bool has_up, int n_lblk, const LevelArgs
         else if (has_up) level0_kernel<LB, VL, TS, true, false><<<grid, block, 0, s>>>(a);
         else level0_kernel<LB, VL, TS, false, false><<<grid, block, 0, s>>>(a);
     } else {
-        if (has_up && fix) level_kernel<LB, VL, TS, true, true><<<grid, block, 0, s>>>(a);
-        else if (has_up) level_kernel<LB, VL, TS, true, false><<<grid, block, 0, s>>>(a);
-        else level_kernel<LB, VL, TS, false, false><<<grid, block, 0, s>>>(a);
+        const bool fast = a.Wshift >= 0 && !a.probe_list;
+        if (has_up && fix) level_kernel<LB, VL, TS, true, true, false><<<grid, block, 0, s>>>(a);
+        else if (has_up && fast) level_kernel<LB, VL, TS, true, false, true><<<grid, block, 0, s>>>(a);
+        else if (has_up) level_kernel<LB, VL, TS, true, false, false><<<grid, block, 0, s>>>(a);
+        else if (fast) level_kernel<LB, VL, TS, false, false, true><<<grid, block, 0, s>>>(a);
+        else level_kernel<LB, VL, TS, false, false, false><<<grid, block, 0, s>>>(a);
     }
     return cudaGetLastError();
 }

@@ -529,7 +529,8 @@ level_kernel(const LevelArgs A) {
 // upper cascade and stores the child averages.
 // ---------------------------------------------------------------------------
 // FIRST / LAST: this launch is the first / last strip (never both: at least 2 strips).
-template <int LB, int VL, typename TS, bool HAS_UP, bool FIRST, bool LAST>
+// FAST as for level_body.
+template <int LB, int VL, typename TS, bool HAS_UP, bool FIRST, bool LAST, bool FAST>
 __global__ void __launch_bounds__(kWarpsPerCta * 32, min_ctas<VL>())
 level_split_kernel(const LevelArgs A) {
     constexpr int LPR = LB / VL;
@@ -548,14 +549,14 @@ level_split_kernel(const LevelArgs A) {
     if (valid) {
         int k;
         long long probe;
-        if (A.Wshift >= 0) {
+        if (FAST || A.Wshift >= 0) {
             k = (int)(ray & (A.W - 1));
             probe = ray >> A.Wshift;
         } else {
             k = (int)(ray % A.W);
             probe = ray / A.W;
         }
-        if (A.probe_list) probe = A.probe_list[probe];
+        if (!FAST && A.probe_list) probe = A.probe_list[probe];
         sray = probe * A.W + k;
         int px, pz;
         grid_xy(probe, A.Px, px, pz);
@@ -1114,24 +1115,31 @@ cudaError_t launch_batched_pack(int LB, const BatchPackArgs& b, int grid, cudaSt
     return cudaGetLastError();
 }
 
+template <int LB, typename TS, bool FAST>
+static cudaError_t split_phase(bool has_up, const LevelArgs& a, dim3 grid, cudaStream_t s) {
+    const dim3 block(kWarpsPerCta * 32);
+    const bool first = a.phase == 0, last = a.phase == a.n_strips - 1;
+    if (has_up) {
+        if (first) level_split_kernel<LB, 4, TS, true, true, false, FAST><<<grid, block, 0, s>>>(a);
+        else if (last) level_split_kernel<LB, 4, TS, true, false, true, FAST><<<grid, block, 0, s>>>(a);
+        else level_split_kernel<LB, 4, TS, true, false, false, FAST><<<grid, block, 0, s>>>(a);
+    } else {
+        if (first) level_split_kernel<LB, 4, TS, false, true, false, FAST><<<grid, block, 0, s>>>(a);
+        else if (last) level_split_kernel<LB, 4, TS, false, false, true, FAST><<<grid, block, 0, s>>>(a);
+        else level_split_kernel<LB, 4, TS, false, false, false, FAST><<<grid, block, 0, s>>>(a);
+    }
+    return cudaGetLastError();
+}
+
 template <int LB, typename TS>
 static cudaError_t level_split_t(bool has_up, const LevelArgs& a, cudaStream_t s) {
     constexpr int G = 32 / (LB / 4);
     if (a.rays == 0) return cudaSuccess;
     const long long per_cta = (long long)G * kWarpsPerCta;
     const dim3 grid((unsigned)((a.rays + per_cta - 1) / per_cta), (unsigned)a.split_nblk);
-    const dim3 block(kWarpsPerCta * 32);
-    const bool first = a.phase == 0, last = a.phase == a.n_strips - 1;
-    if (has_up) {
-        if (first) level_split_kernel<LB, 4, TS, true, true, false><<<grid, block, 0, s>>>(a);
-        else if (last) level_split_kernel<LB, 4, TS, true, false, true><<<grid, block, 0, s>>>(a);
-        else level_split_kernel<LB, 4, TS, true, false, false><<<grid, block, 0, s>>>(a);
-    } else {
-        if (first) level_split_kernel<LB, 4, TS, false, true, false><<<grid, block, 0, s>>>(a);
-        else if (last) level_split_kernel<LB, 4, TS, false, false, true><<<grid, block, 0, s>>>(a);
-        else level_split_kernel<LB, 4, TS, false, false, false><<<grid, block, 0, s>>>(a);
-    }
-    return cudaGetLastError();
+    const bool fast = a.Wshift >= 0 && !a.probe_list;
+    if (fast) return split_phase<LB, TS, true>(has_up, a, grid, s);
+    return split_phase<LB, TS, false>(has_up, a, grid, s);
 }
 
 template <int LB>

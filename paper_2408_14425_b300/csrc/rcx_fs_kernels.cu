@@ -41,6 +41,11 @@
 #ifndef RCX_MIN_CTAS_VL8
 #define RCX_MIN_CTAS_VL8 3
 #endif
+// Cascade 0 for J alone (no operator outputs, dense): 4 CTAs/SM measured 0.98 ms per 1024^2
+// 64-wavelength step against 1.03 ms at 3.
+#ifndef RCX_MIN_CTAS_L0J
+#define RCX_MIN_CTAS_L0J 4
+#endif
 #ifndef RCX_MIN_CTAS_L0
 #define RCX_MIN_CTAS_L0 3
 #endif
@@ -604,8 +609,12 @@ level_split_kernel(const LevelArgs A) {
 // cascade 0: one lane group per cell centre, loop over the W_0 directions,
 // accumulate J (Eq. 1) and the diagonal operator (Eq. 17)
 // ---------------------------------------------------------------------------
-template <int LB, int VL, typename TS, bool HAS_UP, bool FIX = false>
+// OPS: the operator outputs (alo, J_eff, alo_c) may be requested (else J alone); FAST: no
+// sparse cell list.  Both known at compile time.
+template <int LB, int VL, typename TS, bool HAS_UP, bool FIX = false, bool OPS = true,
+          bool FAST = false>
 __device__ __forceinline__ void level0_body(const LevelArgs& A, int lb, long long cta) {
+    constexpr bool ops = OPS && !FIX;
     constexpr int LPR = LB / VL;
     constexpr int G = 32 / LPR;
     const int lane = threadIdx.x & 31;
@@ -613,7 +622,7 @@ __device__ __forceinline__ void level0_body(const LevelArgs& A, int lb, long lon
     const long long wid = cta * kWarpsPerCta + (threadIdx.x >> 5);
     long long cell = wid * G + g;
     if (cell >= A.rays) return;                       // rays = cells (or flagged cells) here
-    if (A.probe_list) cell = A.probe_list[cell];
+    if (!FAST && A.probe_list) cell = A.probe_list[cell];
     int px, pz;
     grid_xy(cell, A.nx, px, pz);
     const float ox = (float)px + 0.5f, oz = (float)pz + 0.5f;
@@ -626,7 +635,7 @@ __device__ __forceinline__ void level0_body(const LevelArgs& A, int lb, long lon
         sc = storage_scale<TS>(A, lb);
     }
     Voxel<VL> own;
-    own.load(F + (size_t)cell * LB + lane_off);
+    if (ops) own.load(F + (size_t)cell * LB + lane_off);
     const Bilinear bl(px, pz, HAS_UP ? A.Px_up : 1, HAS_UP ? A.Pz_up : 1);
 
     // J = mean of the merged rays; J_eff leaves out the emission of the cell's own
@@ -648,7 +657,6 @@ __device__ __forceinline__ void level0_body(const LevelArgs& A, int lb, long lon
         float I[VL], T[VL], I0[VL];
         march_interval<LB, VL, true>(F, A.nx, A.nz, 0, A.nx, ox, oz, d.x, d.y, A.a, A.b, lane_off,
                                      A.max_steps, I, T, I0);
-        const float dk = 0.5f / fmaxf(fabsf(d.x), fabsf(d.y));
         float up[VL];
         if (HAS_UP)
             upper_radiance<LB, VL, TS>(Rup, bl.b00, bl.b01, bl.b10, bl.b11, bl.fx, bl.fz, A.W, k,
@@ -658,11 +666,13 @@ __device__ __forceinline__ void level0_body(const LevelArgs& A, int lb, long lon
             float Rnl = I[j];
             if (HAS_UP) Rnl = fmaf(T[j], up[j] * sc, I[j]);
             Jsum[j] += Rnl + I0[j];
-            Jeff[j] += Rnl;
-            const float y = own.v[j].x * dk;
-            const float e = exp2_neg(y);
-            alo_sum[j] += one_minus_exp2_neg(y, e);
-            aloc_sum[j] += e;
+            if constexpr (ops) {
+                Jeff[j] += Rnl;
+                const float y = own.v[j].x * (0.5f / fmaxf(fabsf(d.x), fabsf(d.y)));
+                const float e = exp2_neg(y);
+                alo_sum[j] += one_minus_exp2_neg(y, e);
+                aloc_sum[j] += e;
+            }
         }
     }
     const float invW = 1.0f / (float)A.W;
@@ -672,17 +682,19 @@ __device__ __forceinline__ void level0_body(const LevelArgs& A, int lb, long lon
         if (lam < A.n_lambda) {
             const size_t o = (size_t)lam * A.ncell + cell;
             A.J[o] = Jsum[j] * invW;
-            if (A.alo) A.alo[o] = alo_sum[j] * invW;
-            if (A.J_eff) A.J_eff[o] = Jeff[j] * invW;
-            if (A.alo_c) A.alo_c[o] = aloc_sum[j] * invW;
+            if constexpr (ops) {
+                if (A.alo) A.alo[o] = alo_sum[j] * invW;
+                if (A.J_eff) A.J_eff[o] = Jeff[j] * invW;
+                if (A.alo_c) A.alo_c[o] = aloc_sum[j] * invW;
+            }
         }
     }
 }
 
-template <int LB, int VL, typename TS, bool HAS_UP, bool FIX>
-__global__ void __launch_bounds__(kWarpsPerCta * 32, RCX_MIN_CTAS_L0)
+template <int LB, int VL, typename TS, bool HAS_UP, bool FIX, bool OPS, bool FAST>
+__global__ void __launch_bounds__(kWarpsPerCta * 32, OPS ? RCX_MIN_CTAS_L0 : RCX_MIN_CTAS_L0J)
 level0_kernel(const LevelArgs A) {
-    level0_body<LB, VL, TS, HAS_UP, FIX>(A, blockIdx.y, blockIdx.x);
+    level0_body<LB, VL, TS, HAS_UP, FIX, OPS, FAST>(A, blockIdx.y, blockIdx.x);
 }
 
 // ---------------------------------------------------------------------------
@@ -1013,9 +1025,14 @@ static cudaError_t level_t(bool level0, bool has_up, int n_lblk, const LevelArgs
     dim3 block(kWarpsPerCta * 32);
     const bool fix = a.bilinear_fix != 0;
     if (level0) {
-        if (has_up && fix) level0_kernel<LB, VL, TS, true, true><<<grid, block, 0, s>>>(a);
-        else if (has_up) level0_kernel<LB, VL, TS, true, false><<<grid, block, 0, s>>>(a);
-        else level0_kernel<LB, VL, TS, false, false><<<grid, block, 0, s>>>(a);
+        const bool ops = a.alo || a.J_eff || a.alo_c, dense = !a.probe_list;
+        if (has_up && fix) level0_kernel<LB, VL, TS, true, true, false, false><<<grid, block, 0, s>>>(a);
+        else if (has_up && !ops && dense)
+            level0_kernel<LB, VL, TS, true, false, false, true><<<grid, block, 0, s>>>(a);
+        else if (has_up) level0_kernel<LB, VL, TS, true, false, true, false><<<grid, block, 0, s>>>(a);
+        else if (!ops && dense)
+            level0_kernel<LB, VL, TS, false, false, false, true><<<grid, block, 0, s>>>(a);
+        else level0_kernel<LB, VL, TS, false, false, true, false><<<grid, block, 0, s>>>(a);
     } else {
         const bool fast = a.Wshift >= 0 && !a.probe_list;
         if (has_up && fix) level_kernel<LB, VL, TS, true, true, false><<<grid, block, 0, s>>>(a);

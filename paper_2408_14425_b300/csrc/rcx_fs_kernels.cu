@@ -1029,6 +1029,8 @@ static cudaError_t level_t(bool level0, bool has_up, int n_lblk, const LevelArgs
         if (has_up && fix) level0_kernel<LB, VL, TS, true, true, false, false><<<grid, block, 0, s>>>(a);
         else if (has_up && !ops && dense)
             level0_kernel<LB, VL, TS, true, false, false, true><<<grid, block, 0, s>>>(a);
+        else if (has_up && dense)
+            level0_kernel<LB, VL, TS, true, false, true, true><<<grid, block, 0, s>>>(a);
         else if (has_up) level0_kernel<LB, VL, TS, true, false, true, false><<<grid, block, 0, s>>>(a);
         else if (!ops && dense)
             level0_kernel<LB, VL, TS, false, false, false, true><<<grid, block, 0, s>>>(a);

@@ -363,7 +363,7 @@ def test_strip_split_automatic_at_1024():
     """At 1024^2 with 16 wavelengths per block (128 MiB of packed field) cascade 5 (intervals
     from 341 to the far corner) runs in 2 strips; cascade 4 (256 voxels long) and cascade 6
     (38 voxels inside the domain) do not.  Each strip launch covers all three wavelength
-    blocks (their partial (I, T), 3 x 512 MiB, fits the 2 GiB it keeps for them)."""
+    blocks (their partial (I, T), 3 x 512 MiB, fits the 8 GiB it keeps for them)."""
     rcx = _rcx()
     chi, eta = W.grf_fields(1024, 48, lambdas=range(48))
     dchi, deta = torch.from_numpy(chi).cuda(), torch.from_numpy(eta).cuda()

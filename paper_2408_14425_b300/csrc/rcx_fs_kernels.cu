@@ -133,9 +133,24 @@ __device__ __forceinline__ void store_vec(TS* __restrict__ p, const float (&v)[V
             for (int j = 0; j < VL; j += 4)
                 *reinterpret_cast<float4*>(p + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
         }
+    } else if constexpr (VL == 1) {
+        Store<TS>::store(p, v[0]);
     } else {
+        // VL / 2 pairs, each rounded to nearest like Store, written in one store of VL * 2 bytes
+        unsigned h[VL / 2];
 #pragma unroll
-        for (int j = 0; j < VL; ++j) Store<TS>::store(p + j, v[j]);
+        for (int j = 0; j < VL / 2; ++j) {
+            if constexpr (std::is_same<TS, __half>::value) {
+                const __half2 t = __floats2half2_rn(v[2 * j], v[2 * j + 1]);
+                h[j] = *reinterpret_cast<const unsigned*>(&t);
+            } else {
+                const __nv_bfloat162 t = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
+                h[j] = *reinterpret_cast<const unsigned*>(&t);
+            }
+        }
+        if constexpr (VL == 2) *reinterpret_cast<unsigned*>(p) = h[0];
+        if constexpr (VL == 4) *reinterpret_cast<uint2*>(p) = make_uint2(h[0], h[1]);
+        if constexpr (VL == 8) *reinterpret_cast<uint4*>(p) = make_uint4(h[0], h[1], h[2], h[3]);
     }
 }
 

@@ -309,11 +309,12 @@ __device__ __forceinline__ bool march_interval(const float2* __restrict__ F, int
 }
 
 // Storage scale of lambda block lb: 16-bit merged intervals are stored divided by a
-// per-block scale; FP32 storage has none (known at compile time).
+// per-block scale (the plan always provides the scales with 16-bit storage); FP32 storage
+// has none (known at compile time).
 template <typename TS>
 __device__ __forceinline__ float storage_scale(const LevelArgs& A, int lb) {
     if constexpr (std::is_same<TS, float>::value) return 1.0f;
-    else return A.scale ? A.scale[lb] : 1.0f;
+    else return __ldg(A.scale + lb);
 }
 
 // Column and row of a probe (or cell) index on a grid P wide.  Probe and cell counts are
@@ -525,7 +526,7 @@ __device__ __forceinline__ void store_child_average(const LevelArgs& A, int lb, 
     }
     if (valid && leader) {
         TS* out = reinterpret_cast<TS*>(A.R_out) + (size_t)lb * A.R_out_lstride;
-        const float inv = 0.25f / storage_scale<TS>(A, lb);
+        const float inv = __fdividef(0.25f, storage_scale<TS>(A, lb));
 #pragma unroll
         for (int j = 0; j < VL; ++j) R[j] *= inv;
         store_vec<TS, VL>(out + (size_t)(sray >> 2) * LB + lane_off, R);

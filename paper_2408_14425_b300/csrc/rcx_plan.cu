@@ -904,12 +904,23 @@ rc_status rc_formal_solve_host(rc_plan_t p, const float* chi_h, const float* eta
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "rc_formal_solve_host: pending CUDA error");
 
-    // Chunks of whole lambda blocks; chunk c's copies overlap chunk c-1's solve.
+    // Chunks of whole lambda blocks; chunk c's copies overlap chunk c-1's solve.  The first
+    // chunk (whose copy in nothing hides) and the last (whose copy out nothing hides) are
+    // the small unit of about 16 wavelengths; the ones between are twice that, so fewer
+    // solves (fewer launch tails) cover the middle.
     const size_t ncell = (size_t)p->nx * p->nz;
     const int LB = p->LB;
-    int chunk = std::max(LB, ((16 + LB - 1) / LB) * LB);
-    if (chunk > n_lambda) chunk = n_lambda;
-    const int n_chunks = (n_lambda + chunk - 1) / chunk;
+    const int unit = std::max(LB, ((16 + LB - 1) / LB) * LB);
+    std::vector<int> bounds{0};                                // chunk c: [bounds[c], bounds[c+1])
+    while (bounds.back() < n_lambda) {
+        const int l0 = bounds.back(), left = n_lambda - l0;
+        // middle chunks: whole blocks, leaving at least one unit for the last chunk
+        const int mid = std::min(2 * unit, (left - unit) / LB * LB);
+        bounds.push_back(l0 + ((l0 == 0 || mid <= unit) ? std::min(unit, left) : mid));
+    }
+    const int n_chunks = (int)bounds.size() - 1;
+    int chunk = 0;
+    for (int c = 0; c < n_chunks; ++c) chunk = std::max(chunk, bounds[c + 1] - bounds[c]);
     const size_t slab = (size_t)chunk * ncell;                 // floats per array per chunk
     const size_t per_buf = slab * (alo_h ? 4 : 3);             // chi, eta, J (, alo)
     const size_t need = 2 * per_buf * sizeof(float);
@@ -944,8 +955,8 @@ rc_status rc_formal_solve_host(rc_plan_t p, const float* chi_h, const float* eta
     p->timing = false;
     for (int c = 0; c < n_chunks && st == RC_OK; ++c) {
         const int b = c & 1;
-        const int l0 = c * chunk;
-        const int nl = std::min(chunk, n_lambda - l0);
+        const int l0 = bounds[c];
+        const int nl = bounds[c + 1] - l0;
         const size_t bytes = (size_t)nl * ncell * sizeof(float);
         float* dchi = p->d_stage + b * per_buf;
         float* deta = dchi + slab;

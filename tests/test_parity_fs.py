@@ -145,9 +145,12 @@ def test_reduced_precision_storage(prec, tol):
     _assert_close(J, _oracle(chi, eta, 6), tol, prec)
 
 
-def test_host_buffer_entry_matches_device_entry():
+@pytest.mark.parametrize("nl", [37, 64, 100])
+def test_host_buffer_entry_matches_device_entry(nl):
+    """The host-buffer entry (chunks of 16 wavelengths at the ends, 32 between) gives the
+    device entry's results bit for bit: 37 -> 16+16+5, 64 -> 16+32+16, 100 -> 16+32+32+16+4."""
     rcx = _rcx()
-    chi, eta = W.grf_fields(64, 37)
+    chi, eta = W.grf_fields(64, nl)
     p = rcx.Plan(64, 64, 5)
     J_host, alo_host = p.formal_solve_host(chi, eta, want_alo=True)
     J_dev, alo_dev = p.formal_solve(torch.from_numpy(chi).cuda(), torch.from_numpy(eta).cuda(),

@@ -78,7 +78,10 @@ typedef struct {
                             launch gathers from a strip that stays in L2); 1 = never; 2..16 =
                             that many strips on every cascade >= 1.  Results agree with the
                             unsplit march to FP32 rounding.  Not with the bilinear fix; lane
-                            layouts with 4 wavelengths per lane and 8-32 per ray. */
+                            layouts with 4 wavelengths per lane and 8-32 per ray.  The strips
+                            hand a partial (I, T) per ray and wavelength (8 bytes) from one
+                            launch to the next; one launch covers as many wavelength blocks as
+                            fit 8 GiB of that state, and the plan's scratch holds it. */
     int reserved;        /* must be zero */
 } rc_options;
 
@@ -111,7 +114,9 @@ void rc_plan_destroy(rc_plan_t plan);
  * Errors: RC_ERR_ARG, RC_ERR_OOM, RC_ERR_CUDA. */
 rc_status rc_plan_reserve(rc_plan_t plan, int n_lambda);
 
-/* Bytes of device scratch the plan holds now. */
+/* Bytes of device scratch the plan holds now: packed field with its guard bands, two
+ * cascades of merged intervals, the strips' partial state (at most 8 GiB) and per-block
+ * scales, plus the host entry's staging buffers once it has run. */
 size_t rc_plan_scratch_bytes(rc_plan_t plan);
 
 /*

@@ -21,7 +21,7 @@ import subprocess
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SOURCES = ["rc_oracle.c", "nlte_oracle.c", "mlp_oracle.c"]
+_SOURCES = ["rc_oracle.c"]
 _LIB_PATH = os.path.join(_HERE, "librcoracle.so")
 _lib = None
 
@@ -30,7 +30,7 @@ _llp = ctypes.POINTER(ctypes.c_longlong)
 
 
 def _sources():
-    return [os.path.join(_HERE, s) for s in _SOURCES if os.path.exists(os.path.join(_HERE, s))]
+    return [os.path.join(_HERE, s) for s in _SOURCES]
 
 
 def build(force: bool = False) -> str:
@@ -89,23 +89,8 @@ def lib():
         L.rco_lc_solve.restype = ctypes.c_int
         L.rco_num_threads.restype = ctypes.c_int
         L.rco_set_num_threads.argtypes = [ctypes.c_int]
-        _bind_extra(L)
         _lib = L
     return _lib
-
-
-def _bind_extra(L):
-    """Bind the non-LTE and MLP oracle entry points when their sources are built in."""
-    try:
-        from . import nlte as _nlte
-        _nlte._bind(L)
-    except (ImportError, AttributeError):
-        pass
-    try:
-        from . import mlp as _mlp
-        _mlp._bind(L)
-    except (ImportError, AttributeError):
-        pass
 
 
 def _ptr(a: np.ndarray):

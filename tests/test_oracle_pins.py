@@ -146,8 +146,8 @@ def test_uniform_medium_closed_form():
     for th in (0.1, 1.0, 2.5, 4.0):
         w = (math.cos(th), math.sin(th))
         I, tau, _ = oracle.march(chi, eta, (10.0, 10.0), w, 1.0, 6.5)
-        assert tau == pytest.approx(0.37 * 5.5, rel=1e-13)
-        assert I == pytest.approx(4.0 * -math.expm1(-0.37 * 5.5), rel=1e-13)
+        assert tau == pytest.approx(0.37 * 5.5, rel=1e-13, abs=0)
+        assert I == pytest.approx(4.0 * -math.expm1(-0.37 * 5.5), rel=1e-13, abs=0)
 
 
 def test_zero_opacity_cells_emit_eta_ds():
@@ -155,7 +155,7 @@ def test_zero_opacity_cells_emit_eta_ds():
     eta = np.full((8, 8), 0.25)
     I, tau, _ = oracle.march(chi, eta, (4.0, 4.0), (1.0, 0.0), 0.0, 2.5)
     assert tau == 0.0
-    assert I == pytest.approx(0.25 * 2.5, rel=1e-14)
+    assert I == pytest.approx(0.25 * 2.5, rel=1e-14, abs=0)
 
 
 def test_free_space_outside_domain():
@@ -177,8 +177,8 @@ def test_merge_splitting_invariance(seed):
     far = oracle.march(chi, eta, o, w, b, c)[:2]
     whole = oracle.march(chi, eta, o, w, a, c)[:2]
     Im, tm = oracle.merge(near, far)
-    assert tm == pytest.approx(whole[1], rel=1e-12)
-    assert Im == pytest.approx(whole[0], rel=1e-12)
+    assert tm == pytest.approx(whole[1], rel=1e-12, abs=0)
+    assert Im == pytest.approx(whole[0], rel=1e-12, abs=0)
     # the order printed in Eq. 11 (far attenuated by nothing, near by far) is not
     # the radiation arriving at the probe for an inhomogeneous medium
     swapped = far[0] + math.exp(-far[1]) * near[0]
@@ -194,8 +194,8 @@ def test_shift_identity(x):
     p = np.array([5.3, 4.1])
     r1 = oracle.march(chi, eta, p, w, 1.0 + x, 9.0 + x)
     r2 = oracle.march(chi, eta, p + x * np.array(w), w, 1.0, 9.0)
-    assert r1[0] == pytest.approx(r2[0], rel=1e-12)
-    assert r1[1] == pytest.approx(r2[1], rel=1e-12)
+    assert r1[0] == pytest.approx(r2[0], rel=1e-12, abs=0)
+    assert r1[1] == pytest.approx(r2[1], rel=1e-12, abs=0)
 
 
 # ---------------------------------------------------------------------------
@@ -312,9 +312,9 @@ def test_alo_is_local_coefficient_of_J():
     c = (4, 6)
     eta[c] = 3.0 * chi[c]
     J, alo, _ = oracle.rc_solve(chi, eta, 1, want_alo=True)
-    assert J[c] == pytest.approx(3.0 * alo[c], rel=1e-13)
+    assert J[c] == pytest.approx(3.0 * alo[c], rel=1e-13, abs=0)
     d = 0.5 * math.sqrt(2.0)  # centre to edge along the cascade-0 diagonals
-    assert alo[c] == pytest.approx(-math.expm1(-chi[c] * d), rel=1e-13)
+    assert alo[c] == pytest.approx(-math.expm1(-chi[c] * d), rel=1e-13, abs=0)
 
 
 def test_thin_disc_closed_form():
@@ -382,7 +382,7 @@ def test_gauss_radau_inclination_rule(n):
     on [0, 1] (Sec. 3.1 uses eight Gauss-Radau inclinations)."""
     mu, w = oracle.gauss_radau_inclinations(n)
     assert mu[0] == 0.0 and np.all(np.diff(mu) > 0) and mu[-1] < 1.0
-    assert w.sum() == pytest.approx(1.0, rel=1e-12)
+    assert w.sum() == pytest.approx(1.0, rel=1e-12, abs=0)
     for p in range(2 * n - 1):
         assert np.sum(w * mu ** p) == pytest.approx(1.0 / (p + 1), rel=1e-11, abs=1e-14)
     if n > 1:   # and not beyond: degree 2n - 1 is not integrated exactly
@@ -439,7 +439,7 @@ def test_emergent_front_to_back_equals_back_to_front():
     for (ox, oz, wx, wz), Ii in zip(rays, I):
         assert Ii == pytest.approx(oracle.march(chi, eta, (ox, oz), (wx, wz), 0.0, math.inf)[0],
                                    rel=1e-12, abs=1e-300)
-    assert C.sum() == pytest.approx(I.sum(), rel=1e-12)
+    assert C.sum() == pytest.approx(I.sum(), rel=1e-12, abs=0)
 
 
 def test_emergent_uniform_slab_closed_form():

@@ -301,7 +301,7 @@ def test_emergent_intensity_and_contribution_function(mu):
                                        rays.astype(np.float64), mu=mu, want_contrib=True)
         _assert_close(I[lam][None, None], I_ref[None, None], 1e-3, f"I lambda {lam}")
         _assert_close(C[lam][None], C_ref[None], 2e-3, f"contribution lambda {lam}")
-        assert C[lam].sum() == pytest.approx(I[lam].sum(), rel=1e-4)
+        assert C[lam].sum() == pytest.approx(I[lam].sum(), rel=1e-4, abs=0)
 
 
 @pytest.mark.parametrize("n,C,launched", [(64, 5, 4), (64, 7, 4), (1024, 8, 7), (100, 4, 4)])

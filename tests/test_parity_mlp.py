@@ -48,7 +48,7 @@ def test_loss_and_gradient_match_oracle():
     loss, g = net.loss_grad(torch.from_numpy(X).cuda(), torch.from_numpy(Y).cuda())
     loss_ref, g_ref = omlp.loss_and_grad(omlp.round_bf16(theta), X, Y, mean.astype(np.float64),
                                          std.astype(np.float64))
-    assert loss == pytest.approx(loss_ref, rel=1e-5)
+    assert loss == pytest.approx(loss_ref, rel=1e-5, abs=0)
     g = g.cpu().numpy()
     err = np.abs(g - g_ref)
     assert np.all(err <= 1e-4 * np.abs(g_ref) + 1e-6 * np.abs(g_ref).max()), \

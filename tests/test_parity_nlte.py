@@ -81,7 +81,7 @@ def test_stat_eq_matches_oracle_on_the_same_inputs():
     dmax = atom.stat_eq(_dev(T), _dev(ne_r), _dev(na_r), _dev(Jeff32, torch.float32),
                         _dev(aloc32, torch.float32), pops)
     np.testing.assert_allclose(pops.cpu().numpy(), new_r, rtol=1e-10)
-    assert dmax == pytest.approx(dmax_r, rel=1e-8)
+    assert dmax == pytest.approx(dmax_r, rel=1e-8, abs=0)
     # plain Lambda iteration (no operator): J as J_eff, alo_c = NULL
     new_l, _ = nlte.stat_eq(ATOM, T, ne_r, na_r, J_r.reshape(chi_r.shape).astype(np.float32)
                             .astype(np.float64), None, pops0)

@@ -192,7 +192,11 @@ const char* rc_plan_launch_name(rc_plan_t plan, int i);
  * 256 bytes; for example 256 x 256 with 8 wavelengths and 7 cascades fits.  A larger problem
  * is rejected with RC_ERR_ARG and a message giving the bytes it needs.
  * The first call on a device (with that device current) looks up the array's device address
- * once with cudaGetSymbolAddress; make that first call before any stream capture.
+ * once with cudaGetSymbolAddress; make that first call before any stream capture.  The address
+ * is kept together with the ID of the CUDA context it came from: after cudaDeviceReset (or
+ * when the primary context is released and created again) the module is loaded anew and the
+ * array may move, so the next call finds a different context, looks the address up again
+ * (that call is again a first call) and never launches on the old address.
  * All calls share the one array, and it keeps the last call's contents: every call rewrites
  * what it reads, so nothing has to be cleared, but calls whose work overlaps on the GPU (on
  * different streams, or from several host threads) race on the array and must be serialised
@@ -395,7 +399,11 @@ rc_status rc_mlp_forward(rc_mlp_t net, const float* X, long long B, float* Y, vo
  * layer on the tensor cores (tcgen05.mma, bf16 h1 and W2 from shared memory, FP32 accumulator in
  * tensor memory, 128 samples per CTA); 0 (default) uses FP32 FMAs with the bf16 weights.
  * rc_mlp_tensor_core_status reports RC_ERR_TIMEOUT if a tensor-core wait ever ran out (the
- * kernel then skipped its outputs).  Training always uses the FMA path. */
+ * kernel then skipped its outputs).  A CTA whose wait ran out waits once more, 8x as long,
+ * before it releases its tensor memory; if the MMAs still have not completed it leaves the
+ * 64 columns allocated rather than free memory a late MMA could still write, and the message
+ * says so (later tensor-core launches on that SM have less tensor memory; recreate the
+ * context).  Training always uses the FMA path. */
 rc_status rc_mlp_use_tensor_cores(rc_mlp_t net, int enable);
 rc_status rc_mlp_tensor_core_status(rc_mlp_t net);
 

@@ -412,7 +412,18 @@ mlp_forward_tc_kernel(const float* __restrict__ wbf, const float* __restrict__ n
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
-    if (warp == 0) {
+    // Release the accumulator only once the MMAs that write it are known to be complete.
+    // After a timeout, wait once more (bounded, 8x as long); if the commit still has not
+    // arrived, the columns stay allocated (a late MMA must not write into columns another
+    // CTA has been given since) and the error says so.
+    bool release = done != 0;
+    if (!done) {
+        unsigned late = mbar_wait_bounded(mb, 0, 8u * kTcWaitLimit) ? 1u : 0u;
+        late = __syncthreads_and(late);
+        release = late != 0;
+        if (!release && tid == 0) atomicExch(err, 2);
+    }
+    if (warp == 0 && release) {
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 64;" ::"r"(tmem));
     }
@@ -745,6 +756,9 @@ rc_status rc_mlp_tensor_core_status(rc_mlp_t n) {
     int h = 0;
     cudaError_t e = cudaMemcpy(&h, n->d_err, sizeof(int), cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return mcuda(e, "rc_mlp_tensor_core_status");
+    if (h == 2)
+        return mfail(RC_ERR_TIMEOUT, "tensor-core MMA wait ran out and the MMAs never completed: "
+                                     "their tensor-memory columns were left allocated");
     return h ? mfail(RC_ERR_TIMEOUT, "tensor-core MMA wait ran out") : RC_OK;
 }
 

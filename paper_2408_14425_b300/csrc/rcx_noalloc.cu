@@ -6,7 +6,13 @@
 // GPU that loads librcx.so holds until the process exits.  Host code never uses
 // the array's name as an address: the first call on a device (with that device
 // current) asks the runtime for the array's device address with
-// cudaGetSymbolAddress, checks the result and caches it for that device.
+// cudaGetSymbolAddress, checks the result and caches it for that device together
+// with the unique ID of the CUDA context it belongs to.  A later call that finds
+// another context current (after cudaDeviceReset, or after the primary context was
+// released and created again, which reloads the module and can move the array)
+// looks the address up again instead of launching on a stale pointer.
+#include <cuda.h>   // CUcontext / CUresult types only; the entry points are fetched at run time
+
 #include <cmath>
 #include <mutex>
 #include <string>
@@ -22,6 +28,10 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocScratch
 
 std::mutex g_setup_mutex;
 void* g_scratch_addr[kMaxDevices] = {};
+unsigned long long g_scratch_ctx[kMaxDevices] = {};   // context ID the address belongs to
+
+typedef CUresult (*CtxGetCurrentFn)(CUcontext*);
+typedef CUresult (*CtxGetIdFn)(CUcontext, unsigned long long*);
 
 rc_status nfail(rc_status s, const std::string& m) {
     rcx::set_last_error(m);
@@ -39,19 +49,50 @@ __global__ void noalloc_dirs_kernel(float2* dirs, long long W, long long off) {
     dirs[off + k] = make_float2((float)c, (float)s);
 }
 
-// Device address of the scratch array on the current device (set up once per device).
+// Unique ID of the current CUDA context (IDs are never reused within a process), or 0
+// when the driver cannot give one; called with g_setup_mutex held.
+unsigned long long current_context_id() {
+    static bool looked_up = false;
+    static CtxGetCurrentFn get_current = nullptr;
+    static CtxGetIdFn get_id = nullptr;
+    if (!looked_up) {
+        looked_up = true;
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess && q == cudaDriverEntryPointSuccess)
+            get_current = reinterpret_cast<CtxGetCurrentFn>(f);
+        f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess && q == cudaDriverEntryPointSuccess)
+            get_id = reinterpret_cast<CtxGetIdFn>(f);
+        cudaGetLastError();
+    }
+    if (!get_current || !get_id) return 0;
+    CUcontext ctx = nullptr;
+    unsigned long long id = 0;
+    if (get_current(&ctx) != CUDA_SUCCESS || !ctx) return 0;
+    if (get_id(ctx, &id) != CUDA_SUCCESS) return 0;
+    return id;
+}
+
+// Device address of the scratch array on the current device.  Looked up once per device
+// and context; with no context ID to compare (an old driver), looked up on every call.
 rc_status scratch_address(int dev, unsigned char** out) {
     if (dev < 0 || dev >= kMaxDevices) return nfail(RC_ERR_UNSUPPORTED, "device index too large");
     std::lock_guard<std::mutex> lk(g_setup_mutex);
-    if (!g_scratch_addr[dev]) {
+    const unsigned long long ctx = current_context_id();
+    if (!g_scratch_addr[dev] || ctx == 0 || ctx != g_scratch_ctx[dev]) {
         void* p = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess || !p) {
             cudaGetLastError();
+            g_scratch_addr[dev] = nullptr;
             return nfail(RC_ERR_CUDA, std::string("cudaGetSymbolAddress of the scratch array: ") +
                                           cudaGetErrorString(e));
         }
         g_scratch_addr[dev] = p;
+        g_scratch_ctx[dev] = ctx;
     }
     *out = static_cast<unsigned char*>(g_scratch_addr[dev]);
     return RC_OK;

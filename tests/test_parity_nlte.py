@@ -197,3 +197,55 @@ def test_full_size_slab_converges_with_sampled_oracle_updates():
                                 J_eff.cpu().numpy()[:, cells].astype(np.float64),
                                 alo_c.cpu().numpy()[:, cells].astype(np.float64), P[:, cells])
     np.testing.assert_allclose(new.cpu().numpy()[:, cells], new_r, rtol=1e-10)
+
+
+def test_c3_crop_populations_over_a_converged_length_run():
+    """The non-LTE workload's slab (seed 11, 5.7 km voxels, 63 wavelengths, 6 cascades)
+    cropped to its central 128^2 (the cool sheet, its transition region and corona): 24
+    whole iterations from LTE -- as many as the full slab needs to reach a 1e-3 change --
+    on the GPU and in the FP64 oracle.  The populations must agree element by element
+    within the population tolerance 1e-4 relative, and the GPU's history of maximum changes
+    must follow the oracle's."""
+    rcx = _rcx()
+    T5, nH5, vox = W.prominence_slab(n=512, seed=11)
+    crop = (slice(192, 320), slice(192, 320))
+    T = np.ascontiguousarray(T5[crop])
+    nH = np.ascontiguousarray(nH5[crop])
+    atom = rcx.Atom(ATOM)
+    ne, na, pops = atom.lte(_dev(T), _dev(nH))
+    plan = rcx.Plan(128, 128, 6, voxel_size=vox)
+    conv, it, hist = rcx.nlte_solve(plan, atom, _dev(T), ne, na, pops, tol=1e-30, max_iter=24)
+    assert it == 24
+    pops_r, hist_r = nlte.nlte_iterate(ATOM, T, nH, vox, 6, max_iter=24, tol=1e-30)
+    g = pops.cpu().numpy()
+    rel = np.abs(g - pops_r) / np.abs(pops_r)
+    assert rel.max() < 1e-4, f"max rel population difference {rel.max():.3e}"
+    np.testing.assert_allclose(hist, hist_r, rtol=2e-2)
+
+
+def test_c3_full_size_J_in_si_units():
+    """The formal solution of the full 512^2 slab in SI units (chi in m^-1, 5.7 km voxels,
+    intensities per unit frequency ~1e-9..1e-13), at the LTE populations: for the Ly-alpha
+    core, a Ly-alpha wing point and the H-alpha core, J from the GPU (all 63 wavelengths in
+    one solve) equals the FP64 oracle's cell by cell within the FP32 tolerance 1e-3."""
+    rcx = _rcx()
+    T, nH, vox = W.prominence_slab(n=512, seed=11)
+    atom = rcx.Atom(ATOM)
+    Td = _dev(T)
+    ne, na, pops = atom.lte(Td, _dev(nH))
+    chi, eta = atom.emis_opac(Td, pops)
+    nl = chi.shape[0]
+    chi = chi.reshape(nl, 512, 512)
+    eta = eta.reshape(nl, 512, 512)
+    plan = rcx.Plan(512, 512, 6, voxel_size=vox)
+    J = plan.formal_solve(chi, eta).cpu().numpy()
+    chi_h = chi.cpu().numpy()
+    eta_h = eta.cpu().numpy()
+    for lam in (10, 2, 52):
+        J_r, _, _ = oracle.rc_solve(chi_h[lam:lam + 1].astype(np.float64),
+                                    eta_h[lam:lam + 1].astype(np.float64), 6, voxel=vox)
+        ref = J_r[0]
+        floor = 1e-7 * np.abs(ref).max()
+        bad = np.abs(J[lam] - ref) > 1e-3 * np.abs(ref) + floor
+        assert not bad.any(), f"lambda {lam}: {bad.sum()} cells off, max rel " \
+                              f"{(np.abs(J[lam] - ref) / np.abs(ref)).max():.2e}"

@@ -74,3 +74,31 @@ def test_noalloc_rejects_problems_beyond_its_static_scratch():
                                    ctypes.c_void_p(chi.data_ptr()), None, None)
     assert st == -1
     assert b"static array" in L.rc_last_error()
+
+
+def test_noalloc_calls_leave_device_free_memory_unchanged():
+    """Once warm (module and kernels loaded by the first calls), further calls must not change
+    the device's free memory: a buffer that a later change kept between calls (a cached scale
+    or work list) would show up here."""
+    rcx = _lib()
+    L = rcx.load()
+    chi, eta = _problem(21, 6, 112, 96)
+    J = torch.empty_like(chi)
+    g = rcx.rc_grid(112, 96, 1.0)
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+    def call():
+        st = L.rc_formal_solve_noalloc(ctypes.byref(g), 6, 4, 1.0, ctypes.c_void_p(chi.data_ptr()),
+                                       ctypes.c_void_p(eta.data_ptr()), 6,
+                                       ctypes.c_void_p(J.data_ptr()), None, stream)
+        assert st == 0, L.rc_last_error()
+
+    for _ in range(2):
+        call()
+    torch.cuda.synchronize()
+    free_before, _ = torch.cuda.mem_get_info()
+    for _ in range(3):
+        call()
+    torch.cuda.synchronize()
+    free_after, _ = torch.cuda.mem_get_info()
+    assert free_after == free_before

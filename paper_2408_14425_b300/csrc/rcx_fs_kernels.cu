@@ -627,6 +627,249 @@ level_split_kernel(const LevelArgs A) {
 }
 
 // ---------------------------------------------------------------------------
+// shared-DDA march (cascades >= 1, dense plans with a power-of-two direction count).
+//
+// In the lane-group march above every lane of a ray's group walks the ray's DDA, so a
+// warp spends one DDA step's instructions on 32 VL / LB rays.  Here a warp owns 32 rays of
+// one lambda block and splits the work in two phases per chunk of kSdSteps steps:
+//   * produce: lane r walks the DDA of ray r for the chunk and writes each step's voxel
+//     offset and path length ds to shared memory (one DDA step per 32 rays);
+//   * replay: the warp integrates the chunk for the rays' LB wavelengths in NP passes of
+//     RPP rays, LB / VL lanes per ray, VL wavelengths per lane: per crossing a lane reads
+//     the step (a shared load broadcast to the ray's lanes), gathers its wavelengths and
+//     applies Eq. 16 -- the same arithmetic as march_interval, so the results are
+//     identical to the lane-group march.
+// A ray that has left its interval repeats its last voxel with ds = 0 (no contribution)
+// until the chunk ends; passes whose rays have all ended are skipped, and the loop ends
+// when every ray of the warp has.  The merge with the upper cascade and the child-average
+// store follow per pass.  Strip-split cascades (PHASE 1 first, 2 middle, 3 last strip; 0
+// unsplit) compose the pieces through it_state as level_split_kernel does.
+// ---------------------------------------------------------------------------
+#ifndef RCX_MIN_CTAS_SD
+#define RCX_MIN_CTAS_SD 3
+#endif
+constexpr int kSdSteps = 8;
+
+// The DDA of one ray over [a, b] clipped to the box [x0, x1] x [0, nz], one step per call
+// (the walk of march_interval: same face parameters, exit and step bound).
+struct DdaWalk {
+    float t, thi, tnx, tnz, kx, kz, tfx, tfz, dtx, dtz;
+    int off, dox, doz, left;
+    bool alive;
+
+    // Returns false when the interval misses the box (then alive is false and off is 0).
+    __device__ __forceinline__ bool init(int LB, int nx, int nz, int x0, int x1, float ox,
+                                         float oz, float wx, float wz, float a, float b,
+                                         int max_steps) {
+        alive = false;
+        off = 0;
+        const float invx = wx != 0.0f ? 1.0f / wx : 1e30f;
+        const float invz = wz != 0.0f ? 1.0f / wz : 1e30f;
+        const float tx0 = ((float)x0 - ox) * invx, tx1 = ((float)x1 - ox) * invx;
+        const float tz0 = (0.0f - oz) * invz, tz1 = ((float)nz - oz) * invz;
+        const float tlo = fmaxf(a, fmaxf(fminf(tx0, tx1), fminf(tz0, tz1)));
+        if (!(tlo < fminf(b, fminf(fmaxf(tx0, tx1), fmaxf(tz0, tz1))))) return false;
+        const bool upx = wx > 0.0f, upz = wz > 0.0f;
+        const float ex = ox + tlo * wx, ez = oz + tlo * wz;
+        int ix = (int)floorf(ex), iz = (int)floorf(ez);
+        if (!upx && (float)ix == ex) --ix;
+        if (!upz && (float)iz == ez) --iz;
+        ix = min(max(ix, x0), x1 - 1);
+        iz = min(max(iz, 0), nz - 1);
+        const float fx0 = (float)(upx ? ix + 1 : ix), fz0 = (float)(upz ? iz + 1 : iz);
+        tfx = (fx0 - ox) * invx;
+        tfz = (fz0 - oz) * invz;
+        dtx = fabsf(invx);
+        dtz = fabsf(invz);
+        const float kx_end = (float)(upx ? x1 - 1 - ix : ix - x0);
+        const float kz_end = (float)(upz ? nz - 1 - iz : iz);
+        thi = fminf(b, fminf(fmaf(kx_end, dtx, tfx), fmaf(kz_end, dtz, tfz)));
+        kx = kz = 0.0f;
+        tnx = tfx;
+        tnz = tfz;
+        off = (iz * nx + ix) * LB;
+        dox = upx ? LB : -LB;
+        doz = upz ? nx * LB : -nx * LB;
+        t = tlo;
+        left = max_steps;
+        alive = max_steps > 0;
+        return true;
+    }
+
+    // The current step as (voxel offset, ds bits), then the advance; ds = 0 once ended.
+    __device__ __forceinline__ int2 next() {
+        const bool stepx = tnx <= tnz;
+        const float tn = fminf(fminf(tnx, tnz), thi);
+        const int2 r = make_int2(off, __float_as_int(alive ? tn - t : 0.0f));
+        const bool go = alive && tn < thi && --left > 0;
+        if (go) {
+            if (stepx) {
+                kx += 1.0f;
+                tnx = fmaf(kx, dtx, tfx);
+                off += dox;
+            } else {
+                kz += 1.0f;
+                tnz = fmaf(kz, dtz, tfz);
+                off += doz;
+            }
+            t = tn;
+        }
+        alive = go;
+        return r;
+    }
+};
+
+// Eq. 16 for one crossing of VL wavelengths (the update of march_interval).
+template <int VL>
+__device__ __forceinline__ void cross_voxel(const Voxel<VL>& v, float ds, float (&I)[VL],
+                                            float (&T)[VL]) {
+#pragma unroll
+    for (int j = 0; j < VL; ++j) {
+        const float y = v.v[j].x * ds;
+        const float e = exp2_neg(y);
+        const float om = one_minus_exp2_neg(y, e);
+        I[j] = fmaf(T[j] * v.v[j].y, om, I[j]);
+        T[j] *= e;
+    }
+}
+
+template <int LB, int VL, typename TS, bool HAS_UP, int PHASE>
+__global__ void __launch_bounds__(kWarpsPerCta * 32, RCX_MIN_CTAS_SD)
+level_sdda_kernel(const LevelArgs A) {
+    constexpr int LPR = LB / VL;          // lanes per ray in the replay
+    constexpr int RPP = 32 / LPR;         // rays per pass
+    constexpr int NP = 32 / RPP;          // passes
+    constexpr unsigned PASS_MASK = RPP >= 32 ? 0xffffffffu : ((1u << RPP) - 1u);
+    constexpr bool SPLIT = PHASE != 0, FIRST = PHASE == 1, LAST = PHASE == 3;
+    __shared__ int2 sbuf[kWarpsPerCta][kSdSteps][32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int g = lane / LPR, q = lane % LPR, lane_off = q * VL;
+    const int lb = SPLIT ? A.split_lb + (int)blockIdx.y : (int)blockIdx.y;
+    const long long ray0 = ((long long)blockIdx.x * kWarpsPerCta + w) * 32;
+    const float2* F = A.field + (size_t)lb * A.ncell * LB;
+
+    // producer: the DDA of ray ray0 + lane
+    DdaWalk walk;
+    walk.alive = false;
+    walk.off = 0;
+    bool hit = false;
+    {
+        const long long ray = ray0 + lane;
+        if (ray < A.rays) {
+            const int k = (int)(ray & (A.W - 1));
+            int px, pz;
+            grid_xy(ray >> A.Wshift, A.Px, px, pz);
+            const float2 d = A.dirs[k];
+            hit = walk.init(LB, A.nx, A.nz, SPLIT ? A.strip_x0 : 0, SPLIT ? A.strip_x1 : A.nx,
+                            ((float)px + 0.5f) * A.spacing, ((float)pz + 0.5f) * A.spacing,
+                            d.x, d.y, A.a, A.b, A.max_steps);
+        }
+    }
+    const unsigned hitmask = __ballot_sync(0xffffffffu, hit);
+
+    float I[NP][VL], T[NP][VL];
+#pragma unroll
+    for (int p = 0; p < NP; ++p)
+#pragma unroll
+        for (int j = 0; j < VL; ++j) {
+            I[p][j] = 0.0f;
+            T[p][j] = 1.0f;
+        }
+    const float2* Fl = F + lane_off;
+    int2 (*buf)[32] = sbuf[w];
+    unsigned live = __ballot_sync(0xffffffffu, walk.alive);
+    while (live) {
+#pragma unroll
+        for (int s = 0; s < kSdSteps; ++s) buf[s][lane] = walk.next();
+        __syncwarp();
+#pragma unroll
+        for (int p = 0; p < NP; ++p) {
+            if (!((live >> (p * RPP)) & PASS_MASK)) continue;   // warp-uniform
+            const int rp = p * RPP + g;
+            int2 st = buf[0][rp];
+            Voxel<VL> cur;
+            cur.load(Fl + st.x);
+#pragma unroll
+            for (int s = 0; s < kSdSteps; ++s) {
+                Voxel<VL> nxt;
+                int2 stn;
+                if (s + 1 < kSdSteps) {
+                    stn = buf[s + 1][rp];
+                    nxt.load(Fl + stn.x);
+                }
+                cross_voxel<VL>(cur, __int_as_float(st.y), I[p], T[p]);
+                if (s + 1 < kSdSteps) {
+                    cur = nxt;
+                    st = stn;
+                }
+            }
+        }
+        __syncwarp();
+        live = __ballot_sync(0xffffffffu, walk.alive);
+    }
+
+    // merge and store, pass by pass (all lanes take part in the sibling sums)
+#pragma unroll
+    for (int p = 0; p < NP; ++p) {
+        const int rp = p * RPP + g;
+        const long long ray = ray0 + rp;
+        const bool valid = ray < A.rays;
+        float R[VL];
+#pragma unroll
+        for (int j = 0; j < VL; ++j) R[j] = 0.0f;
+        if (valid) {
+            const int k = (int)(ray & (A.W - 1));
+            int px, pz;
+            grid_xy(ray >> A.Wshift, A.Px, px, pz);
+            float* Ip = I[p];
+            float* Tp = T[p];
+            bool merge = !SPLIT;
+            if constexpr (SPLIT) {
+                float2* st = A.it_state + ((size_t)blockIdx.y * A.rays + ray) * LB + lane_off;
+                const bool h = (hitmask >> rp) & 1u;
+                if (h || FIRST || LAST) {
+                    if constexpr (!FIRST) {
+                        const bool forward = A.dirs[k].x >= 0.0f;   // strips met front to back
+#pragma unroll
+                        for (int j = 0; j < VL; ++j) {
+                            const float2 acc = st[j];
+                            Ip[j] = forward ? fmaf(acc.y, Ip[j], acc.x) : fmaf(Tp[j], acc.x, Ip[j]);
+                            Tp[j] *= acc.y;
+                        }
+                    }
+                    if constexpr (!LAST) {
+#pragma unroll
+                        for (int j = 0; j < VL; ++j) {
+                            float* sp = reinterpret_cast<float*>(st + j);
+                            asm volatile("st.global.f32 [%0], %1;" :: "l"(sp), "f"(Ip[j]) : "memory");
+                            asm volatile("st.global.f32 [%0], %1;" :: "l"(sp + 1), "f"(Tp[j]) : "memory");
+                        }
+                    } else {
+                        merge = true;
+                    }
+                }
+            }
+            if (merge) {
+                if constexpr (HAS_UP) {
+                    const TS* Rup = reinterpret_cast<const TS*>(A.R_up) + (size_t)lb * A.R_up_lstride;
+                    const Bilinear bl(px, pz, A.Px_up, A.Pz_up);
+                    const float sc = storage_scale<TS>(A, lb);
+                    float up[VL];
+                    upper_radiance<LB, VL, TS>(Rup, bl.b00, bl.b01, bl.b10, bl.b11, bl.fx, bl.fz,
+                                               A.W, k, lane_off, up);
+#pragma unroll
+                    for (int j = 0; j < VL; ++j) R[j] = fmaf(Tp[j], up[j] * sc, Ip[j]);
+                } else {
+#pragma unroll
+                    for (int j = 0; j < VL; ++j) R[j] = Ip[j];
+                }
+            }
+        }
+        if (!SPLIT || LAST) store_child_average<LB, VL, TS>(A, lb, valid, ray, lane_off, R);
+    }
+}
+
+// ---------------------------------------------------------------------------
 // cascade 0: one lane group per cell centre, loop over the W_0 directions,
 // accumulate J (Eq. 1) and the diagonal operator (Eq. 17)
 // ---------------------------------------------------------------------------
@@ -1210,6 +1453,68 @@ cudaError_t launch_level_split(int LB, int VL, int precision, bool has_up, const
         case 32: return level_split_p<32>(precision, has_up, b, s);
     }
     return cudaErrorInvalidValue;
+}
+
+template <int LB, int VL, typename TS, int PHASE>
+static cudaError_t sdda_t(bool has_up, const LevelArgs& a, unsigned nblk, cudaStream_t s) {
+    if (a.rays == 0) return cudaSuccess;
+    const long long per_cta = 32LL * kWarpsPerCta;
+    const dim3 grid((unsigned)((a.rays + per_cta - 1) / per_cta), nblk);
+    const dim3 block(kWarpsPerCta * 32);
+    if (has_up) level_sdda_kernel<LB, VL, TS, true, PHASE><<<grid, block, 0, s>>>(a);
+    else level_sdda_kernel<LB, VL, TS, false, PHASE><<<grid, block, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+template <int LB, int VL, typename TS>
+static cudaError_t sdda_phase(bool has_up, int phase, const LevelArgs& a, unsigned nblk,
+                              cudaStream_t s) {
+    switch (phase) {
+        case 0: return sdda_t<LB, VL, TS, 0>(has_up, a, nblk, s);
+        case 1: return sdda_t<LB, VL, TS, 1>(has_up, a, nblk, s);
+        case 2: return sdda_t<LB, VL, TS, 2>(has_up, a, nblk, s);
+        case 3: return sdda_t<LB, VL, TS, 3>(has_up, a, nblk, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+template <int LB, int VL>
+static cudaError_t sdda_p(int precision, bool has_up, int phase, const LevelArgs& a,
+                          unsigned nblk, cudaStream_t s) {
+    switch (precision) {
+        case RC_STORE_F32: return sdda_phase<LB, VL, float>(has_up, phase, a, nblk, s);
+        case RC_STORE_F16: return sdda_phase<LB, VL, __half>(has_up, phase, a, nblk, s);
+        case RC_STORE_BF16: return sdda_phase<LB, VL, __nv_bfloat16>(has_up, phase, a, nblk, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+bool level_sdda_supported(int LB, int VL, const LevelArgs& a) {
+    return LB == 16 && VL == 4 && a.Wshift >= 0 && !a.probe_list && !a.bilinear_fix;
+}
+
+static cudaError_t sdda_dispatch(int LB, int VL, int precision, bool has_up, int phase,
+                                 const LevelArgs& a, unsigned nblk, cudaStream_t s) {
+    if (!level_sdda_supported(LB, VL, a) || nblk < 1 || nblk > 65535) return cudaErrorInvalidValue;
+    return sdda_p<16, 4>(precision, has_up, phase, a, nblk, s);
+}
+
+cudaError_t launch_level_sdda(int LB, int VL, int precision, bool has_up, int n_lblk,
+                              const LevelArgs& a, cudaStream_t s) {
+    return sdda_dispatch(LB, VL, precision, has_up, 0, a, (unsigned)n_lblk, s);
+}
+
+cudaError_t launch_level_split_sdda(int LB, int VL, int precision, bool has_up,
+                                    const LevelArgs& a, cudaStream_t s) {
+    if (a.n_strips < 2 || !a.it_state || a.phase < 0 || a.phase >= a.n_strips ||
+        a.split_nblk < 0 || a.split_nblk > 65535)
+        return cudaErrorInvalidValue;
+    LevelArgs b = a;
+    b.split_nblk = std::max(1, a.split_nblk);
+    b.strip_x0 = (int)((long long)a.phase * a.nx / a.n_strips);
+    b.strip_x1 = (int)((long long)(a.phase + 1) * a.nx / a.n_strips);
+    const int phase = a.phase == 0 ? 1 : (a.phase == a.n_strips - 1 ? 3 : 2);
+    return sdda_dispatch(LB, VL, precision, has_up, phase, b, (unsigned)b.split_nblk, s);
 }
 
 cudaError_t launch_level(int LB, int VL, int precision, bool level0, bool has_up, int n_lblk,

@@ -142,6 +142,14 @@ cudaError_t launch_level_split(int LB, int VL, int precision, bool has_up, const
 bool level_split_supported(int LB, int VL);
 cudaError_t launch_level(int LB, int VL, int precision, bool level0, bool has_up, int n_lblk,
                          const LevelArgs& a, cudaStream_t s);
+// The shared-DDA march of a cascade >= 1 (one warp walks the DDA of 32 rays into shared
+// memory and replays it for their wavelengths): whether a launch can take it, the unsplit
+// launch and one phase of a strip-split cascade (arguments as launch_level(_split)).
+bool level_sdda_supported(int LB, int VL, const LevelArgs& a);
+cudaError_t launch_level_sdda(int LB, int VL, int precision, bool has_up, int n_lblk,
+                              const LevelArgs& a, cudaStream_t s);
+cudaError_t launch_level_split_sdda(int LB, int VL, int precision, bool has_up,
+                                    const LevelArgs& a, cudaStream_t s);
 cudaError_t launch_scales(int n_lblk, const unsigned int* smax_bits, float* scale,
                           cudaStream_t s);
 

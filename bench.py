@@ -217,6 +217,7 @@ def run_ours(args):
                     precision=args.precision, lambda_block=args.lambda_block,
                     lambda_per_lane=args.lambda_per_lane, bilinear_fix=args.bilinear_fix,
                     n_incl=args.n_incl)
+    plan.set_march(rcx.Plan.MARCH_SHARED_DDA if args.march == "shared-dda" else rcx.Plan.MARCH_LANE_GROUP)
     plan.reserve(n_lambda)
     stream = torch.cuda.current_stream()
 
@@ -355,6 +356,7 @@ def run_ours(args):
                    "n_lambda_per_gpu": n_lambda, "n_cascades": n_casc, "dirs0": 4, "branching": 4,
                    "interval0": 1.0, "storage": args.precision,
                    "bilinear_fix": bool(args.bilinear_fix), "n_incl": args.n_incl,
+                   "march": args.march,
                    "lambda_block": args.lambda_block or 16,
                    "lambda_per_lane": args.lambda_per_lane or min(args.lambda_block or 16, 4),
                    "l2": (f"inputs (chi+eta {2 * n_lambda * n_side * n_side * 4 / 1e6:.0f} MB per GPU) "
@@ -799,6 +801,8 @@ def main():
     ap.add_argument("--n-lambda", type=int, default=N_LAMBDA, help="wavelengths per GPU")
     ap.add_argument("--n-cascades", type=int, default=N_CASC)
     ap.add_argument("--precision", default="f32", choices=["f32", "f16", "bf16"])
+    ap.add_argument("--march", choices=["shared-dda", "lane-group"], default="shared-dda",
+                    help="cascades >= 1: shared-DDA march (default) or lane-group march")
     ap.add_argument("--lambda-block", type=int, default=0)
     ap.add_argument("--lambda-per-lane", type=int, default=0)
     args = ap.parse_args()

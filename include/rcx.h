@@ -227,6 +227,21 @@ rc_status rc_plan_set_lane_layout(rc_plan_t plan, int lambda_block, int lambda_p
 rc_status rc_plan_get_lane_layout(rc_plan_t plan, int* lambda_block, int* lambda_per_lane);
 
 /*
+ * How the cascades >= 1 walk their rays (the DDA of Sec. 3.2 through the uniform voxel grid;
+ * no counterpart choice in the paper, whose DexRT walks each ray in its own thread).
+ *   RC_MARCH_LANE_GROUP  every lane of a ray's lane group walks the ray's DDA itself.
+ *   RC_MARCH_SHARED_DDA  (default) a warp owns 32 rays; each lane walks one ray's DDA for a
+ *                        chunk of steps into shared memory, and the warp replays the chunk for
+ *                        the rays' wavelengths.  Applies to dense plans with a power-of-two
+ *                        direction count, the 16 x 4 lane layout and no bilinear fix; other
+ *                        plans keep the lane-group march.  Both give identical results.
+ * Takes effect at the next solve.  Errors: RC_ERR_ARG.
+ */
+enum { RC_MARCH_LANE_GROUP = 0, RC_MARCH_SHARED_DDA = 1 };
+rc_status rc_plan_set_march(rc_plan_t plan, int mode);
+rc_status rc_plan_get_march(rc_plan_t plan, int* mode);
+
+/*
  * rc_plan_autotune -- times the formal solution of these inputs (device buffers as
  * rc_formal_solve; J is overwritten) with each candidate lane layout (16/4, 8/4, 32/4, 8/2,
  * 4/4, 4/2, 4/1, 2/2, 1/1 wavelengths per ray / per lane; blocks wider than twice n_lambda

@@ -193,6 +193,7 @@ struct rc_plan_s {
     rc_options opt{};
     int LB = 4;                      // wavelengths per lane group (one ray)
     int VL = 1;                      // wavelengths per lane
+    int march = RC_MARCH_SHARED_DDA; // cascades >= 1: shared-DDA march where it applies
     int n_incl = 1;                  // inclination quadrature (2D invariance)
     float* d_incl = nullptr;         // [r_j (n_incl)][w_j (n_incl)]
     float* d_vout = nullptr;         // per-inclination cascade-0 outputs before the reduction

@@ -320,6 +320,8 @@ rc_status solve_device(rc_plan_s* p, const float* chi, const float* eta, int n_l
         rcx::LevelArgs a = rcx::level_args(p, i, n_lambda, Jv, alov, Jeffv, alocv);
         const bool has_up = i < live - 1;
         const int S = strips_for_impl(p, i);
+        const bool sdda = i > 0 && p->march == RC_MARCH_SHARED_DDA &&
+                          rcx::level_sdda_supported(LB, p->VL, a);
         if (S > 1) {
             // one launch per strip, over as many wavelength blocks as it_state holds
             const size_t per_blk = (size_t)a.rays * LB * sizeof(float2);
@@ -331,15 +333,15 @@ rc_status solve_device(rc_plan_s* p, const float* chi, const float* eta, int n_l
                     a.split_lb = lb;
                     a.split_nblk = std::min(G, n_lblk - lb);
                     a.phase = ph;
-                    if ((e = rcx::launch_level_split(LB, p->VL, p->opt.precision, has_up, a, s)) !=
-                        cudaSuccess)
-                        return cuda_fail(e, "cascade launch (strips)");
+                    e = sdda ? rcx::launch_level_split_sdda(LB, p->VL, p->opt.precision, has_up, a, s)
+                             : rcx::launch_level_split(LB, p->VL, p->opt.precision, has_up, a, s);
+                    if (e != cudaSuccess) return cuda_fail(e, "cascade launch (strips)");
                     ++launches;
                 }
         } else {
-            if ((e = rcx::launch_level(LB, p->VL, p->opt.precision, i == 0, has_up, n_lblk, a,
-                                       s)) != cudaSuccess)
-                return cuda_fail(e, "cascade launch");
+            e = sdda ? rcx::launch_level_sdda(LB, p->VL, p->opt.precision, has_up, n_lblk, a, s)
+                     : rcx::launch_level(LB, p->VL, p->opt.precision, i == 0, has_up, n_lblk, a, s);
+            if (e != cudaSuccess) return cuda_fail(e, "cascade launch");
             ++launches;
         }
         mark("cascade " + std::to_string(i));
@@ -746,6 +748,22 @@ rc_status rc_plan_set_lane_layout(rc_plan_t p, int lambda_block, int lambda_per_
         return fail(RC_ERR_ARG, "rc_plan_set_lane_layout: nx * nz * lambda_block too large");
     DeviceGuard dg(p->device);
     return rcx::plan_set_layout(p, LB, VL);
+}
+
+rc_status rc_plan_set_march(rc_plan_t p, int mode) {
+    g_last_error.clear();
+    if (!p) return fail(RC_ERR_ARG, "rc_plan_set_march: plan is NULL");
+    if (mode != RC_MARCH_LANE_GROUP && mode != RC_MARCH_SHARED_DDA)
+        return fail(RC_ERR_ARG, "rc_plan_set_march: mode must be RC_MARCH_LANE_GROUP or "
+                                "RC_MARCH_SHARED_DDA");
+    p->march = mode;
+    return RC_OK;
+}
+
+rc_status rc_plan_get_march(rc_plan_t p, int* mode) {
+    if (!p || !mode) return fail(RC_ERR_ARG, "rc_plan_get_march: NULL argument");
+    *mode = p->march;
+    return RC_OK;
 }
 
 rc_status rc_plan_get_lane_layout(rc_plan_t p, int* lambda_block, int* lambda_per_lane) {

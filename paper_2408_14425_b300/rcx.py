@@ -28,6 +28,7 @@ EXPORTS = [
     "rc_plan_launch_times", "rc_plan_launch_name", "rc_formal_solve_noalloc",
     "rc_formal_solve_mali", "rc_atom_create", "rc_atom_destroy", "rc_atom_n_lambda", "rc_lte",
     "rc_emis_opac", "rc_stat_eq", "rc_nlte_solve", "rc_plan_set_lane_layout",
+    "rc_plan_set_march", "rc_plan_get_march",
     "rc_plan_get_lane_layout", "rc_plan_autotune", "rc_batch_create", "rc_batch_run",
     "rc_batch_info", "rc_batch_destroy", "rc_formal_solve_batched", "rc_mlp_create",
     "rc_mlp_destroy", "rc_mlp_n_params", "rc_mlp_set_params", "rc_mlp_get_params",
@@ -143,6 +144,10 @@ def load():
     L.rc_plan_set_lane_layout.restype = ctypes.c_int
     L.rc_plan_get_lane_layout.argtypes = [_vp, _ip, _ip]
     L.rc_plan_get_lane_layout.restype = ctypes.c_int
+    L.rc_plan_set_march.argtypes = [_vp, ctypes.c_int]
+    L.rc_plan_set_march.restype = ctypes.c_int
+    L.rc_plan_get_march.argtypes = [_vp, _ip]
+    L.rc_plan_get_march.restype = ctypes.c_int
     L.rc_plan_autotune.argtypes = [_vp, _vp, _vp, ctypes.c_int, _vp, _vp, _ip, _ip]
     L.rc_plan_autotune.restype = ctypes.c_int
     _pp = ctypes.POINTER(_vp)
@@ -336,6 +341,17 @@ class Plan:
         a, b = ctypes.c_int(), ctypes.c_int()
         check(load().rc_plan_get_lane_layout(self._h, ctypes.byref(a), ctypes.byref(b)))
         return a.value, b.value
+
+    MARCH_LANE_GROUP, MARCH_SHARED_DDA = 0, 1
+
+    def set_march(self, mode: int):
+        """rc_plan_set_march: 0 lane-group DDA, 1 shared DDA (default where it applies)."""
+        check(load().rc_plan_set_march(self._h, int(mode)))
+
+    def march(self) -> int:
+        m = ctypes.c_int()
+        check(load().rc_plan_get_march(self._h, ctypes.byref(m)))
+        return m.value
 
     def autotune(self, chi, eta, J, stream=None):
         """rc_plan_autotune: keep the fastest lane layout for these inputs; returns it."""

@@ -80,3 +80,8 @@ def test_null_arguments(lib):
     assert lib.rc_plan_reserve(None, 4) == -1
     lib.rc_plan_destroy(None)  # no-op
     assert lib.rc_plan_scratch_bytes(None) == 0
+
+
+def test_march_mode_setter_rejects_bad_arguments(lib):
+    assert lib.rc_plan_set_march(None, 1) == -1
+    assert lib.rc_plan_get_march(None, None) == -1

@@ -400,3 +400,28 @@ def test_large_thick_uniform_domain():
     assert rel < 1e-5, rel
     assert p.last_launch_count() > 1 + 8     # strips on the long cascades
     del chi, eta, J
+
+
+@pytest.mark.parametrize("nx,nz,C,strips,prec,nl", [
+    (96, 80, 5, 0, "f32", 20), (130, 67, 6, 4, "f32", 17), (64, 64, 5, 3, "bf16", 16),
+    (257, 129, 7, 0, "f16", 33), (200, 200, 6, 2, "f32", 1)])
+def test_shared_dda_march_equals_lane_group_march(nx, nz, C, strips, prec, nl):
+    """The shared-DDA march (one warp walks 32 rays' DDA into shared memory and replays it
+    for their wavelengths) performs the same arithmetic as the lane-group march: J, the
+    operator outputs and the merged result agree bit for bit, unsplit and strip by strip,
+    on ragged grids whose ray counts leave partial warps and CTAs."""
+    rcx = _rcx()
+    rng = np.random.default_rng(nx + nz)
+    chi = (10 ** rng.uniform(-4, 1.5, (nl, nz, nx))).astype(np.float32)
+    eta = (chi * 10 ** rng.uniform(-1, 1, chi.shape)).astype(np.float32)
+    dchi, deta = torch.from_numpy(chi).cuda(), torch.from_numpy(eta).cuda()
+    out = []
+    for mode in (rcx.Plan.MARCH_LANE_GROUP, rcx.Plan.MARCH_SHARED_DDA):
+        p = rcx.Plan(nx, nz, C, precision=prec, strips=strips)
+        p.set_march(mode)
+        assert p.march() == mode
+        J, Jeff, aloc = p.formal_solve_mali(dchi, deta)
+        out.append((J.cpu(), Jeff.cpu(), aloc.cpu()))
+        p.close()
+    for a, b in zip(*out):
+        assert torch.equal(a, b), f"max abs diff {(a - b).abs().max().item():.3e}"

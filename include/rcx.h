@@ -410,15 +410,24 @@ rc_status rc_mlp_get_params(rc_mlp_t net, float* theta, float* mean, float* std_
 rc_status rc_mlp_fit_normalization(rc_mlp_t net, const float* X, long long N, void* stream);
 /* Y [B][3] = network(X [B][6]); device buffers, asynchronous. */
 rc_status rc_mlp_forward(rc_mlp_t net, const float* X, long long B, float* Y, void* stream);
-/* Inference path of rc_mlp_forward (and so of rc_surrogate_seed): enable != 0 runs the 64 x 64
- * layer on the tensor cores (tcgen05.mma, bf16 h1 and W2 from shared memory, FP32 accumulator in
- * tensor memory, 128 samples per CTA); 0 (default) uses FP32 FMAs with the bf16 weights.
+/* Tensor cores for the network (enable is a bit set; 0, the default, uses FP32 FMAs with the
+ * bf16 weights everywhere):
+ *   RC_MLP_TC_INFERENCE (1)  rc_mlp_forward (and so rc_surrogate_seed) runs the 64 x 64 layer on
+ *                            the tensor cores (tcgen05.mma, bf16 h1 and W2 from shared memory,
+ *                            FP32 accumulator in tensor memory, 128 samples per CTA);
+ *   RC_MLP_TC_TRAINING (2)   rc_mlp_loss_grad and rc_mlp_train run the three 64-wide products of
+ *                            a tile (h1 W2^T, dh2 W2, dh2^T h1) on the tensor cores, each FP32
+ *                            activation passed as two bf16 parts (hi + lo, ~16 significant bits),
+ *                            so the gradient keeps the FMA path's accuracy; per-tile partial
+ *                            gradients are summed in a fixed order as on the FMA path
+ *                            (reproducible bit for bit, though not bit-equal to the FMA path).
  * rc_mlp_tensor_core_status reports RC_ERR_TIMEOUT if a tensor-core wait ever ran out (the
  * kernel then skipped its outputs).  A CTA whose wait ran out waits once more, 8x as long,
  * before it releases its tensor memory; if the MMAs still have not completed it leaves the
  * 64 columns allocated rather than free memory a late MMA could still write, and the message
  * says so (later tensor-core launches on that SM have less tensor memory; recreate the
- * context).  Training always uses the FMA path. */
+ * context).  A training tile whose wait ran out stores a zero gradient. */
+enum { RC_MLP_TC_INFERENCE = 1, RC_MLP_TC_TRAINING = 2 };
 rc_status rc_mlp_use_tensor_cores(rc_mlp_t net, int enable);
 rc_status rc_mlp_tensor_core_status(rc_mlp_t net);
 

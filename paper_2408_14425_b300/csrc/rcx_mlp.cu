@@ -437,6 +437,315 @@ mlp_forward_tc_kernel(const float* __restrict__ wbf, const float* __restrict__ n
     }
 }
 
+// ---------------------------------------------------------------------------
+// training on the tensor cores.  Per tile of 128 samples the three 64-wide products --
+// h1 W2^T (forward), dh2 W2 (the gradient reaching h1) and dh2^T h1 (the gradient of W2)
+// -- run as tcgen05 MMAs (M = 128, N = 64, K = 16 per instruction, FP32 accumulators in
+// 192 TMEM columns).  The bf16 operands carry the FP32 activations in two parts,
+// x = hi + lo with hi = bf16(x) and lo = bf16(x - hi) (about 16 significant bits): W2 is
+// bf16 already, so the first two products take hi and lo of the activation (two MMA
+// passes), the third hi*hi + hi*lo + lo*hi (three passes; lo*lo is below 2^-16 relative).
+// The 6-wide and 3-wide layers, tanh, the loss and the bias gradients stay on the FMA
+// pipes as in mlp_tile_kernel, and the tile stores its partial gradient for the same
+// fixed-order sum.
+// dh2^T h1 is a 64-row product: it is issued with M = 128 and its rows 64..127 (which read
+// the operand tiles that follow in shared memory) are not used.
+// ---------------------------------------------------------------------------
+struct TrainTcSmem {
+    alignas(1024) unsigned char wf[NH * NH * 2];       // B, K = 64: W2 [o][k]
+    alignas(1024) unsigned char wb[NH * NH * 2];       // B, K = 64: W2^T [k][o]
+    alignas(1024) unsigned char a_hi[TILE * NH * 2];   // A, K = 64: h1 [s][k], then dh2 [s][o]
+    alignas(1024) unsigned char a_lo[TILE * NH * 2];
+    alignas(1024) unsigned char t_hi[NH * TILE * 2];   // A, K = 128: dh2^T [o][s] (64 rows)
+    alignas(1024) unsigned char t_lo[NH * TILE * 2];
+    alignas(1024) unsigned char h_hi[NH * TILE * 2];   // B, K = 128: h1^T [k][s]
+    alignas(1024) unsigned char h_lo[NH * TILE * 2];
+    float w1[NH * NI], b1[NH], b2[NH], w3[NO * NH], b3[NO];
+    float mean[NI], istd[NI];
+    float xn[TILE * NI];
+    float h1[TILE * LD];
+    float hd[TILE * LD];      // h2, then dh2 (in place), then dh1
+    float dy[TILE * NO];
+    float red[THREADS / 32];
+    alignas(8) unsigned long long mbar;
+    unsigned tmem_base;
+};
+
+// byte offset of element (row r, k) of a K-major no-swizzle operand of K columns: 8-row x
+// 16-byte core matrices, K step 128 B, row-group step K / 8 x 128 B
+__device__ __forceinline__ int core_offset_k(int r, int k, int K) {
+    return (r >> 3) * (K * 16) + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2;
+}
+
+__device__ __forceinline__ unsigned long long smem_desc_sbo(const void* p, unsigned sbo) {
+    const unsigned addr = (unsigned)__cvta_generic_to_shared(p);
+    unsigned long long d = 0;
+    d |= (unsigned long long)((addr >> 4) & 0x3FFF);          // start address
+    d |= (unsigned long long)((128 >> 4) & 0x3FFF) << 16;      // leading (K) byte offset
+    d |= (unsigned long long)((sbo >> 4) & 0x3FFF) << 32;      // stride (row group) byte offset
+    d |= 1ull << 46;                                           // descriptor version (sm_100)
+    return d;
+}
+
+__device__ __forceinline__ void mma_bf16(unsigned tmem, unsigned long long da,
+                                         unsigned long long db, unsigned idesc, unsigned acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
+        ::"r"(tmem), "l"(da), "l"(db), "r"(idesc), "r"(acc));
+}
+
+// x as hi + lo bf16 parts at byte offsets o_hi / o_lo of the two tiles
+__device__ __forceinline__ void put_split(unsigned char* hi, unsigned char* lo, int off, float x) {
+    const __nv_bfloat16 h = __float2bfloat16_rn(x);
+    *reinterpret_cast<__nv_bfloat16*>(hi + off) = h;
+    *reinterpret_cast<__nv_bfloat16*>(lo + off) = __float2bfloat16_rn(x - __bfloat162float(h));
+}
+
+// 32 consecutive FP32 accumulator columns of this warp's 32 TMEM lanes
+__device__ __forceinline__ void tmem_ld32(unsigned taddr, unsigned (&v)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+          "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]),
+          "=r"(v[13]), "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]),
+          "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]),
+          "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]),
+          "=r"(v[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+__global__ void __launch_bounds__(THREADS)
+mlp_train_tc_kernel(const float* __restrict__ wbf, const float* __restrict__ norm,
+                    const float* __restrict__ X, const float* __restrict__ Yt, long long B,
+                    float* __restrict__ part, int* __restrict__ err) {
+    extern __shared__ __align__(1024) unsigned char tt_raw[];
+    const unsigned raw_s = (unsigned)__cvta_generic_to_shared(tt_raw);
+    TrainTcSmem& S = *reinterpret_cast<TrainTcSmem*>(tt_raw + (((raw_s + 1023u) & ~1023u) - raw_s));
+    float* const grad = part + (size_t)blockIdx.x * (NPARAM + 1);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const long long s0 = (long long)blockIdx.x * TILE;
+    const int nvalid = (int)min((long long)TILE, B - s0);
+
+    if (warp == 0) {   // TMEM: 256 columns (D1 at 0, D2 at 64, D3 at 128)
+        const unsigned dst = (unsigned)__cvta_generic_to_shared(&S.tmem_base);
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 256;" ::"r"(dst));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (tid == 0) {
+        const unsigned mb = (unsigned)__cvta_generic_to_shared(&S.mbar);
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb));
+    }
+    for (int i = tid; i < NH * NI; i += THREADS) S.w1[i] = wbf[OFF_W1 + i];
+    for (int i = tid; i < NH; i += THREADS) {
+        S.b1[i] = wbf[OFF_B1 + i];
+        S.b2[i] = wbf[OFF_B2 + i];
+    }
+    for (int i = tid; i < NO * NH; i += THREADS) S.w3[i] = wbf[OFF_W3 + i];
+    if (tid < NO) S.b3[tid] = wbf[OFF_B3 + tid];
+    if (tid < NI) {
+        S.mean[tid] = norm[tid];
+        S.istd[tid] = 1.0f / norm[NI + tid];
+    }
+    for (int i = tid; i < NH * NH; i += THREADS) {
+        const int o = i / NH, k = i % NH;
+        const __nv_bfloat16 w = __float2bfloat16_rn(wbf[OFF_W2 + i]);   // exact: wbf is bf16
+        *reinterpret_cast<__nv_bfloat16*>(S.wf + core_offset_k(o, k, NH)) = w;
+        *reinterpret_cast<__nv_bfloat16*>(S.wb + core_offset_k(k, o, NH)) = w;
+    }
+    __syncthreads();
+    for (int i = tid; i < TILE * NI; i += THREADS) {
+        const int r = i / NI, f = i % NI;
+        S.xn[i] = r < nvalid ? (X[(s0 + r) * NI + f] - S.mean[f]) * S.istd[f] : 0.0f;
+    }
+    __syncthreads();
+    // h1 = tanh(W1 xn + b1): FP32, and split into the two bf16 layouts the MMAs read
+    for (int i = tid; i < TILE * NH; i += THREADS) {
+        const int r = i / NH, o = i % NH;
+        float a = S.b1[o];
+#pragma unroll
+        for (int f = 0; f < NI; ++f) a = fmaf(S.w1[o * NI + f], S.xn[r * NI + f], a);
+        const float h = tanhf(a);
+        S.h1[r * LD + o] = h;
+        put_split(S.a_hi, S.a_lo, core_offset_k(r, o, NH), h);
+        put_split(S.h_hi, S.h_lo, core_offset_k(o, r, TILE), h);
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const unsigned tmem = S.tmem_base;
+    const unsigned mb = (unsigned)__cvta_generic_to_shared(&S.mbar);
+    const unsigned idesc = mma_idesc();
+    if (tid == 0) {   // D1 = (h1_hi + h1_lo) W2^T
+        for (int part_i = 0; part_i < 2; ++part_i) {
+            const unsigned char* A = part_i ? S.a_lo : S.a_hi;
+#pragma unroll
+            for (int kk = 0; kk < NH / 16; ++kk)
+                mma_bf16(tmem, smem_desc_sbo(A + kk * 256, NH * 16),
+                         smem_desc_sbo(S.wf + kk * 256, NH * 16), idesc,
+                         (part_i | kk) ? 1u : 0u);
+        }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                     ::"r"(mb) : "memory");
+    }
+    unsigned done = mbar_wait_bounded(mb, 0, kTcWaitLimit) ? 1u : 0u;
+    done = __syncthreads_and(done);
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const int rbase = 32 * (warp & 3), cbase = 32 * (warp >> 2);
+    const unsigned tlane = (unsigned)rbase << 16;
+    if (done) {   // h2 = tanh(D1 + b2)
+        unsigned v[32];
+        tmem_ld32(tmem + tlane + (unsigned)cbase, v);
+        const int r = rbase + lane;
+#pragma unroll
+        for (int c = 0; c < 32; ++c)
+            S.hd[r * LD + cbase + c] = tanhf(__uint_as_float(v[c]) + S.b2[cbase + c]);
+    }
+    __syncthreads();
+    // y = W3 h2 + b3, loss, dy
+    float lsum = 0.0f;
+    for (int i = tid; i < TILE * NO; i += THREADS) {
+        const int r = i / NO, o = i % NO;
+        float a = S.b3[o];
+        for (int k = 0; k < NH; ++k) a = fmaf(S.w3[o * NH + k], S.hd[r * LD + k], a);
+        if (r < nvalid) {
+            const float d = a - Yt[(s0 + r) * NO + o];
+            lsum += d * d;
+            S.dy[i] = 2.0f * d / (float)(B * NO);
+        } else {
+            S.dy[i] = 0.0f;
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) lsum += __shfl_xor_sync(0xffffffffu, lsum, o);
+    if (lane == 0) S.red[warp] = lsum;
+    __syncthreads();
+    if (tid == 0) {
+        float t = 0.0f;
+        for (int w = 0; w < THREADS / 32; ++w) t += S.red[w];
+        grad[NPARAM] = t / (float)(B * NO);
+    }
+    // dW3, db3
+    if (tid < NO * NH) {
+        const int o = tid / NH, k = tid % NH;
+        float g = 0.0f;
+        for (int r = 0; r < TILE; ++r) g = fmaf(S.dy[r * NO + o], S.hd[r * LD + k], g);
+        grad[OFF_W3 + tid] = g;
+    } else if (tid < NO * NH + NO) {
+        const int o = tid - NO * NH;
+        float g = 0.0f;
+        for (int r = 0; r < TILE; ++r) g += S.dy[r * NO + o];
+        grad[OFF_B3 + o] = g;
+    }
+    __syncthreads();
+    // dh2 = (W3^T dy) (1 - h2^2), in place, and split into the layouts of the backward MMAs
+    for (int i = tid; i < TILE * NH; i += THREADS) {
+        const int r = i / NH, k = i % NH;
+        float a = 0.0f;
+#pragma unroll
+        for (int o = 0; o < NO; ++o) a = fmaf(S.dy[r * NO + o], S.w3[o * NH + k], a);
+        const float h = S.hd[r * LD + k];
+        const float d = a * (1.0f - h * h);
+        S.hd[r * LD + k] = d;
+        put_split(S.a_hi, S.a_lo, core_offset_k(r, k, NH), d);
+        put_split(S.t_hi, S.t_lo, core_offset_k(k, r, TILE), d);
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (tid == 0 && done) {
+        // D2 = (dh2_hi + dh2_lo) W2
+        for (int part_i = 0; part_i < 2; ++part_i) {
+            const unsigned char* A = part_i ? S.a_lo : S.a_hi;
+#pragma unroll
+            for (int kk = 0; kk < NH / 16; ++kk)
+                mma_bf16(tmem + 64, smem_desc_sbo(A + kk * 256, NH * 16),
+                         smem_desc_sbo(S.wb + kk * 256, NH * 16), idesc,
+                         (part_i | kk) ? 1u : 0u);
+        }
+        // D3 = dh2^T h1 over the 128 samples: hi hi + hi lo + lo hi
+        for (int part_i = 0; part_i < 3; ++part_i) {
+            const unsigned char* A = part_i == 2 ? S.t_lo : S.t_hi;
+            const unsigned char* Bm = part_i == 1 ? S.h_lo : S.h_hi;
+#pragma unroll
+            for (int kk = 0; kk < TILE / 16; ++kk)
+                mma_bf16(tmem + 128, smem_desc_sbo(A + kk * 256, TILE * 16),
+                         smem_desc_sbo(Bm + kk * 256, TILE * 16), idesc,
+                         (part_i | kk) ? 1u : 0u);
+        }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                     ::"r"(mb) : "memory");
+    }
+    // db2 while the MMAs run
+    if (tid < NH) {
+        float gb = 0.0f;
+        for (int r = 0; r < TILE; ++r) gb += S.hd[r * LD + tid];
+        grad[OFF_B2 + tid] = gb;
+    }
+    unsigned done2 = done ? (mbar_wait_bounded(mb, 1, kTcWaitLimit) ? 1u : 0u) : 0u;
+    done2 = __syncthreads_and(done2);
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (done2) {
+        unsigned v[32];
+        // dh1 = D2 (1 - h1^2), over dh2 (db2 has been summed above)
+        tmem_ld32(tmem + tlane + 64u + (unsigned)cbase, v);
+        const int r = rbase + lane;
+#pragma unroll
+        for (int c = 0; c < 32; ++c) {
+            const float h = S.h1[r * LD + cbase + c];
+            S.hd[r * LD + cbase + c] = __uint_as_float(v[c]) * (1.0f - h * h);
+        }
+        // dW2 [o][k]: rows 0..63 of D3 (warps 0, 1, 4, 5 hold them)
+        if (rbase < NH) {
+            tmem_ld32(tmem + tlane + 128u + (unsigned)cbase, v);
+            float* g = grad + OFF_W2 + (size_t)r * NH + cbase;
+#pragma unroll
+            for (int c = 0; c < 32; c += 4)
+                *reinterpret_cast<float4*>(g + c) =
+                    make_float4(__uint_as_float(v[c]), __uint_as_float(v[c + 1]),
+                                __uint_as_float(v[c + 2]), __uint_as_float(v[c + 3]));
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    // Release the accumulators only once the MMAs writing them are known to be complete
+    // (as in mlp_forward_tc_kernel); a tile whose waits ran out stores a zero gradient.
+    bool release = done2 != 0;
+    if (!done2) {
+        const unsigned phase = done ? 1u : 0u;
+        unsigned late = mbar_wait_bounded(mb, phase, 8u * kTcWaitLimit) ? 1u : 0u;
+        late = __syncthreads_and(late);
+        release = late != 0;
+        if (tid == 0) atomicExch(err, release ? 1 : 2);
+        for (int i = tid; i <= NPARAM; i += THREADS) grad[i] = 0.0f;
+    }
+    if (warp == 0 && release) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 256;" ::"r"(tmem));
+    }
+    if (!done2) return;
+    __syncthreads();
+    // dW1[o][f] = sum_s dh1[s][o] xn[s][f]; db1
+    for (int i = tid; i < NH * NI + NH; i += THREADS) {
+        if (i < NH * NI) {
+            const int o = i / NI, f = i % NI;
+            float g = 0.0f;
+            for (int r = 0; r < TILE; ++r) g = fmaf(S.hd[r * LD + o], S.xn[r * NI + f], g);
+            grad[OFF_W1 + i] = g;
+        } else {
+            const int o = i - NH * NI;
+            float g = 0.0f;
+            for (int r = 0; r < TILE; ++r) g += S.hd[r * LD + o];
+            grad[OFF_B1 + o] = g;
+        }
+    }
+}
+
 // Adam (Kingma & Ba 2015) on the FP32 master weights; also refreshes the bf16-rounded copy.
 // grad[i] = sum over tiles t of part[t][i], t ascending (i = NPARAM: the loss)
 __global__ void grad_sum_kernel(const float* __restrict__ part, long long tiles,
@@ -533,6 +842,7 @@ struct rc_mlp_s {
     unsigned long long seed = 0;
     float* h_loss = nullptr;       // pinned
     bool tensor_cores = false;     // inference through mlp_forward_tc_kernel
+    bool tc_train = false;         // loss and gradient through mlp_train_tc_kernel
     int* d_err = nullptr;          // set if a tensor-core wait ran out
     float* part = nullptr;         // per-tile partial gradients and losses [tiles][NPARAM + 1]
     long long part_tiles = 0;
@@ -542,6 +852,7 @@ namespace {
 
 size_t smem_bytes() { return sizeof(Smem); }
 size_t tc_smem_bytes() { return sizeof(TcSmem) + 1024; }   // + alignment slack
+size_t tt_smem_bytes() { return sizeof(TrainTcSmem) + 1024; }
 
 rc_status ensure_configured() {
     static bool done = false;
@@ -554,6 +865,9 @@ rc_status ensure_configured() {
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(mlp_forward_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)tc_smem_bytes());
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(mlp_train_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)tt_smem_bytes());
     if (e != cudaSuccess) return mcuda(e, "mlp: shared-memory opt-in");
     done = true;
     return RC_OK;
@@ -573,8 +887,12 @@ rc_status loss_grad(rc_mlp_t n, const float* X, const float* Yt, long long B, cu
             return mcuda(e, "mlp: partial-gradient buffer");
         n->part_tiles = tiles;
     }
-    mlp_tile_kernel<true><<<(unsigned)tiles, THREADS, smem_bytes(), s>>>(n->wbf, n->norm, X, Yt, B,
-                                                                        nullptr, n->part);
+    if (n->tc_train)
+        mlp_train_tc_kernel<<<(unsigned)tiles, THREADS, tt_smem_bytes(), s>>>(n->wbf, n->norm, X, Yt,
+                                                                             B, n->part, n->d_err);
+    else
+        mlp_tile_kernel<true><<<(unsigned)tiles, THREADS, smem_bytes(), s>>>(n->wbf, n->norm, X, Yt,
+                                                                            B, nullptr, n->part);
     // grad and the loss after it: the tiles' partials summed in tile order
     grad_sum_kernel<<<(NPARAM + 1 + 255) / 256, 256, 0, s>>>(n->part, tiles, n->grad);
     e = cudaGetLastError();
@@ -715,7 +1033,8 @@ rc_status rc_mlp_use_tensor_cores(rc_mlp_t n, int enable) {
         if (e == cudaSuccess) e = cudaMemset(n->d_err, 0, sizeof(int));
         if (e != cudaSuccess) return mcuda(e, "rc_mlp_use_tensor_cores");
     }
-    n->tensor_cores = enable != 0;
+    n->tensor_cores = (enable & RC_MLP_TC_INFERENCE) != 0;
+    n->tc_train = (enable & RC_MLP_TC_TRAINING) != 0;
     return RC_OK;
 }
 

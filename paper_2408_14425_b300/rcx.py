@@ -616,9 +616,10 @@ class MLP:
                                        sd.ctypes.data_as(fp)))
         return th, mu, sd
 
-    def use_tensor_cores(self, enable: bool = True):
-        """Inference with the 64 x 64 layer on tcgen05 tensor cores (bf16 in, FP32 out)."""
-        check(load().rc_mlp_use_tensor_cores(self._h, int(enable)))
+    def use_tensor_cores(self, enable: bool = True, training: bool = False):
+        """rc_mlp_use_tensor_cores: inference with the 64 x 64 layer on tcgen05 tensor cores
+        (bf16 in, FP32 out) when enable; training's 64-wide products on them when training."""
+        check(load().rc_mlp_use_tensor_cores(self._h, (1 if enable else 0) | (2 if training else 0)))
 
     def tensor_core_status(self):
         check(load().rc_mlp_tensor_core_status(self._h))

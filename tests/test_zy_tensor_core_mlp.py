@@ -69,3 +69,53 @@ def test_tensor_core_forward(B):
                           f"{err[tuple(bad[0])]} > {bound[tuple(bad[0])]}"
     # the FMA path keeps h1 in FP32: the two differ only by the bf16 rounding of h1
     assert np.abs(y_tc - y_fma).max() < 2e-2 * scale
+
+
+def test_tensor_core_training_gradient_matches_oracle():
+    """The training tile on the tensor cores (h1 W2^T, dh2 W2 and dh2^T h1 as tcgen05 MMAs,
+    activations as hi + lo bf16 parts): loss and gradient against the FP64 oracle within the
+    tolerance of the FMA path's gradient test."""
+    from paper_2408_14425_b300 import build, rcx
+    build.build()
+    rng = np.random.default_rng(0)
+    theta = rng.normal(0, 0.3, 4803).astype(np.float32)
+    X = rng.normal([4.0, 16.0, 17.0, -12.0, -13.0, -9.0], [0.8, 1.0, 0.9, 1.5, 1.5, 1.5],
+                   (1000, 6)).astype(np.float32)
+    Y = rng.normal(0, 1.0, (1000, 3)).astype(np.float32)
+    mean, std = X.mean(axis=0).astype(np.float32), X.std(axis=0).astype(np.float32)
+    net = rcx.MLP()
+    net.set_params(theta, mean, std)
+    net.use_tensor_cores(False, training=True)
+    loss, g = net.loss_grad(torch.from_numpy(X).cuda(), torch.from_numpy(Y).cuda())
+    net.tensor_core_status()
+    loss_ref, g_ref = omlp.loss_and_grad(omlp.round_bf16(theta), X, Y, mean.astype(np.float64),
+                                         std.astype(np.float64))
+    assert loss == pytest.approx(loss_ref, rel=1e-5, abs=0)
+    g = g.cpu().numpy()
+    err = np.abs(g - g_ref)
+    assert np.all(err <= 1e-4 * np.abs(g_ref) + 1e-6 * np.abs(g_ref).max()), \
+        f"max gradient error {err.max():.3e} (max |g| {np.abs(g_ref).max():.3e})"
+
+
+def test_tensor_core_training_is_reproducible_and_learns():
+    """Adam on the tensor-core training path: two runs from the same seed end with identical
+    parameters (fixed-order gradient sum), and the loss falls as on the FMA path."""
+    from paper_2408_14425_b300 import build, rcx
+    build.build()
+    rng = np.random.default_rng(1)
+    X = rng.normal(0, 1, (20000, 6)).astype(np.float32)
+    Y = np.stack([np.sin(X[:, 0]), np.tanh(X[:, 1] - X[:, 2]), 0.3 * X[:, 3] * X[:, 4]],
+                 axis=1).astype(np.float32)
+    dX, dY = torch.from_numpy(X).cuda(), torch.from_numpy(Y).cuda()
+    out = []
+    for _ in range(2):
+        net = rcx.MLP(seed=7)
+        net.use_tensor_cores(False, training=True)
+        net.fit_normalization(dX)
+        l0, _ = net.loss_grad(dX, dY)
+        net.train(dX, dY, batch=1024, steps=600, lr=3e-3, record=False)
+        l1, _ = net.loss_grad(dX, dY)
+        net.tensor_core_status()
+        out.append((net.get_params()[0], l0, l1))
+    np.testing.assert_array_equal(out[0][0], out[1][0])
+    assert out[0][2] < 0.15 * out[0][1]

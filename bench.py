@@ -105,13 +105,13 @@ def _ncu_traffic(kernel_hash):
 
 
 def _issue_peak():
-    """Thread instructions per second with every issue slot busy: 4 warp instructions per
-    clock per SM x 32 lanes x SMs x the maximum SM clock.  Divided by the thread
-    instructions one wavelength-crossing takes (ncu), it bounds wavelength-crossings/s."""
+    """Warp instructions per second with every issue slot busy: 4 per clock per SM (one per
+    scheduler) x SMs x the maximum SM clock.  Divided by the warp instructions one
+    wavelength-crossing takes (ncu), it bounds wavelength-crossings/s."""
     import torch
     props = torch.cuda.get_device_properties(torch.cuda.current_device())
     clock_hz = 2032e6   # maximum SM clock of the B300 (nvidia-smi clocks.max.sm)
-    return props.multi_processor_count * 4 * 32 * clock_hz
+    return props.multi_processor_count * 4 * clock_hz
 
 
 class ClockSampler:
@@ -217,7 +217,8 @@ def run_ours(args):
                     precision=args.precision, lambda_block=args.lambda_block,
                     lambda_per_lane=args.lambda_per_lane, bilinear_fix=args.bilinear_fix,
                     n_incl=args.n_incl)
-    plan.set_march(rcx.Plan.MARCH_SHARED_DDA if args.march == "shared-dda" else rcx.Plan.MARCH_LANE_GROUP)
+    plan.set_march({"shared-dda": rcx.Plan.MARCH_SHARED_DDA, "lane-group": rcx.Plan.MARCH_LANE_GROUP,
+                    "shared-dda-all": rcx.Plan.MARCH_SHARED_DDA_ALL}[args.march])
     plan.reserve(n_lambda)
     stream = torch.cuda.current_stream()
 
@@ -297,7 +298,8 @@ def run_ours(args):
                        "alg_GBps": round(alg[i] / (ms / 1e3) / 1e9, 1) if ms > 0 else None})
     pack_ms = per_launch.get("pack", 0.0) / args.steps
     summ = _ncu_summary(khash) if headline else {}
-    ipc = summ.get("issue", {}).get("thread_inst_per_lambda_crossing")
+    ipc = summ.get("issue", {}).get("warp_inst_per_lambda_crossing")
+    tpc = summ.get("issue", {}).get("thread_inst_per_lambda_crossing")
     lam_cross = sum(cross["per_cascade"]) * n_lambda / (march_ms / 1e3)
     # the compulsory-traffic floor: chi, eta read and J written once (12 B per cell), every
     # cascade's merged intervals written and read back once (4 B per ray each way)
@@ -308,9 +310,10 @@ def run_ours(args):
                 "frac": round(lam_cross * ipc / _issue_peak(), 4) if ipc else None,
                 "traffic": traffic,
                 "traffic_unit": "DRAM bytes read + written per step by the march launches (ncu)",
-                "thread_inst_per_lambda_crossing": ipc,
-                "peak_kind": "derived: SMs x 4 warp instructions/clk x 32 lanes x 2032 MHz (max SM "
-                             "clock) / ncu-counted thread instructions per wavelength-crossing",
+                "warp_inst_per_lambda_crossing": ipc, "thread_inst_per_lambda_crossing": tpc,
+                "peak_kind": "derived: SMs x 4 warp instructions/clk x 2032 MHz (max SM clock) / "
+                             "ncu-counted warp instructions per wavelength-crossing (all march "
+                             "launches of a step, same kernel source)",
                 "kernel": f"cascade march (level kernels + cascade 0), all {n_casc} launches of a step",
                 "march_ms_per_step": round(march_ms, 3), "pack_ms_per_step": round(pack_ms, 3),
                 "per_cascade": levels, "kernel_source_sha256_16": khash,
@@ -801,8 +804,10 @@ def main():
     ap.add_argument("--n-lambda", type=int, default=N_LAMBDA, help="wavelengths per GPU")
     ap.add_argument("--n-cascades", type=int, default=N_CASC)
     ap.add_argument("--precision", default="f32", choices=["f32", "f16", "bf16"])
-    ap.add_argument("--march", choices=["shared-dda", "lane-group"], default="shared-dda",
-                    help="cascades >= 1: shared-DDA march (default) or lane-group march")
+    ap.add_argument("--march", choices=["shared-dda", "lane-group", "shared-dda-all"],
+                    default="shared-dda",
+                    help="cascades >= 1: shared-DDA march on the short cascades (default), "
+                         "lane-group march everywhere, or shared DDA everywhere")
     ap.add_argument("--lambda-block", type=int, default=0)
     ap.add_argument("--lambda-per-lane", type=int, default=0)
     args = ap.parse_args()

@@ -230,14 +230,19 @@ rc_status rc_plan_get_lane_layout(rc_plan_t plan, int* lambda_block, int* lambda
  * How the cascades >= 1 walk their rays (the DDA of Sec. 3.2 through the uniform voxel grid;
  * no counterpart choice in the paper, whose DexRT walks each ray in its own thread).
  *   RC_MARCH_LANE_GROUP  every lane of a ray's lane group walks the ray's DDA itself.
- *   RC_MARCH_SHARED_DDA  (default) a warp owns 32 rays; each lane walks one ray's DDA for a
- *                        chunk of steps into shared memory, and the warp replays the chunk for
- *                        the rays' wavelengths.  Applies to dense plans with a power-of-two
- *                        direction count, the 16 x 4 lane layout and no bilinear fix; other
- *                        plans keep the lane-group march.  Both give identical results.
- * Takes effect at the next solve.  Errors: RC_ERR_ARG.
+ *   RC_MARCH_SHARED_DDA  (default) the cascades whose intervals are at most 16 voxels long
+ *                        take the shared-DDA march: a warp owns 32 rays, each lane walks one
+ *                        ray's DDA for a chunk of steps into shared memory, and the warp
+ *                        replays the chunk for the rays' wavelengths (one DDA walk per 32 rays
+ *                        instead of per 8); longer cascades keep the lane-group march, which is
+ *                        faster there (its 8 rays per warp keep more gathers in flight and a
+ *                        smaller L2 working set).
+ *   RC_MARCH_SHARED_DDA_ALL  the shared-DDA march on every cascade >= 1 (for comparison).
+ * The shared-DDA march applies to dense plans with a power-of-two direction count, the 16 x 4
+ * lane layout and no bilinear fix; other plans keep the lane-group march.  All modes give
+ * identical results.  Takes effect at the next solve.  Errors: RC_ERR_ARG.
  */
-enum { RC_MARCH_LANE_GROUP = 0, RC_MARCH_SHARED_DDA = 1 };
+enum { RC_MARCH_LANE_GROUP = 0, RC_MARCH_SHARED_DDA = 1, RC_MARCH_SHARED_DDA_ALL = 2 };
 rc_status rc_plan_set_march(rc_plan_t plan, int mode);
 rc_status rc_plan_get_march(rc_plan_t plan, int* mode);
 
@@ -372,6 +377,33 @@ rc_status rc_emis_opac(rc_atom_t atom, const double* T, const double* pops, long
 rc_status rc_stat_eq(rc_atom_t atom, const double* T, const double* ne, const double* n_atom,
                      const float* J_eff, const float* alo_c, long long ncell, double* pops,
                      double* max_rel_change, void* stream);
+
+/*
+ * rc_stat_eq in two halves, for a non-LTE iteration whose wavelengths are split between
+ * processes (each runs the formal solution of its own range; Sec. 3.6 treats wavelengths as
+ * independent within an iteration).  The rates of Sec. 3.3 depend on the radiation field only
+ * through two integrals per line and cell, Jeff_bar = sum_k w_k phi_k J_eff and
+ * (1 - Lambda*)_bar = sum_k w_k phi_k (1 - Lambda*), and an integral over a range of a line's
+ * wavelengths is a partial sum of it (the profile is normalised over the whole line).
+ * rc_line_integrals -- the integrals over the atom's grid wavelengths
+ *   [lambda_begin, lambda_begin + lambda_count) (global indices, line after line):
+ *   J_eff, alo_c   device FP32 [lambda_count][ncell], the range's wavelengths only; alo_c NULL
+ *                  means Lambda* = 0.
+ *   out            device FP64 [n_lines][2][ncell]: (Jeff_bar, (1 - Lambda*)_bar) of each line
+ *                  over the range (0 for lines outside it).  Asynchronous.
+ * rc_stat_eq_integrals -- the update of rc_stat_eq from integrals summed over every range (an
+ *   all-reduce of the n_lines x 2 x ncell FP64 partials: 6 per cell for the 3-level atom);
+ *   T, ne, n_atom, pops, max_rel_change as rc_stat_eq.  Every process holding the same sums
+ *   computes the same populations.  With one range covering all wavelengths the two calls
+ *   equal rc_stat_eq bit for bit.
+ * Errors: RC_ERR_ARG (NULL arguments, range outside the grid), RC_ERR_CUDA.
+ */
+rc_status rc_line_integrals(rc_atom_t atom, const double* T, const float* J_eff, const float* alo_c,
+                            int lambda_begin, int lambda_count, long long ncell, double* out,
+                            void* stream);
+rc_status rc_stat_eq_integrals(rc_atom_t atom, const double* T, const double* ne,
+                               const double* n_atom, const double* integrals, long long ncell,
+                               double* pops, double* max_rel_change, void* stream);
 
 /*
  * rc_nlte_solve -- the non-LTE iteration (Sec. 3.3): repeat {rc_emis_opac, rc_formal_solve_mali,

@@ -210,27 +210,45 @@ def effective_inputs(atom, J, alo, pops_old):
     return Jeff, 1.0 - alo
 
 
-def rate_matrix_eff(atom, T, ne, J_eff, alo_c):
-    """Gamma [cell][i][j] from the effective intensity: rate j -> i per atom in j
-    (off-diagonal), diagonal from conservation.  J_eff, alo_c: [line*n_per_line][cell];
+def line_integrals(atom, T, J_eff, alo_c, lambda_begin=0):
+    """The two radiation integrals of each line's rates (Sec. 3.3) over the grid wavelengths
+    [lambda_begin, lambda_begin + len(J_eff)) (global indices, line after line):
+    Jbar = sum_k w phi J_eff and Lbar = sum_k w phi (1 - Lambda*), [line][2][cell], with phi
+    normalised over the whole line, so integrals over disjoint ranges add up to the line's.
     alo_c = None means Lambda* = 0."""
     T = np.asarray(T, dtype=np.float64).ravel()
     ncell = T.size
-    nlev = len(atom["E_eV"])
     npl = atom["n_per_line"]
     J_eff = np.asarray(J_eff, dtype=np.float64).reshape(-1, ncell)
+    cnt = J_eff.shape[0]
     alo_c = np.ones_like(J_eff) if alo_c is None else \
         np.asarray(alo_c, dtype=np.float64).reshape(-1, ncell)
     phis = profiles(atom, T)
     grids = frequency_grid(atom)
+    out = np.zeros((len(phis), 2, ncell))
+    for li, (phi, (nu, w)) in enumerate(zip(phis, grids)):
+        ks = [k for k in range(npl) if 0 <= li * npl + k - lambda_begin < cnt]
+        if not ks:
+            continue
+        rows = [li * npl + k - lambda_begin for k in ks]
+        wphi = w[ks, None] * phi[ks]
+        out[li, 0] = np.sum(wphi * J_eff[rows], axis=0)
+        out[li, 1] = np.sum(wphi * alo_c[rows], axis=0)
+    return out
+
+
+def rate_matrix_from_integrals(atom, T, ne, integrals):
+    """Gamma [cell][i][j] (rate j -> i per atom in j off the diagonal, diagonal from
+    conservation) from each line's Jbar and Lbar [line][2][cell]:
+    R_lu = B_lu Jbar, R_ul = A_ul Lbar + B_ul Jbar, plus the collisions."""
+    T = np.asarray(T, dtype=np.float64).ravel()
+    ncell = T.size
+    nlev = len(atom["E_eV"])
+    integrals = np.asarray(integrals, dtype=np.float64).reshape(-1, 2, ncell)
     coll = collision_rates(atom, T, ne)
     G = np.zeros((ncell, nlev, nlev))
-    for li, (L, phi, (nu, w), (Clu, Cul)) in enumerate(zip(line_constants(atom), phis, grids,
-                                                           coll)):
-        sl = slice(li * npl, (li + 1) * npl)
-        wphi = w[:, None] * phi
-        Jb = np.sum(wphi * J_eff[sl], axis=0)          # sum_k w phi (J - Lambda* S_dagger)
-        Lc = np.sum(wphi * alo_c[sl], axis=0)          # sum_k w phi (1 - Lambda*)
+    for li, (L, (Clu, Cul)) in enumerate(zip(line_constants(atom), coll)):
+        Jb, Lc = integrals[li, 0], integrals[li, 1]
         Rlu = L["Blu"] * Jb
         Rul = L["A"] * Lc + L["Bul"] * Jb
         G[:, L["up"], L["lo"]] += Rlu + Clu
@@ -238,6 +256,13 @@ def rate_matrix_eff(atom, T, ne, J_eff, alo_c):
     for i in range(nlev):
         G[:, i, i] = -np.sum(G[:, :, i], axis=1)
     return G
+
+
+def rate_matrix_eff(atom, T, ne, J_eff, alo_c):
+    """Gamma [cell][i][j] from the effective intensity: rate j -> i per atom in j
+    (off-diagonal), diagonal from conservation.  J_eff, alo_c: [line*n_per_line][cell];
+    alo_c = None means Lambda* = 0."""
+    return rate_matrix_from_integrals(atom, T, ne, line_integrals(atom, T, J_eff, alo_c))
 
 
 def rate_matrix(atom, T, ne, J, alo, pops_old):
@@ -263,6 +288,15 @@ def solve_populations(G, n_atom, pops_old):
 def stat_eq(atom, T, ne, n_atom, J, alo, pops_old):
     """New populations and the maximum relative change max |n_new - n_old| / n_new."""
     G = rate_matrix(atom, T, ne, J, alo, pops_old)
+    new = solve_populations(G, n_atom, pops_old)
+    old = np.asarray(pops_old, dtype=np.float64).reshape(new.shape)
+    rel = np.abs(new - old) / np.abs(new)
+    return new, float(np.max(rel))
+
+
+def stat_eq_integrals(atom, T, ne, n_atom, integrals, pops_old):
+    """stat_eq from each line's radiation integrals summed over all its wavelengths."""
+    G = rate_matrix_from_integrals(atom, T, ne, integrals)
     new = solve_populations(G, n_atom, pops_old)
     old = np.asarray(pops_old, dtype=np.float64).reshape(new.shape)
     rel = np.abs(new - old) / np.abs(new)

@@ -36,10 +36,11 @@
 #ifndef RCX_MIN_CTAS
 #define RCX_MIN_CTAS 6
 #endif
-// With 8 wavelengths per lane the prefetched voxel alone takes 16 registers: a 40-register
-// budget spills inside the march loop, so those instantiations get a budget of their own.
+// With 8 wavelengths per lane the field data in flight alone takes 16 registers: a 40-register
+// budget spills inside the march loop, so those instantiations get a budget of their own
+// (4 CTAs/SM: 676 slices/s at 1024^2 x 64, 565 at 5 CTAs/SM with spills, 803 with 4 per lane).
 #ifndef RCX_MIN_CTAS_VL8
-#define RCX_MIN_CTAS_VL8 3
+#define RCX_MIN_CTAS_VL8 4
 #endif
 // Cascade 0 for J alone (no operator outputs, dense): 4 CTAs/SM measured 0.98 ms per 1024^2
 // 64-wavelength step against 1.03 ms at 3.
@@ -270,6 +271,50 @@ __device__ __forceinline__ bool march_interval(const float2* __restrict__ F, int
     // After the last step that fetch is one voxel past the exit face (up to a row outside
     // the block); the packed field is allocated with a guard band of a row of voxels on
     // both sides, so it reads allocated memory, and the value is never used.
+    if constexpr (VL == 8 && !SPLIT_FIRST && !CONTRIB) {
+        // Eight wavelengths per lane in two halves of four: the next voxel's first half is
+        // fetched as soon as this voxel's first half has been integrated, and its second half
+        // after the second, so each half is prefetched about half a step ahead and only 16
+        // registers of field data are live (instead of 32 for a whole voxel ahead).
+        Voxel<4> lo, hi;
+        lo.load(F + off);
+        hi.load(F + off + 4);
+        for (int step = 0; step < max_steps; ++step) {
+            const bool stepx = tnx <= tnz;
+            const float tn = fminf(fminf(tnx, tnz), thi);
+            const float ds = tn - t;
+            const int off_next = off + (stepx ? dox : doz);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const float y = lo.v[j].x * ds;
+                const float e = exp2_neg(y);
+                const float om = one_minus_exp2_neg(y, e);
+                I[j] = fmaf(T[j] * lo.v[j].y, om, I[j]);
+                T[j] *= e;
+            }
+            lo.load(F + off_next);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const float y = hi.v[j].x * ds;
+                const float e = exp2_neg(y);
+                const float om = one_minus_exp2_neg(y, e);
+                I[4 + j] = fmaf(T[4 + j] * hi.v[j].y, om, I[4 + j]);
+                T[4 + j] *= e;
+            }
+            hi.load(F + off_next + 4);
+            if (tn >= thi) break;
+            if (stepx) {
+                kx += 1.0f;
+                tnx = fmaf(kx, dtx, tfx);
+            } else {
+                kz += 1.0f;
+                tnz = fmaf(kz, dtz, tfz);
+            }
+            off = off_next;
+            t = tn;
+        }
+        return true;
+    }
     Voxel<VL> cur;
     cur.load(F + off);
     for (int step = 0; step < max_steps; ++step) {
@@ -645,8 +690,12 @@ level_split_kernel(const LevelArgs A) {
 // store follow per pass.  Strip-split cascades (PHASE 1 first, 2 middle, 3 last strip; 0
 // unsplit) compose the pieces through it_state as level_split_kernel does.
 // ---------------------------------------------------------------------------
+// Two warps per CTA at 16 CTAs/SM (64 registers, 12 KB of shared memory per CTA).  Measured at
+// 1024^2 x 64 wavelengths: cascades 1 and 2 take 1.33 and 3.05 ms per step with 2-warp CTAs,
+// 1.46 and 3.24 with 8-warp CTAs, 1.56 and 3.49 in the lane-group march.
+constexpr int kSdWarps = 2;
 #ifndef RCX_MIN_CTAS_SD
-#define RCX_MIN_CTAS_SD 3
+#define RCX_MIN_CTAS_SD 16
 #endif
 constexpr int kSdSteps = 8;
 
@@ -733,19 +782,23 @@ __device__ __forceinline__ void cross_voxel(const Voxel<VL>& v, float ds, float 
     }
 }
 
-template <int LB, int VL, typename TS, bool HAS_UP, int PHASE>
-__global__ void __launch_bounds__(kWarpsPerCta * 32, RCX_MIN_CTAS_SD)
+template <int LB, int VL, typename TS, bool HAS_UP, int PHASE, int WPC>
+__global__ void __launch_bounds__(WPC * 32, RCX_MIN_CTAS_SD)
 level_sdda_kernel(const LevelArgs A) {
+    static_assert(VL == 4, "the replay keeps a lane's (I, T) as one float4 pair");
     constexpr int LPR = LB / VL;          // lanes per ray in the replay
     constexpr int RPP = 32 / LPR;         // rays per pass
     constexpr int NP = 32 / RPP;          // passes
     constexpr unsigned PASS_MASK = RPP >= 32 ? 0xffffffffu : ((1u << RPP) - 1u);
     constexpr bool SPLIT = PHASE != 0, FIRST = PHASE == 1, LAST = PHASE == 3;
-    __shared__ int2 sbuf[kWarpsPerCta][kSdSteps][32];
+    // per warp: the chunk's steps [step][ray] and the lanes' (I, T) of every pass, kept in
+    // shared memory between passes so that a lane holds one pass's state at a time
+    __shared__ int2 sbuf[WPC][kSdSteps][32];
+    __shared__ float4 sI[WPC][NP][32], sT[WPC][NP][32];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int g = lane / LPR, q = lane % LPR, lane_off = q * VL;
     const int lb = SPLIT ? A.split_lb + (int)blockIdx.y : (int)blockIdx.y;
-    const long long ray0 = ((long long)blockIdx.x * kWarpsPerCta + w) * 32;
+    const long long ray0 = ((long long)blockIdx.x * WPC + w) * 32;
     const float2* F = A.field + (size_t)lb * A.ncell * LB;
 
     // producer: the DDA of ray ray0 + lane
@@ -766,15 +819,11 @@ level_sdda_kernel(const LevelArgs A) {
         }
     }
     const unsigned hitmask = __ballot_sync(0xffffffffu, hit);
-
-    float I[NP][VL], T[NP][VL];
 #pragma unroll
-    for (int p = 0; p < NP; ++p)
-#pragma unroll
-        for (int j = 0; j < VL; ++j) {
-            I[p][j] = 0.0f;
-            T[p][j] = 1.0f;
-        }
+    for (int p = 0; p < NP; ++p) {
+        sI[w][p][lane] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        sT[w][p][lane] = make_float4(1.0f, 1.0f, 1.0f, 1.0f);
+    }
     const float2* Fl = F + lane_off;
     int2 (*buf)[32] = sbuf[w];
     unsigned live = __ballot_sync(0xffffffffu, walk.alive);
@@ -782,27 +831,29 @@ level_sdda_kernel(const LevelArgs A) {
 #pragma unroll
         for (int s = 0; s < kSdSteps; ++s) buf[s][lane] = walk.next();
         __syncwarp();
-#pragma unroll
+#pragma unroll 1
         for (int p = 0; p < NP; ++p) {
             if (!((live >> (p * RPP)) & PASS_MASK)) continue;   // warp-uniform
             const int rp = p * RPP + g;
-            int2 st = buf[0][rp];
-            Voxel<VL> cur;
-            cur.load(Fl + st.x);
+            float4 i4 = sI[w][p][lane], t4 = sT[w][p][lane];
+            float I[VL] = {i4.x, i4.y, i4.z, i4.w}, T[VL] = {t4.x, t4.y, t4.z, t4.w};
+            // two gathers ahead: steps s + 1 and s + 2 are in flight while s is integrated
+            int2 st[kSdSteps];
+#pragma unroll
+            for (int s = 0; s < kSdSteps; ++s) st[s] = buf[s][rp];
+            Voxel<VL> v0, v1;
+            v0.load(Fl + st[0].x);
+            v1.load(Fl + st[1].x);
 #pragma unroll
             for (int s = 0; s < kSdSteps; ++s) {
-                Voxel<VL> nxt;
-                int2 stn;
-                if (s + 1 < kSdSteps) {
-                    stn = buf[s + 1][rp];
-                    nxt.load(Fl + stn.x);
-                }
-                cross_voxel<VL>(cur, __int_as_float(st.y), I[p], T[p]);
-                if (s + 1 < kSdSteps) {
-                    cur = nxt;
-                    st = stn;
-                }
+                Voxel<VL> v2;
+                if (s + 2 < kSdSteps) v2.load(Fl + st[s + 2].x);
+                cross_voxel<VL>(v0, __int_as_float(st[s].y), I, T);
+                v0 = v1;
+                if (s + 2 < kSdSteps) v1 = v2;
             }
+            sI[w][p][lane] = make_float4(I[0], I[1], I[2], I[3]);
+            sT[w][p][lane] = make_float4(T[0], T[1], T[2], T[3]);
         }
         __syncwarp();
         live = __ballot_sync(0xffffffffu, walk.alive);
@@ -821,8 +872,8 @@ level_sdda_kernel(const LevelArgs A) {
             const int k = (int)(ray & (A.W - 1));
             int px, pz;
             grid_xy(ray >> A.Wshift, A.Px, px, pz);
-            float* Ip = I[p];
-            float* Tp = T[p];
+            const float4 i4 = sI[w][p][lane], t4 = sT[w][p][lane];
+            float Ip[VL] = {i4.x, i4.y, i4.z, i4.w}, Tp[VL] = {t4.x, t4.y, t4.z, t4.w};
             bool merge = !SPLIT;
             if constexpr (SPLIT) {
                 float2* st = A.it_state + ((size_t)blockIdx.y * A.rays + ray) * LB + lane_off;
@@ -1398,45 +1449,48 @@ cudaError_t launch_batched_pack(int LB, const BatchPackArgs& b, int grid, cudaSt
     return cudaGetLastError();
 }
 
-template <int LB, typename TS, bool FAST>
+template <int LB, int VL, typename TS, bool FAST>
 static cudaError_t split_phase(bool has_up, const LevelArgs& a, dim3 grid, cudaStream_t s) {
     const dim3 block(kWarpsPerCta * 32);
     const bool first = a.phase == 0, last = a.phase == a.n_strips - 1;
     if (has_up) {
-        if (first) level_split_kernel<LB, 4, TS, true, true, false, FAST><<<grid, block, 0, s>>>(a);
-        else if (last) level_split_kernel<LB, 4, TS, true, false, true, FAST><<<grid, block, 0, s>>>(a);
-        else level_split_kernel<LB, 4, TS, true, false, false, FAST><<<grid, block, 0, s>>>(a);
+        if (first) level_split_kernel<LB, VL, TS, true, true, false, FAST><<<grid, block, 0, s>>>(a);
+        else if (last) level_split_kernel<LB, VL, TS, true, false, true, FAST><<<grid, block, 0, s>>>(a);
+        else level_split_kernel<LB, VL, TS, true, false, false, FAST><<<grid, block, 0, s>>>(a);
     } else {
-        if (first) level_split_kernel<LB, 4, TS, false, true, false, FAST><<<grid, block, 0, s>>>(a);
-        else if (last) level_split_kernel<LB, 4, TS, false, false, true, FAST><<<grid, block, 0, s>>>(a);
-        else level_split_kernel<LB, 4, TS, false, false, false, FAST><<<grid, block, 0, s>>>(a);
+        if (first) level_split_kernel<LB, VL, TS, false, true, false, FAST><<<grid, block, 0, s>>>(a);
+        else if (last) level_split_kernel<LB, VL, TS, false, false, true, FAST><<<grid, block, 0, s>>>(a);
+        else level_split_kernel<LB, VL, TS, false, false, false, FAST><<<grid, block, 0, s>>>(a);
     }
     return cudaGetLastError();
 }
 
-template <int LB, typename TS>
+template <int LB, int VL, typename TS>
 static cudaError_t level_split_t(bool has_up, const LevelArgs& a, cudaStream_t s) {
-    constexpr int G = 32 / (LB / 4);
+    constexpr int G = 32 / (LB / VL);
     if (a.rays == 0) return cudaSuccess;
     const long long per_cta = (long long)G * kWarpsPerCta;
     const dim3 grid((unsigned)((a.rays + per_cta - 1) / per_cta), (unsigned)a.split_nblk);
     const bool fast = a.Wshift >= 0 && !a.probe_list;
-    if (fast) return split_phase<LB, TS, true>(has_up, a, grid, s);
-    return split_phase<LB, TS, false>(has_up, a, grid, s);
+    if (fast) return split_phase<LB, VL, TS, true>(has_up, a, grid, s);
+    return split_phase<LB, VL, TS, false>(has_up, a, grid, s);
 }
 
-template <int LB>
+template <int LB, int VL>
 static cudaError_t level_split_p(int precision, bool has_up, const LevelArgs& a, cudaStream_t s) {
     switch (precision) {
-        case RC_STORE_F32: return level_split_t<LB, float>(has_up, a, s);
-        case RC_STORE_F16: return level_split_t<LB, __half>(has_up, a, s);
-        case RC_STORE_BF16: return level_split_t<LB, __nv_bfloat16>(has_up, a, s);
+        case RC_STORE_F32: return level_split_t<LB, VL, float>(has_up, a, s);
+        case RC_STORE_F16: return level_split_t<LB, VL, __half>(has_up, a, s);
+        case RC_STORE_BF16: return level_split_t<LB, VL, __nv_bfloat16>(has_up, a, s);
     }
     return cudaErrorInvalidValue;
 }
 
-// The split march is instantiated for 4 wavelengths per lane and 8-32 per ray.
-bool level_split_supported(int LB, int VL) { return VL == 4 && (LB == 8 || LB == 16 || LB == 32); }
+// The split march is instantiated for 4 wavelengths per lane and 8-32 per ray, and for 8
+// per lane and 16 per ray.
+bool level_split_supported(int LB, int VL) {
+    return (VL == 4 && (LB == 8 || LB == 16 || LB == 32)) || (VL == 8 && LB == 16);
+}
 
 cudaError_t launch_level_split(int LB, int VL, int precision, bool has_up, const LevelArgs& a,
                                cudaStream_t s) {
@@ -1447,23 +1501,29 @@ cudaError_t launch_level_split(int LB, int VL, int precision, bool has_up, const
     b.split_nblk = std::max(1, a.split_nblk);
     b.strip_x0 = (int)((long long)a.phase * a.nx / a.n_strips);
     b.strip_x1 = (int)((long long)(a.phase + 1) * a.nx / a.n_strips);
+    if (VL == 8) return level_split_p<16, 8>(precision, has_up, b, s);
     switch (LB) {
-        case 8: return level_split_p<8>(precision, has_up, b, s);
-        case 16: return level_split_p<16>(precision, has_up, b, s);
-        case 32: return level_split_p<32>(precision, has_up, b, s);
+        case 8: return level_split_p<8, 4>(precision, has_up, b, s);
+        case 16: return level_split_p<16, 4>(precision, has_up, b, s);
+        case 32: return level_split_p<32, 4>(precision, has_up, b, s);
     }
     return cudaErrorInvalidValue;
+}
+
+template <int LB, int VL, typename TS, int PHASE, int WPC>
+static cudaError_t sdda_w(bool has_up, const LevelArgs& a, unsigned nblk, cudaStream_t s) {
+    const long long per_cta = 32LL * WPC;
+    const dim3 grid((unsigned)((a.rays + per_cta - 1) / per_cta), nblk);
+    const dim3 block(WPC * 32);
+    if (has_up) level_sdda_kernel<LB, VL, TS, true, PHASE, WPC><<<grid, block, 0, s>>>(a);
+    else level_sdda_kernel<LB, VL, TS, false, PHASE, WPC><<<grid, block, 0, s>>>(a);
+    return cudaGetLastError();
 }
 
 template <int LB, int VL, typename TS, int PHASE>
 static cudaError_t sdda_t(bool has_up, const LevelArgs& a, unsigned nblk, cudaStream_t s) {
     if (a.rays == 0) return cudaSuccess;
-    const long long per_cta = 32LL * kWarpsPerCta;
-    const dim3 grid((unsigned)((a.rays + per_cta - 1) / per_cta), nblk);
-    const dim3 block(kWarpsPerCta * 32);
-    if (has_up) level_sdda_kernel<LB, VL, TS, true, PHASE><<<grid, block, 0, s>>>(a);
-    else level_sdda_kernel<LB, VL, TS, false, PHASE><<<grid, block, 0, s>>>(a);
-    return cudaGetLastError();
+    return sdda_w<LB, VL, TS, PHASE, kSdWarps>(has_up, a, nblk, s);
 }
 
 template <int LB, int VL, typename TS>

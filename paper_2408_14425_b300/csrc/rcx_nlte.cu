@@ -152,7 +152,126 @@ __global__ void emis_opac_kernel(AtomDev A, const double* __restrict__ T,
     }
 }
 
-// Gamma n = 0 per cell (Eq. 20) with MALI rates; FP64 throughout.
+// Gamma n = 0 for cell c (Eq. 20) from the per-line integrals Jb[li] = sum_k w phi J_eff and
+// Lc[li] = sum_k w phi (1 - Lambda*) (MALI rates, Sec. 3.3) and the collisions; the most
+// populated level's row replaced by sum n = n_atom; FP64 throughout.  Writes the new
+// populations and returns max |n_new - n_old| / n_new (infinite for a NaN).
+__device__ double solve_cell(const AtomDev& A, long long c, long long ncell, double t, double nec,
+                             double na, const double* Jb, const double* Lc,
+                             double* __restrict__ pops) {
+    const int n = A.n_levels;
+    const double sqT = sqrt(t);
+    double G[kMaxLevels][kMaxLevels];
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) G[i][j] = 0.0;
+    for (int li = 0; li < A.n_lines; ++li) {
+        const LineConst& L = A.line[li];
+        const double Rlu = L.Blu * Jb[li];
+        const double Rul = L.A * Lc[li] + L.Bul * Jb[li];
+        const double y = L.y_T / t;
+        const double Clu = nec * L.coll * van_regemorter_p(y) / sqT * exp(-y);
+        const double Cul = Clu * L.glo_gup * exp(y);
+        G[L.up][L.lo] += Rlu + Clu;                  // lo -> up, per atom in lo
+        G[L.lo][L.up] += Rul + Cul;                  // up -> lo, per atom in up
+    }
+    double old[kMaxLevels];
+    int r = 0;
+    for (int i = 0; i < n; ++i) {
+        old[i] = pops[(size_t)i * ncell + c];
+        if (old[i] > old[r]) r = i;
+    }
+    for (int j = 0; j < n; ++j) {
+        double s = 0.0;
+        for (int i = 0; i < n; ++i)
+            if (i != j) s += G[i][j];
+        G[j][j] = -s;
+    }
+    double b[kMaxLevels];
+    for (int i = 0; i < n; ++i) b[i] = 0.0;
+    for (int j = 0; j < n; ++j) G[r][j] = 1.0;       // particle conservation
+    b[r] = na;
+    // Gaussian elimination with partial pivoting
+    for (int col = 0; col < n; ++col) {
+        int p = col;
+        for (int i = col + 1; i < n; ++i)
+            if (fabs(G[i][col]) > fabs(G[p][col])) p = i;
+        if (p != col) {
+            for (int j = 0; j < n; ++j) {
+                const double tmp = G[col][j];
+                G[col][j] = G[p][j];
+                G[p][j] = tmp;
+            }
+            const double tb = b[col];
+            b[col] = b[p];
+            b[p] = tb;
+        }
+        const double inv = 1.0 / G[col][col];
+        for (int i = col + 1; i < n; ++i) {
+            const double f = G[i][col] * inv;
+            if (f == 0.0) continue;
+            for (int j = col; j < n; ++j) G[i][j] -= f * G[col][j];
+            b[i] -= f * b[col];
+        }
+    }
+    double x[kMaxLevels];
+    for (int i = n - 1; i >= 0; --i) {
+        double s = b[i];
+        for (int j = i + 1; j < n; ++j) s -= G[i][j] * x[j];
+        x[i] = s / G[i][i];
+    }
+    double rel = 0.0;
+    for (int i = 0; i < n; ++i) {
+        pops[(size_t)i * ncell + c] = x[i];
+        const double d = fabs(x[i] - old[i]) / fabs(x[i]);
+        rel = (d == d) ? fmax(rel, d) : INFINITY;    // NaN -> infinite change
+    }
+    return rel;
+}
+
+// block max of a non-negative double -> one atomic per block (non-negative doubles order like
+// their bits)
+__device__ __forceinline__ void block_max_to(double rel, unsigned long long* dmax_bits) {
+    __shared__ double red[256];
+    red[threadIdx.x] = rel;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if ((int)threadIdx.x < s) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + s]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0 && dmax_bits)
+        atomicMax(dmax_bits, (unsigned long long)__double_as_longlong(red[0]));
+}
+
+// The line integrals of cell c over the grid wavelengths [lam_begin, lam_begin + lam_count) of
+// every line (J_eff, alo_c hold those wavelengths only, [lam - lam_begin][cell]); the profile
+// is normalised over the whole line, so integrals over disjoint wavelength ranges add up to the
+// integral over the line.  alo_c NULL means Lambda* = 0.
+__device__ __forceinline__ void line_integrals_cell(const AtomDev& A, long long c, long long ncell,
+                                                    double t, const float* __restrict__ Jeff,
+                                                    const float* __restrict__ aloc, int lam_begin,
+                                                    int lam_count, double* Jb, double* Lc) {
+    const double sqT = sqrt(t);
+    for (int li = 0; li < A.n_lines; ++li) {
+        const LineConst& L = A.line[li];
+        const double h = L.ddnu / (L.dop * sqT);
+        const double* w = A.w + (size_t)li * A.n_per_line;
+        double norm = 0.0, sj = 0.0, sl = 0.0;
+        for_each_gauss(A.n_per_line, h, [&](int k, double g) {
+            const double wp = w[k] * g;
+            norm += wp;
+            const int lam = L.lam0 + k - lam_begin;
+            if (lam >= 0 && lam < lam_count) {
+                const size_t o = (size_t)lam * ncell + c;
+                sj += wp * (double)Jeff[o];
+                sl += aloc ? wp * (double)aloc[o] : wp;
+            }
+        });
+        Jb[li] = sj / norm;                 // sum_k w phi J_eff
+        Lc[li] = sl / norm;                 // sum_k w phi (1 - Lambda*)
+    }
+}
+
+// Gamma n = 0 per cell (Eq. 20) with MALI rates from J_eff and 1 - Lambda* of every wavelength.
 __global__ void stat_eq_kernel(AtomDev A, const double* __restrict__ T,
                                const double* __restrict__ ne, const double* __restrict__ n_atom,
                                const float* __restrict__ Jeff, const float* __restrict__ aloc,
@@ -163,94 +282,47 @@ __global__ void stat_eq_kernel(AtomDev A, const double* __restrict__ T,
     double rel = 0.0;
     // cells outside a sparse plan's active set (Sec. 3.5) keep their populations
     if (c < ncell && (!active || active[c])) {
-        const int n = A.n_levels;
-        const double t = T[c], sqT = sqrt(t), nec = ne[c];
-        double G[kMaxLevels][kMaxLevels];
-        for (int i = 0; i < n; ++i)
-            for (int j = 0; j < n; ++j) G[i][j] = 0.0;
+        double Jb[kMaxLines], Lc[kMaxLines];
+        line_integrals_cell(A, c, ncell, T[c], Jeff, aloc, 0, 1 << 30, Jb, Lc);
+        rel = solve_cell(A, c, ncell, T[c], ne[c], n_atom[c], Jb, Lc, pops);
+    }
+    block_max_to(rel, dmax_bits);
+}
+
+// Partial line integrals over a range of the atom's wavelengths: out [line][2][cell] =
+// (sum_k w phi J_eff, sum_k w phi (1 - Lambda*)) over the range's grid points.
+__global__ void line_integrals_kernel(AtomDev A, const double* __restrict__ T,
+                                      const float* __restrict__ Jeff, const float* __restrict__ aloc,
+                                      int lam_begin, int lam_count, long long ncell,
+                                      double* __restrict__ out) {
+    const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= ncell) return;
+    double Jb[kMaxLines], Lc[kMaxLines];
+    line_integrals_cell(A, c, ncell, T[c], Jeff, aloc, lam_begin, lam_count, Jb, Lc);
+    for (int li = 0; li < A.n_lines; ++li) {
+        out[(size_t)(2 * li) * ncell + c] = Jb[li];
+        out[(size_t)(2 * li + 1) * ncell + c] = Lc[li];
+    }
+}
+
+// Gamma n = 0 per cell from line integrals summed over every wavelength of every line.
+__global__ void stat_eq_integrals_kernel(AtomDev A, const double* __restrict__ T,
+                                         const double* __restrict__ ne,
+                                         const double* __restrict__ n_atom,
+                                         const double* __restrict__ integ, long long ncell,
+                                         double* __restrict__ pops,
+                                         unsigned long long* __restrict__ dmax_bits) {
+    const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    double rel = 0.0;
+    if (c < ncell) {
+        double Jb[kMaxLines], Lc[kMaxLines];
         for (int li = 0; li < A.n_lines; ++li) {
-            const LineConst& L = A.line[li];
-            const double h = L.ddnu / (L.dop * sqT);
-            const double* w = A.w + (size_t)li * A.n_per_line;
-            double norm = 0.0, sj = 0.0, sl = 0.0;
-            for_each_gauss(A.n_per_line, h, [&](int k, double g) {
-                const double wp = w[k] * g;
-                const size_t o = (size_t)(L.lam0 + k) * ncell + c;
-                norm += wp;
-                sj += wp * (double)Jeff[o];
-                if (aloc) sl += wp * (double)aloc[o];
-            });
-            const double Jb = sj / norm;                 // sum_k w phi J_eff
-            const double Lc = aloc ? sl / norm : 1.0;    // sum_k w phi (1 - Lambda*)
-            const double Rlu = L.Blu * Jb;
-            const double Rul = L.A * Lc + L.Bul * Jb;
-            const double y = L.y_T / t;
-            const double Clu = nec * L.coll * van_regemorter_p(y) / sqT * exp(-y);
-            const double Cul = Clu * L.glo_gup * exp(y);
-            G[L.up][L.lo] += Rlu + Clu;                  // lo -> up, per atom in lo
-            G[L.lo][L.up] += Rul + Cul;                  // up -> lo, per atom in up
+            Jb[li] = integ[(size_t)(2 * li) * ncell + c];
+            Lc[li] = integ[(size_t)(2 * li + 1) * ncell + c];
         }
-        double old[kMaxLevels];
-        int r = 0;
-        for (int i = 0; i < n; ++i) {
-            old[i] = pops[(size_t)i * ncell + c];
-            if (old[i] > old[r]) r = i;
-        }
-        for (int j = 0; j < n; ++j) {
-            double s = 0.0;
-            for (int i = 0; i < n; ++i)
-                if (i != j) s += G[i][j];
-            G[j][j] = -s;
-        }
-        double b[kMaxLevels];
-        for (int i = 0; i < n; ++i) b[i] = 0.0;
-        for (int j = 0; j < n; ++j) G[r][j] = 1.0;       // particle conservation
-        b[r] = n_atom[c];
-        // Gaussian elimination with partial pivoting
-        for (int col = 0; col < n; ++col) {
-            int p = col;
-            for (int i = col + 1; i < n; ++i)
-                if (fabs(G[i][col]) > fabs(G[p][col])) p = i;
-            if (p != col) {
-                for (int j = 0; j < n; ++j) {
-                    const double tmp = G[col][j];
-                    G[col][j] = G[p][j];
-                    G[p][j] = tmp;
-                }
-                const double tb = b[col];
-                b[col] = b[p];
-                b[p] = tb;
-            }
-            const double inv = 1.0 / G[col][col];
-            for (int i = col + 1; i < n; ++i) {
-                const double f = G[i][col] * inv;
-                if (f == 0.0) continue;
-                for (int j = col; j < n; ++j) G[i][j] -= f * G[col][j];
-                b[i] -= f * b[col];
-            }
-        }
-        double x[kMaxLevels];
-        for (int i = n - 1; i >= 0; --i) {
-            double s = b[i];
-            for (int j = i + 1; j < n; ++j) s -= G[i][j] * x[j];
-            x[i] = s / G[i][i];
-        }
-        for (int i = 0; i < n; ++i) {
-            pops[(size_t)i * ncell + c] = x[i];
-            const double d = fabs(x[i] - old[i]) / fabs(x[i]);
-            rel = (d == d) ? fmax(rel, d) : INFINITY;    // NaN -> infinite change
-        }
+        rel = solve_cell(A, c, ncell, T[c], ne[c], n_atom[c], Jb, Lc, pops);
     }
-    // block max -> one atomic per block (non-negative doubles order like their bits)
-    __shared__ double red[256];
-    red[threadIdx.x] = rel;
-    __syncthreads();
-    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-        if ((int)threadIdx.x < s) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + s]);
-        __syncthreads();
-    }
-    if (threadIdx.x == 0 && dmax_bits)
-        atomicMax(dmax_bits, (unsigned long long)__double_as_longlong(red[0]));
+    block_max_to(rel, dmax_bits);
 }
 
 }  // namespace
@@ -446,6 +518,41 @@ rc_status rc_stat_eq(rc_atom_t a, const double* T, const double* ne, const doubl
     cudaStream_t s = (cudaStream_t)stream;
     rc_status st = launch_stat_eq(a, T, ne, n_atom, J_eff, alo_c, ncell, pops, s);
     if (st != RC_OK || !max_rel_change) return st;
+    return read_dmax(a, s, max_rel_change);
+}
+
+rc_status rc_line_integrals(rc_atom_t a, const double* T, const float* J_eff, const float* alo_c,
+                            int lambda_begin, int lambda_count, long long ncell, double* out,
+                            void* stream) {
+    rcx::set_last_error("");
+    if (!a || !T || !J_eff || !out || ncell < 0 || lambda_begin < 0 || lambda_count < 0 ||
+        lambda_begin + lambda_count > a->n_lambda)
+        return nfail(RC_ERR_ARG, "rc_line_integrals: NULL argument or wavelength range outside "
+                                 "the atom's grid");
+    if (ncell == 0) return RC_OK;
+    line_integrals_kernel<<<(unsigned)((ncell + 127) / 128), 128, 0, (cudaStream_t)stream>>>(
+        a->dev, T, J_eff, alo_c, lambda_begin, lambda_count, ncell, out);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? RC_OK : ncuda(e, "rc_line_integrals launch");
+}
+
+rc_status rc_stat_eq_integrals(rc_atom_t a, const double* T, const double* ne,
+                               const double* n_atom, const double* integrals, long long ncell,
+                               double* pops, double* max_rel_change, void* stream) {
+    rcx::set_last_error("");
+    if (!a || !T || !ne || !n_atom || !integrals || !pops || ncell < 0)
+        return nfail(RC_ERR_ARG, "rc_stat_eq_integrals: NULL argument or negative ncell");
+    if (ncell == 0) {
+        if (max_rel_change) *max_rel_change = 0.0;
+        return RC_OK;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = cudaMemsetAsync(a->d_dmax, 0, sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return ncuda(e, "rc_stat_eq_integrals");
+    stat_eq_integrals_kernel<<<(unsigned)((ncell + 255) / 256), 256, 0, s>>>(
+        a->dev, T, ne, n_atom, integrals, ncell, pops, a->d_dmax);
+    if ((e = cudaGetLastError()) != cudaSuccess) return ncuda(e, "rc_stat_eq_integrals launch");
+    if (!max_rel_change) return RC_OK;
     return read_dmax(a, s, max_rel_change);
 }
 

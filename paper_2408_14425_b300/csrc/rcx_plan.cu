@@ -149,6 +149,21 @@ double far_corner(const rc_plan_s* p, int i) {
 // strips; 1408^2 42.0 -> 31.3 ms with 4; 1984^2 150 -> 90 ms with 8); shorter cascades lose
 // more to the extra launches and the (I, T) traffic than they gain.  rc_options.strips >= 2
 // forces a count on every cascade >= 1.
+// Cascades >= 1 whose intervals are at most this long (voxels) take the shared-DDA march by
+// default: their rays are short, and one DDA walk per 32 rays beats the lane-group march
+// (1024^2 x 64 wavelengths: cascade 1, 4 voxels, 1.33 vs 1.56 ms; cascade 2, 16 voxels, 3.05
+// vs 3.49 ms).  Longer cascades keep the lane-group march: there the shared DDA's 32 rays in
+// flight per warp cost more L2 hits and memory parallelism than its 14-20 % fewer
+// instructions save (cascade 3 9.81 vs 9.61 ms, cascade 4 38.9 vs 29.6 ms).
+constexpr double kSdMaxInterval = 16.0;
+
+bool use_shared_dda(const rc_plan_s* p, int i, const rcx::LevelArgs& a) {
+    if (i == 0 || p->march == RC_MARCH_LANE_GROUP || !rcx::level_sdda_supported(p->LB, p->VL, a))
+        return false;
+    if (p->march == RC_MARCH_SHARED_DDA_ALL) return true;
+    return p->lv[i].b - p->lv[i].a <= kSdMaxInterval;
+}
+
 int strips_for_impl(const rc_plan_s* p, int i) {
     if (i == 0 || p->opt.bilinear_fix || p->opt.strips == 1 ||
         !rcx::level_split_supported(p->LB, p->VL))
@@ -320,8 +335,7 @@ rc_status solve_device(rc_plan_s* p, const float* chi, const float* eta, int n_l
         rcx::LevelArgs a = rcx::level_args(p, i, n_lambda, Jv, alov, Jeffv, alocv);
         const bool has_up = i < live - 1;
         const int S = strips_for_impl(p, i);
-        const bool sdda = i > 0 && p->march == RC_MARCH_SHARED_DDA &&
-                          rcx::level_sdda_supported(LB, p->VL, a);
+        const bool sdda = use_shared_dda(p, i, a);
         if (S > 1) {
             // one launch per strip, over as many wavelength blocks as it_state holds
             const size_t per_blk = (size_t)a.rays * LB * sizeof(float2);
@@ -753,9 +767,10 @@ rc_status rc_plan_set_lane_layout(rc_plan_t p, int lambda_block, int lambda_per_
 rc_status rc_plan_set_march(rc_plan_t p, int mode) {
     g_last_error.clear();
     if (!p) return fail(RC_ERR_ARG, "rc_plan_set_march: plan is NULL");
-    if (mode != RC_MARCH_LANE_GROUP && mode != RC_MARCH_SHARED_DDA)
-        return fail(RC_ERR_ARG, "rc_plan_set_march: mode must be RC_MARCH_LANE_GROUP or "
-                                "RC_MARCH_SHARED_DDA");
+    if (mode != RC_MARCH_LANE_GROUP && mode != RC_MARCH_SHARED_DDA &&
+        mode != RC_MARCH_SHARED_DDA_ALL)
+        return fail(RC_ERR_ARG, "rc_plan_set_march: mode must be RC_MARCH_LANE_GROUP, "
+                                "RC_MARCH_SHARED_DDA or RC_MARCH_SHARED_DDA_ALL");
     p->march = mode;
     return RC_OK;
 }

@@ -28,7 +28,7 @@ EXPORTS = [
     "rc_plan_launch_times", "rc_plan_launch_name", "rc_formal_solve_noalloc",
     "rc_formal_solve_mali", "rc_atom_create", "rc_atom_destroy", "rc_atom_n_lambda", "rc_lte",
     "rc_emis_opac", "rc_stat_eq", "rc_nlte_solve", "rc_plan_set_lane_layout",
-    "rc_plan_set_march", "rc_plan_get_march",
+    "rc_plan_set_march", "rc_plan_get_march", "rc_line_integrals", "rc_stat_eq_integrals",
     "rc_plan_get_lane_layout", "rc_plan_autotune", "rc_batch_create", "rc_batch_run",
     "rc_batch_info", "rc_batch_destroy", "rc_formal_solve_batched", "rc_mlp_create",
     "rc_mlp_destroy", "rc_mlp_n_params", "rc_mlp_set_params", "rc_mlp_get_params",
@@ -128,6 +128,12 @@ def load():
     L.rc_stat_eq.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp, ctypes.c_longlong, _vp,
                              ctypes.POINTER(ctypes.c_double), _vp]
     L.rc_stat_eq.restype = ctypes.c_int
+    L.rc_line_integrals.argtypes = [_vp, _vp, _vp, _vp, ctypes.c_int, ctypes.c_int,
+                                    ctypes.c_longlong, _vp, _vp]
+    L.rc_line_integrals.restype = ctypes.c_int
+    L.rc_stat_eq_integrals.argtypes = [_vp, _vp, _vp, _vp, _vp, ctypes.c_longlong, _vp,
+                                       ctypes.POINTER(ctypes.c_double), _vp]
+    L.rc_stat_eq_integrals.restype = ctypes.c_int
     L.rc_nlte_solve.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp, ctypes.c_double, ctypes.c_int,
                                 ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double),
                                 ctypes.POINTER(ctypes.c_double), _vp]
@@ -342,10 +348,11 @@ class Plan:
         check(load().rc_plan_get_lane_layout(self._h, ctypes.byref(a), ctypes.byref(b)))
         return a.value, b.value
 
-    MARCH_LANE_GROUP, MARCH_SHARED_DDA = 0, 1
+    MARCH_LANE_GROUP, MARCH_SHARED_DDA, MARCH_SHARED_DDA_ALL = 0, 1, 2
 
     def set_march(self, mode: int):
-        """rc_plan_set_march: 0 lane-group DDA, 1 shared DDA (default where it applies)."""
+        """rc_plan_set_march: 0 lane-group DDA everywhere, 1 shared DDA on the short cascades
+        (default), 2 shared DDA on every cascade >= 1 where it applies."""
         check(load().rc_plan_set_march(self._h, int(mode)))
 
     def march(self) -> int:
@@ -464,6 +471,7 @@ class Atom:
         self._h = h
         self.n_levels = len(desc["E_eV"])
         self.n_lambda = L.rc_atom_n_lambda(h)
+        self.n_per_line = int(desc["n_per_line"])
 
     def close(self):
         if getattr(self, "_h", None):
@@ -511,6 +519,38 @@ class Atom:
             _dev_ptr(n_atom.reshape(-1), "n_atom", (n,), "float64"),
             _dev_ptr(J_eff.reshape(shp), "J_eff", shp),
             _dev_ptr(alo_c.reshape(shp), "alo_c", shp) if alo_c is not None else None, n,
+            _dev_ptr(pops, "pops", (self.n_levels, n), "float64"), ctypes.byref(ch),
+            _stream_ptr(stream)))
+        return ch.value
+
+    def line_integrals(self, T, J_eff, alo_c, lambda_begin: int, stream=None):
+        """rc_line_integrals: (Jeff_bar, (1 - Lambda*)_bar) per line over the grid wavelengths
+        [lambda_begin, lambda_begin + J_eff.shape[0]); device FP64 [n_lines][2][ncell]."""
+        import torch
+        n = T.numel()
+        cnt = int(J_eff.shape[0])
+        n_lines = self.n_lambda // self.n_per_line
+        out = torch.empty((n_lines, 2, n), dtype=torch.float64, device=T.device)
+        shp = (cnt, n)
+        check(load().rc_line_integrals(
+            self._h, _dev_ptr(T.reshape(-1), "T", (n,), "float64"),
+            _dev_ptr(J_eff.reshape(shp), "J_eff", shp),
+            _dev_ptr(alo_c.reshape(shp), "alo_c", shp) if alo_c is not None else None,
+            int(lambda_begin), cnt, n, _dev_ptr(out, "out", out.shape, "float64"),
+            _stream_ptr(stream)))
+        return out
+
+    def stat_eq_integrals(self, T, ne, n_atom, integrals, pops, stream=None):
+        """rc_stat_eq_integrals: updates pops in place from summed line integrals; returns the
+        max relative change."""
+        n = T.numel()
+        ch = ctypes.c_double()
+        n_lines = self.n_lambda // self.n_per_line
+        check(load().rc_stat_eq_integrals(
+            self._h, _dev_ptr(T.reshape(-1), "T", (n,), "float64"),
+            _dev_ptr(ne.reshape(-1), "ne", (n,), "float64"),
+            _dev_ptr(n_atom.reshape(-1), "n_atom", (n,), "float64"),
+            _dev_ptr(integrals, "integrals", (n_lines, 2, n), "float64"), n,
             _dev_ptr(pops, "pops", (self.n_levels, n), "float64"), ctypes.byref(ch),
             _stream_ptr(stream)))
         return ch.value

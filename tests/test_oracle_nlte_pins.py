@@ -306,3 +306,24 @@ def test_mali_and_lambda_iteration_share_the_fixed_point():
     assert h_mali[-1] < 1e-9 and h_lam[-1] < 1e-9
     np.testing.assert_allclose(p_mali, p_lam, rtol=1e-6)
     assert len(h_mali) * 4 < len(h_lam)
+
+
+def test_line_integrals_over_disjoint_ranges_add_up():
+    """The rates see the radiation field only through each line's two integrals; with the
+    profile normalised over the whole line, the integrals over disjoint wavelength ranges
+    (the split between processes) add up to the line's, and the rate matrix built from them
+    equals the one built from all wavelengths at once."""
+    rng = np.random.default_rng(9)
+    T = rng.uniform(6000, 3e4, 25)
+    nH = 10 ** rng.uniform(15, 18, 25)
+    ne, _ = nlte.saha_hydrogen(T, nH)
+    J = _planck_J(T) * rng.uniform(0.2, 2.0, (63, 25))
+    aloc = rng.uniform(0, 1, (63, 25))
+    full = nlte.line_integrals(ATOM, T, J, aloc)
+    parts = sum(nlte.line_integrals(ATOM, T, J[a:b], aloc[a:b], a)
+                for a, b in [(0, 17), (17, 40), (40, 63)])
+    np.testing.assert_allclose(parts, full, rtol=1e-14)
+    np.testing.assert_allclose(nlte.rate_matrix_from_integrals(ATOM, T, ne, parts),
+                               nlte.rate_matrix_eff(ATOM, T, ne, J, aloc), rtol=1e-13)
+    # Lambda* = 0: the second integral is the profile's integral, 1
+    np.testing.assert_allclose(nlte.line_integrals(ATOM, T, J, None)[:, 1], 1.0, rtol=1e-14)

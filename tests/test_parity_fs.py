@@ -416,12 +416,14 @@ def test_shared_dda_march_equals_lane_group_march(nx, nz, C, strips, prec, nl):
     eta = (chi * 10 ** rng.uniform(-1, 1, chi.shape)).astype(np.float32)
     dchi, deta = torch.from_numpy(chi).cuda(), torch.from_numpy(eta).cuda()
     out = []
-    for mode in (rcx.Plan.MARCH_LANE_GROUP, rcx.Plan.MARCH_SHARED_DDA):
+    for mode in (rcx.Plan.MARCH_LANE_GROUP, rcx.Plan.MARCH_SHARED_DDA,
+                 rcx.Plan.MARCH_SHARED_DDA_ALL):
         p = rcx.Plan(nx, nz, C, precision=prec, strips=strips)
         p.set_march(mode)
         assert p.march() == mode
         J, Jeff, aloc = p.formal_solve_mali(dchi, deta)
         out.append((J.cpu(), Jeff.cpu(), aloc.cpu()))
         p.close()
-    for a, b in zip(*out):
-        assert torch.equal(a, b), f"max abs diff {(a - b).abs().max().item():.3e}"
+    for other in out[1:]:
+        for a, b in zip(out[0], other):
+            assert torch.equal(a, b), f"max abs diff {(a - b).abs().max().item():.3e}"

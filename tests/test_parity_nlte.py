@@ -249,3 +249,55 @@ def test_c3_full_size_J_in_si_units():
         bad = np.abs(J[lam] - ref) > 1e-3 * np.abs(ref) + floor
         assert not bad.any(), f"lambda {lam}: {bad.sum()} cells off, max rel " \
                               f"{(np.abs(J[lam] - ref) / np.abs(ref)).max():.2e}"
+
+
+def test_line_integrals_split_equals_stat_eq():
+    """rc_line_integrals over disjoint wavelength ranges, summed (the all-reduce of a
+    wavelength split), then rc_stat_eq_integrals: the populations of rc_stat_eq to 1e-12;
+    with one range over all wavelengths, bit for bit.  The integrals match the FP64
+    oracle's on the same FP32 inputs to 1e-10, the bar of the other FP64 kernels here (the
+    kernel's Gaussian profile comes from a ratio recurrence a few ulps from the direct
+    exponentials)."""
+    rcx = _rcx()
+    atom = rcx.Atom(ATOM)
+    T, nH, vox = _slab(48)
+    Td = _dev(T)
+    ne, na, pops0 = atom.lte(Td, _dev(nH))
+    chi, eta = atom.emis_opac(Td, pops0)
+    nl = chi.shape[0]
+    plan = rcx.Plan(48, 48, 5, voxel_size=vox)
+    _, J_eff, alo_c = plan.formal_solve_mali(chi.reshape(nl, 48, 48), eta.reshape(nl, 48, 48))
+    J_eff, alo_c = J_eff.reshape(nl, -1), alo_c.reshape(nl, -1)
+    ref = pops0.clone()
+    d_ref = atom.stat_eq(Td, ne, na, J_eff, alo_c, ref)
+    whole = atom.line_integrals(Td, J_eff, alo_c, 0)
+    one = pops0.clone()
+    d_one = atom.stat_eq_integrals(Td, ne, na, whole, one)
+    assert torch.equal(one, ref) and d_one == d_ref
+    split = atom.line_integrals(Td, J_eff[:30].contiguous(), alo_c[:30].contiguous(), 0) + \
+        atom.line_integrals(Td, J_eff[30:].contiguous(), alo_c[30:].contiguous(), 30)
+    two = pops0.clone()
+    atom.stat_eq_integrals(Td, ne, na, split, two)
+    np.testing.assert_allclose(two.cpu().numpy(), ref.cpu().numpy(), rtol=1e-12)
+    w_r = nlte.line_integrals(ATOM, T, J_eff.cpu().numpy().astype(np.float64),
+                              alo_c.cpu().numpy().astype(np.float64))
+    np.testing.assert_allclose(whole.cpu().numpy(), w_r, rtol=1e-10)
+
+
+def test_sharded_driver_in_one_process_equals_nlte_solve():
+    """The wavelength-split driver with a single process (one range, no collective) walks
+    the same iteration as rc_nlte_solve: same iteration count and populations."""
+    from paper_2408_14425_b300 import distributed
+    rcx = _rcx()
+    atom = rcx.Atom(ATOM)
+    T, nH, vox = _slab(48)
+    Td = _dev(T)
+    plan = rcx.Plan(48, 48, 5, voxel_size=vox)
+    ne, na, pops = atom.lte(Td, _dev(nH))
+    conv, it, hist = rcx.nlte_solve(plan, atom, Td, ne, na, pops, tol=1e-3, max_iter=100)
+    _, _, pops2 = atom.lte(Td, _dev(nH))
+    ops = distributed.GpuOps(plan, atom, Td, ne, na)
+    conv2, it2, hist2 = distributed.nlte_solve_sharded(ops, atom.n_lambda, pops2, tol=1e-3,
+                                                       max_iter=100)
+    assert conv and conv2 and it == it2
+    np.testing.assert_allclose(pops2.cpu().numpy(), pops.cpu().numpy(), rtol=1e-13)

@@ -266,9 +266,29 @@ def run_ours(args):
             plan.formal_solve_host(chi_p, eta_p, J_p)
         t_e2e = max_over_ranks((time.perf_counter() - t0) / args.steps, dist, "cuda")
         slab = n_lambda * n_side * n_side * 4
-        e2e = {"value": world * n_lambda / t_e2e, "unit": UNIT,
+        # the same through the pipelined entry point: consecutive steps overlap their first
+        # chunk's copy in and last chunk's copy out with the neighbouring step's solves; two
+        # sets of pinned buffers alternate between steps, and the timed region ends when the
+        # last step's J is in host memory
+        chi_q = torch.from_numpy(chi_h).pin_memory()
+        eta_q = torch.from_numpy(eta_h).pin_memory()
+        J_q = torch.empty_like(chi_q).pin_memory()
+        bufs = [(chi_p, eta_p, J_p), (chi_q, eta_q, J_q)]
+        plan.formal_solve_host_async(*bufs[1])
+        plan.wait()
+        if dist:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for k in range(args.steps):
+            plan.formal_solve_host_async(*bufs[k & 1])
+        plan.wait()
+        t_pipe = max_over_ranks((time.perf_counter() - t0) / args.steps, dist, "cuda")
+        e2e = {"value": world * n_lambda / t_pipe, "unit": UNIT,
                "h2d_bytes_per_step": 2 * slab, "d2h_bytes_per_step": slab,
-               "api": "rc_formal_solve_host (pinned host buffers, chunked copy/compute overlap)"}
+               "api": "rc_formal_solve_host_async + rc_plan_wait (pinned host buffers, two sets "
+                      "alternating; chunked copy/compute overlap within and across steps)",
+               "blocking_call": {"value": world * n_lambda / t_e2e,
+                                 "api": "rc_formal_solve_host (one blocking call per step)"}}
 
     if rank != 0:
         if dist:
@@ -465,9 +485,12 @@ def nlte_heldout(args, atom):
     Y = torch.cat(Ys)
     del Xs, Ys
     net = rcx.MLP(seed=1)
+    if args.train_tc:
+        net.use_tensor_cores(False, training=True)   # the 64-wide products on tcgen05
     t0 = time.perf_counter()
     net.fit_normalization(X)
     hist = net.train(X, Y, batch=4096, steps=args.train_steps, lr=2e-3)
+    net.tensor_core_status()
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t0
     train_loss, _ = net.loss_grad(X, Y)
@@ -506,6 +529,8 @@ def nlte_heldout(args, atom):
                        "samples": n_samples, "data_seconds": round(t_data, 2),
                        "mean_iterations": float(np.mean(its)),
                        "train_seconds": round(t_train, 2), "steps": args.train_steps,
+                       "products": "tcgen05 (hi + lo bf16 activations, FP32 accumulation)"
+                                   if args.train_tc else "FP32 FMA",
                        "batch": 4096, "final_minibatch_loss": hist[-1] if hist else None,
                        "full_set_loss": train_loss}
     return out, net, plan, T, nH
@@ -621,7 +646,9 @@ def run_batched(args):
     if _env_int("RANK", 0) != 0:
         return
     rbuild.build()
-    doms = workloads.batched_domains()
+    doms = workloads.batched_domains(n_domains=args.n_domains, side_min=args.side_min,
+                                     side_max=args.side_max, nl_min=args.nl_min,
+                                     nl_max=args.nl_max)
     plans, chis, etas, Js = [], [], [], []
     for side, nl, sb in doms:
         chi, eta = workloads.grf_fields(side, nl, seed_base=sb)
@@ -676,9 +703,10 @@ def run_batched(args):
             "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": round(ms, 3), "higher_is_better": True, "dtype": "f32",
             "data": "synthetic",
-            "config": {"workload": "16 domains, sides " + ",".join(str(s) for s, _, _ in doms) +
-                       " (seed 7), 32..128 wavelengths each (" + str(slices) + " slices), GRF "
-                       "recipe, 8 cascades, W0=4, branching 4, interval0=1", "storage": args.precision,
+            "config": {"workload": f"{len(doms)} domains, sides " + ",".join(str(s) for s, _, _ in doms) +
+                       f" (seed 7), {args.nl_min}..{args.nl_max} wavelengths each (" + str(slices) +
+                       " slices), GRF recipe, 8 cascades, W0=4, branching 4, interval0=1",
+                       "storage": args.precision,
                        "lane_layout": [info["lambda_block"], info["lambda_per_lane"]],
                        "launches_per_step": info["launches"], "graph": True,
                        "solo_domains": info["solo_domains"],
@@ -696,6 +724,49 @@ def run_batched(args):
                                       "launches over the others)",
                             "algorithmic_bytes_per_step": alg}
     print(json.dumps(line), flush=True)
+
+
+def run_mlp(args):
+    """The surrogate network's kernels on 2^20 samples (random features and targets): the
+    forward pass (FP32 FMA vs the 64 x 64 layer on tcgen05) and the loss + gradient of a
+    training step (FP32 FMA vs the three 64-wide products on tcgen05), CUDA events over
+    `steps` calls after `warmup`."""
+    import torch
+
+    from paper_2408_14425_b300 import build as rbuild
+    from paper_2408_14425_b300 import rcx
+    torch.cuda.set_device(_env_int("LOCAL_RANK", 0))
+    if _env_int("RANK", 0) != 0:
+        return
+    rbuild.build()
+    n = 1 << 20
+    gen = torch.Generator(device="cuda").manual_seed(0)
+    X = torch.randn(n, 6, device="cuda", generator=gen)
+    Y = torch.randn(n, 3, device="cuda", generator=gen)
+    net = rcx.MLP(seed=1)
+    net.fit_normalization(X)
+    out = {"metric": "surrogate network kernels, ms per call on 2^20 samples", "unit": "ms",
+           "higher_is_better": False, "data": "synthetic", "samples": n}
+
+    def timed(fn):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return round(e0.elapsed_time(e1) / args.steps, 4)
+
+    for infer, train, key in [(False, False, "fma"), (True, True, "tensor_cores")]:
+        net.use_tensor_cores(infer, training=train)
+        out[key] = {"forward_ms": timed(lambda: net.forward(X)),
+                    "loss_grad_ms": timed(lambda: net.loss_grad(X, Y))}
+        net.tensor_core_status()
+    out["value"] = out["tensor_cores"]["loss_grad_ms"]
+    print(json.dumps(out), flush=True)
 
 
 def emergent_rays(n_side: int, n_view: int = 16, per_view: int = 2048):
@@ -781,11 +852,16 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["formal", "nlte", "batched", "emergent"],
+    ap.add_argument("--workload", choices=["formal", "nlte", "batched", "emergent", "mlp"],
                     default="formal",
                     help="formal: the RC formal solution (headline); nlte: time-to-1e-3; "
                          "batched: 16 uneven domains in one graph; emergent: lines of sight")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--n-domains", type=int, default=16, help="batched: number of domains")
+    ap.add_argument("--side-min", type=int, default=256, help="batched: smallest side")
+    ap.add_argument("--side-max", type=int, default=2048, help="batched: largest side")
+    ap.add_argument("--nl-min", type=int, default=32, help="batched: fewest wavelengths")
+    ap.add_argument("--nl-max", type=int, default=128, help="batched: most wavelengths")
     ap.add_argument("--n-incl", type=int, default=1,
                     help="inclinations per in-plane ray (2D invariance; not the headline)")
     ap.add_argument("--bilinear-fix", action="store_true",
@@ -794,6 +870,8 @@ def main():
     ap.add_argument("--train-side", type=int, default=512,
                     help="training slabs: the non-LTE workload's 512^2 prominence slab")
     ap.add_argument("--train-cascades", type=int, default=6)
+    ap.add_argument("--train-tc", action="store_true",
+                    help="train the surrogate with its 64-wide products on the tensor cores")
     ap.add_argument("--no-nlte", action="store_true",
                     help="skip the non-LTE half of the metric in the default run")
     ap.add_argument("--train-steps", type=int, default=16000)
@@ -819,6 +897,8 @@ def main():
         run_nlte(args)
     elif args.workload == "emergent":
         run_emergent(args)
+    elif args.workload == "mlp":
+        run_mlp(args)
     elif args.workload == "batched":
         if args.precision == "f32" and "--precision" not in sys.argv:
             args.precision = "bf16"

@@ -154,6 +154,23 @@ rc_status rc_formal_solve(rc_plan_t plan, const float* chi, const float* eta, in
 rc_status rc_formal_solve_host(rc_plan_t plan, const float* chi_host, const float* eta_host,
                                int n_lambda, float* J_host, float* alo_host);
 
+/*
+ * rc_formal_solve_host_async -- rc_formal_solve_host without the wait at the end: the copies
+ * and solves are enqueued on the plan's three streams and the call returns.  Consecutive calls
+ * on one plan pipeline: a call's first chunk is copied in while the previous call's last chunk
+ * is solved, and the previous call's last J is copied out while this call's first chunk is
+ * solved (the staging buffers alternate across calls).  The host buffers of a call must stay
+ * valid, and chi / eta unmodified, until the call has completed: after rc_plan_wait, or after
+ * a later rc_formal_solve_host on the same plan returns.  Until then the plan must not be used
+ * by other calls on other streams (rc_formal_solve and friends share its scratch).
+ * rc_plan_wait -- blocks until every host-buffer solve enqueued on the plan has completed and
+ * its results are in host memory.
+ * Errors: as rc_formal_solve_host; asynchronous CUDA errors are reported by rc_plan_wait.
+ */
+rc_status rc_formal_solve_host_async(rc_plan_t plan, const float* chi, const float* eta,
+                                     int n_lambda, float* J, float* alo);
+rc_status rc_plan_wait(rc_plan_t plan);
+
 /* Per-cascade geometry of a plan: probes per axis, directions, interval bounds (b = inf for
  * the top cascade).  Any output pointer may be NULL.  Errors: RC_ERR_ARG. */
 rc_status rc_plan_cascade(rc_plan_t plan, int i, int* px, int* pz, long long* dirs,

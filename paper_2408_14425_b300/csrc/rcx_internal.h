@@ -224,6 +224,8 @@ struct rc_plan_s {
     cudaStream_t s_io[3] = {nullptr, nullptr, nullptr};   // copies in, solves, copies out
     float* d_stage = nullptr;        // 2 chunks x (chi, eta, J, alo)
     size_t stage_bytes = 0;
+    cudaEvent_t io_done[2] = {nullptr, nullptr};   // staging buffer b free (its J copied out)
+    long long io_chunks = 0;         // chunks enqueued so far (buffer of a chunk: count % 2)
     int last_launches = 0;
     // tracing
     bool timing = false;

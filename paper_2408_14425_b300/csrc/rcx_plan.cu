@@ -613,6 +613,8 @@ void rc_plan_destroy(rc_plan_t p) {
     cudaFree(p->d_stage);
     for (auto& s : p->s_io)
         if (s) cudaStreamDestroy(s);
+    for (auto& e : p->io_done)
+        if (e) cudaEventDestroy(e);
     for (auto& e : p->ev) cudaEventDestroy(e);
     delete p;
 }
@@ -924,18 +926,11 @@ rc_status rc_formal_solve_mali(rc_plan_t p, const float* chi, const float* eta, 
     return solve_device(p, chi, eta, n_lambda, J, alo, (cudaStream_t)stream, J_eff, alo_c);
 }
 
-rc_status rc_formal_solve_host(rc_plan_t p, const float* chi_h, const float* eta_h, int n_lambda,
-                               float* J_h, float* alo_h) {
-    g_last_error.clear();
-    if (!p) return fail(RC_ERR_ARG, "rc_formal_solve_host: plan is NULL");
-    if (n_lambda < 0) return fail(RC_ERR_ARG, "rc_formal_solve_host: n_lambda < 0");
-    if (n_lambda == 0) return RC_OK;
-    if (!chi_h || !eta_h || !J_h)
-        return fail(RC_ERR_ARG, "rc_formal_solve_host: chi, eta and J must be non-NULL");
-    DeviceGuard dg(p->device);
-    if (!dg.ok) return fail(RC_ERR_CUDA, "rc_formal_solve_host: cannot select the plan's device");
+// Enqueues a host-buffer solve on the plan's three streams without waiting for it.
+static rc_status enqueue_host_solve(rc_plan_t p, const float* chi_h, const float* eta_h,
+                                    int n_lambda, float* J_h, float* alo_h, const char* who) {
     cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return cuda_fail(e, "rc_formal_solve_host: pending CUDA error");
+    if (e != cudaSuccess) return cuda_fail(e, (std::string(who) + ": pending CUDA error").c_str());
 
     // Chunks of whole lambda blocks; chunk c's copies overlap chunk c-1's solve.  The first
     // chunk (whose copy in nothing hides) and the last (whose copy out nothing hides) are
@@ -958,36 +953,40 @@ rc_status rc_formal_solve_host(rc_plan_t p, const float* chi_h, const float* eta
     const size_t per_buf = slab * (alo_h ? 4 : 3);             // chi, eta, J (, alo)
     const size_t need = 2 * per_buf * sizeof(float);
     if (p->stage_bytes < need) {
-        cudaDeviceSynchronize();
+        cudaDeviceSynchronize();                               // earlier solves may use it
         cudaFree(p->d_stage);
         p->d_stage = nullptr;
         p->stage_bytes = 0;
         if ((e = cudaMalloc(&p->d_stage, need)) != cudaSuccess) {
             cudaGetLastError();
-            return fail(RC_ERR_OOM, "rc_formal_solve_host: staging allocation failed");
+            return fail(RC_ERR_OOM, (std::string(who) + ": staging allocation failed").c_str());
         }
         p->stage_bytes = need;
     }
     for (auto& s : p->s_io)
         if (!s && (e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking)) != cudaSuccess)
-            return cuda_fail(e, "rc_formal_solve_host: stream creation");
+            return cuda_fail(e, (std::string(who) + ": stream creation").c_str());
+    for (auto& ev : p->io_done)
+        if (!ev && (e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess)
+            return cuda_fail(e, (std::string(who) + ": event creation").c_str());
     rc_status st = ensure_scratch(p, chunk);
     if (st != RC_OK) return st;
 
     // s_io[0] carries copies in, s_io[1] the solves, s_io[2] copies out, so the copy of
-    // chunk c's J overlaps chunk c+1's solve.  Buffer b = c % 2 is reused two chunks
-    // later, after its J has left (event done[b]).
-    cudaEvent_t loaded[2], solved[2], done[2];
+    // chunk c's J overlaps chunk c+1's solve.  Chunks are counted across calls: buffer
+    // b = count % 2 is reused two chunks later, after its J has left (io_done[b]), so the
+    // first chunk of a call copies in while the previous call's last chunk is solved.
+    cudaEvent_t loaded[2], solved[2];
     for (int b = 0; b < 2; ++b) {
         cudaEventCreateWithFlags(&loaded[b], cudaEventDisableTiming);
         cudaEventCreateWithFlags(&solved[b], cudaEventDisableTiming);
-        cudaEventCreateWithFlags(&done[b], cudaEventDisableTiming);
     }
     int launches = 0;
     const bool timing_was = p->timing;
     p->timing = false;
     for (int c = 0; c < n_chunks && st == RC_OK; ++c) {
-        const int b = c & 1;
+        const long long g = p->io_chunks++;
+        const int b = (int)(g & 1);
         const int l0 = bounds[c];
         const int nl = bounds[c + 1] - l0;
         const size_t bytes = (size_t)nl * ncell * sizeof(float);
@@ -995,7 +994,7 @@ rc_status rc_formal_solve_host(rc_plan_t p, const float* chi_h, const float* eta
         float* deta = dchi + slab;
         float* dJ = deta + slab;
         float* dalo = alo_h ? dJ + slab : nullptr;
-        if (c >= 2) cudaStreamWaitEvent(p->s_io[0], done[b], 0);
+        if (g >= 2) cudaStreamWaitEvent(p->s_io[0], p->io_done[b], 0);
         cudaMemcpyAsync(dchi, chi_h + (size_t)l0 * ncell, bytes, cudaMemcpyHostToDevice, p->s_io[0]);
         cudaMemcpyAsync(deta, eta_h + (size_t)l0 * ncell, bytes, cudaMemcpyHostToDevice, p->s_io[0]);
         cudaEventRecord(loaded[b], p->s_io[0]);
@@ -1007,22 +1006,67 @@ rc_status rc_formal_solve_host(rc_plan_t p, const float* chi_h, const float* eta
         cudaMemcpyAsync(J_h + (size_t)l0 * ncell, dJ, bytes, cudaMemcpyDeviceToHost, p->s_io[2]);
         if (alo_h)
             cudaMemcpyAsync(alo_h + (size_t)l0 * ncell, dalo, bytes, cudaMemcpyDeviceToHost, p->s_io[2]);
-        cudaEventRecord(done[b], p->s_io[2]);
+        cudaEventRecord(p->io_done[b], p->s_io[2]);
     }
-    e = cudaStreamSynchronize(p->s_io[2]);
-    cudaError_t e1 = cudaStreamSynchronize(p->s_io[1]);
-    cudaError_t e0 = cudaStreamSynchronize(p->s_io[0]);
-    if (e == cudaSuccess) e = e1 != cudaSuccess ? e1 : e0;
+    // events recorded on a stream may be destroyed at once (released when they complete)
     for (int b = 0; b < 2; ++b) {
         cudaEventDestroy(loaded[b]);
         cudaEventDestroy(solved[b]);
-        cudaEventDestroy(done[b]);
     }
     p->last_launches = launches;
     p->timing = timing_was;
     if (st != RC_OK) return st;
-    if (e != cudaSuccess) return cuda_fail(e, "rc_formal_solve_host");
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, who);
     return RC_OK;
+}
+
+static rc_status wait_host_solves(rc_plan_t p, const char* who) {
+    cudaError_t e = cudaSuccess;
+    for (int k = 2; k >= 0; --k)
+        if (p->s_io[k]) {
+            const cudaError_t ek = cudaStreamSynchronize(p->s_io[k]);
+            if (e == cudaSuccess) e = ek;
+        }
+    return e == cudaSuccess ? RC_OK : cuda_fail(e, who);
+}
+
+static rc_status check_host_args(rc_plan_t p, const float* chi_h, const float* eta_h,
+                                 int n_lambda, const float* J_h, const char* who) {
+    if (!p) return fail(RC_ERR_ARG, (std::string(who) + ": plan is NULL").c_str());
+    if (n_lambda < 0) return fail(RC_ERR_ARG, (std::string(who) + ": n_lambda < 0").c_str());
+    if (n_lambda > 0 && (!chi_h || !eta_h || !J_h))
+        return fail(RC_ERR_ARG, (std::string(who) + ": chi, eta and J must be non-NULL").c_str());
+    return RC_OK;
+}
+
+rc_status rc_formal_solve_host(rc_plan_t p, const float* chi_h, const float* eta_h, int n_lambda,
+                               float* J_h, float* alo_h) {
+    g_last_error.clear();
+    rc_status st = check_host_args(p, chi_h, eta_h, n_lambda, J_h, "rc_formal_solve_host");
+    if (st != RC_OK || n_lambda == 0) return st;
+    DeviceGuard dg(p->device);
+    if (!dg.ok) return fail(RC_ERR_CUDA, "rc_formal_solve_host: cannot select the plan's device");
+    st = enqueue_host_solve(p, chi_h, eta_h, n_lambda, J_h, alo_h, "rc_formal_solve_host");
+    const rc_status sw = wait_host_solves(p, "rc_formal_solve_host");
+    return st != RC_OK ? st : sw;
+}
+
+rc_status rc_formal_solve_host_async(rc_plan_t p, const float* chi_h, const float* eta_h,
+                                     int n_lambda, float* J_h, float* alo_h) {
+    g_last_error.clear();
+    rc_status st = check_host_args(p, chi_h, eta_h, n_lambda, J_h, "rc_formal_solve_host_async");
+    if (st != RC_OK || n_lambda == 0) return st;
+    DeviceGuard dg(p->device);
+    if (!dg.ok) return fail(RC_ERR_CUDA, "rc_formal_solve_host_async: cannot select the plan's device");
+    return enqueue_host_solve(p, chi_h, eta_h, n_lambda, J_h, alo_h, "rc_formal_solve_host_async");
+}
+
+rc_status rc_plan_wait(rc_plan_t p) {
+    g_last_error.clear();
+    if (!p) return fail(RC_ERR_ARG, "rc_plan_wait: plan is NULL");
+    DeviceGuard dg(p->device);
+    if (!dg.ok) return fail(RC_ERR_CUDA, "rc_plan_wait: cannot select the plan's device");
+    return wait_host_solves(p, "rc_plan_wait");
 }
 
 }  // extern "C"

@@ -29,6 +29,7 @@ EXPORTS = [
     "rc_formal_solve_mali", "rc_atom_create", "rc_atom_destroy", "rc_atom_n_lambda", "rc_lte",
     "rc_emis_opac", "rc_stat_eq", "rc_nlte_solve", "rc_plan_set_lane_layout",
     "rc_plan_set_march", "rc_plan_get_march", "rc_line_integrals", "rc_stat_eq_integrals",
+    "rc_formal_solve_host_async", "rc_plan_wait",
     "rc_plan_get_lane_layout", "rc_plan_autotune", "rc_batch_create", "rc_batch_run",
     "rc_batch_info", "rc_batch_destroy", "rc_formal_solve_batched", "rc_mlp_create",
     "rc_mlp_destroy", "rc_mlp_n_params", "rc_mlp_set_params", "rc_mlp_get_params",
@@ -93,6 +94,10 @@ def load():
     L.rc_formal_solve.restype = ctypes.c_int
     L.rc_formal_solve_host.argtypes = [_vp, _vp, _vp, ctypes.c_int, _vp, _vp]
     L.rc_formal_solve_host.restype = ctypes.c_int
+    L.rc_formal_solve_host_async.argtypes = L.rc_formal_solve_host.argtypes
+    L.rc_formal_solve_host_async.restype = ctypes.c_int
+    L.rc_plan_wait.argtypes = [_vp]
+    L.rc_plan_wait.restype = ctypes.c_int
     L.rc_plan_cascade.argtypes = [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                   ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_longlong),
                                   ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
@@ -424,6 +429,19 @@ class Plan:
             self._h, _host_ptr(chi, "chi", shape), _host_ptr(eta, "eta", shape), nl,
             _host_ptr(J, "J", shape), _host_ptr(alo, "alo", shape) if alo is not None else None))
         return (J, alo) if alo is not None else J
+
+    def formal_solve_host_async(self, chi, eta, J, alo=None):
+        """rc_formal_solve_host_async: enqueues the host-buffer solve and returns; the buffers
+        must stay alive and chi / eta unmodified until wait() (consecutive calls pipeline)."""
+        nl = chi.shape[0]
+        shape = (nl, self.nz, self.nx)
+        check(load().rc_formal_solve_host_async(
+            self._h, _host_ptr(chi, "chi", shape), _host_ptr(eta, "eta", shape), nl,
+            _host_ptr(J, "J", shape), _host_ptr(alo, "alo", shape) if alo is not None else None))
+
+    def wait(self):
+        """rc_plan_wait: every enqueued host-buffer solve has completed."""
+        check(load().rc_plan_wait(self._h))
 
 
 def formal_solve_noalloc(chi, eta, n_cascades: int, dirs0: int = 4, interval0: float = 1.0,

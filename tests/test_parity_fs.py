@@ -427,3 +427,27 @@ def test_shared_dda_march_equals_lane_group_march(nx, nz, C, strips, prec, nl):
     for other in out[1:]:
         for a, b in zip(out[0], other):
             assert torch.equal(a, b), f"max abs diff {(a - b).abs().max().item():.3e}"
+
+
+def test_pipelined_host_solves_equal_blocking_ones():
+    """rc_formal_solve_host_async: three consecutive calls on different inputs (each cut into
+    16 + 32 + 16-wavelength chunks whose staging buffers alternate across the calls) give,
+    after rc_plan_wait, the J and Lambda* of one blocking rc_formal_solve_host per input, bit
+    for bit."""
+    rcx = _rcx()
+    n, nl = 96, 64
+    ins = []
+    for seed in range(3):
+        rng = np.random.default_rng(50 + seed)
+        chi = (10 ** rng.uniform(-4, 1.5, (nl, n, n))).astype(np.float32)
+        ins.append((chi, (chi * 10 ** rng.uniform(-1, 1, chi.shape)).astype(np.float32)))
+    plan = rcx.Plan(n, n, 6)
+    outs = [(np.full((nl, n, n), np.nan, np.float32), np.full((nl, n, n), np.nan, np.float32))
+            for _ in ins]
+    for (chi, eta), (J, alo) in zip(ins, outs):
+        plan.formal_solve_host_async(chi, eta, J, alo)
+    plan.wait()
+    for (chi, eta), (J, alo) in zip(ins, outs):
+        J_ref, alo_ref = plan.formal_solve_host(chi, eta, want_alo=True)
+        np.testing.assert_array_equal(J, J_ref)
+        np.testing.assert_array_equal(alo, alo_ref)

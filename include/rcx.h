@@ -40,7 +40,7 @@ typedef enum {
     RC_ERR_CUDA = -3,          /* a CUDA runtime call failed (message in rc_last_error) */
     RC_ERR_TIMEOUT = -4,       /* a bounded device-side wait ran out */
     RC_ERR_NOT_CONVERGED = -5, /* an iteration hit its iteration cap */
-    RC_ERR_UNSUPPORTED = -6    /* a valid request this build does not implement */
+    RC_ERR_UNSUPPORTED = -6    /* a valid request the library does not implement */
 } rc_status;
 
 /* Uniform 2D grid (Sec. 3.2: only uniform grids, traversed by DDA). */
@@ -92,7 +92,7 @@ void rc_options_default(rc_options* opt);
  * rc_plan -- geometry of a cascade set (Sec. 2.3, Eq. 12-13; Sec. 3.2).
  *   n_cascades  number of cascades C >= 1; the top one extends to the domain edge.
  *   dirs0       directions of cascade 0 (W_0 >= 1), directions theta_k = 2 pi (k+1/2)/W_0.
- *   branching   children per direction per cascade (2 alpha); this build supports 4 (alpha = 2,
+ *   branching   children per direction per cascade (2 alpha); the library supports 4 (alpha = 2,
  *               the value the paper uses throughout, Sec. 2.4).
  *   interval0   length of the cascade-0 interval in voxels (> 0).
  *   opt         NULL for defaults.

@@ -56,6 +56,21 @@ def rank_lambdas(rank: int, n_lambda: int):
     return list(range(rank * n_lambda, (rank + 1) * n_lambda))
 
 
+def rank_domains(rank: int, world: int, doms):
+    """Indices of the batched workload's domains that `rank` solves: the domains are
+    independent (Sec. 3.6), so they are dealt out by estimated cost (side^2 x wavelengths),
+    largest first, each to the rank with the least cost so far (ties to the lower rank)."""
+    load = [0] * world
+    mine = []
+    order = sorted(range(len(doms)), key=lambda d: (-doms[d][0] ** 2 * doms[d][1], d))
+    for d in order:
+        r = min(range(world), key=lambda k: (load[k], k))
+        load[r] += doms[d][0] ** 2 * doms[d][1]
+        if r == rank:
+            mine.append(d)
+    return sorted(mine)
+
+
 def max_over_ranks(value: float, dist=None, device="cpu") -> float:
     """Maximum of a per-rank scalar over all ranks (the step time of the slowest rank)."""
     if dist is None:
@@ -645,13 +660,17 @@ def run_batched(args):
 
     from paper_2408_14425_b300 import build as rbuild
     from paper_2408_14425_b300 import rcx, workloads
-    torch.cuda.set_device(_env_int("LOCAL_RANK", 0))
-    if _env_int("RANK", 0) != 0:
-        return
+    rank, world, local = _env_int("RANK", 0), _env_int("WORLD_SIZE", 1), _env_int("LOCAL_RANK", 0)
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:   # domains dealt out to the ranks, no data-path collective
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     rbuild.build()
-    doms = workloads.batched_domains(n_domains=args.n_domains, side_min=args.side_min,
-                                     side_max=args.side_max, nl_min=args.nl_min,
-                                     nl_max=args.nl_max)
+    all_doms = workloads.batched_domains(n_domains=args.n_domains, side_min=args.side_min,
+                                         side_max=args.side_max, nl_min=args.nl_min,
+                                         nl_max=args.nl_max)
+    doms = [all_doms[d] for d in rank_domains(rank, world, all_doms)]
     plans, chis, etas, Js = [], [], [], []
     for side, nl, sb in doms:
         chi, eta = workloads.grf_fields(side, nl, seed_base=sb)
@@ -679,7 +698,7 @@ def run_batched(args):
     ev1.record(stream)
     torch.cuda.synchronize()
     clk = clocks.stop()
-    ms = ev0.elapsed_time(ev1) / args.steps
+    ms = max_over_ranks(ev0.elapsed_time(ev1) / args.steps, dist, "cuda")
     # the same work domain by domain (one rc_formal_solve per domain, same lane layout)
     for _ in range(2):
         for p, c, e, j in zip(plans, chis, etas, Js):
@@ -690,11 +709,15 @@ def run_batched(args):
         p.formal_solve(c, e, j)
     ev1.record(stream)
     torch.cuda.synchronize()
-    ms_seq = ev0.elapsed_time(ev1)
-    slices = sum(nl for _, nl, _ in doms)
+    ms_seq = max_over_ranks(ev0.elapsed_time(ev1), dist, "cuda")
+    if dist:
+        dist.destroy_process_group()
+    if rank != 0:
+        return
+    slices = sum(nl for _, nl, _ in all_doms)
     alg = 0
-    have_cross = True
-    for (side, nl, _), p in zip(doms, plans):
+    have_cross = world == 1        # the byte model needs every domain's plan
+    for (side, nl, _), p in zip(doms if have_cross else [], plans):
         try:
             cross = _load_crossings(side, 8)
         except KeyError:
@@ -703,10 +726,11 @@ def run_batched(args):
         alg += sum(_algorithmic_bytes(cross, p, nl, side)[0])
     peak, peak_kind = _peaks()
     line = {"metric": "RC wavelength-slices/s, batched uneven domains", "value": round(slices / (ms / 1e3), 2),
-            "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "scaling": "strong", "rank0_domains": len(doms),
             "ms_per_step": round(ms, 3), "higher_is_better": True, "dtype": "f32",
             "data": "synthetic",
-            "config": {"workload": f"{len(doms)} domains, sides " + ",".join(str(s) for s, _, _ in doms) +
+            "config": {"workload": f"{len(all_doms)} domains, sides " + ",".join(str(s) for s, _, _ in all_doms) +
                        f" (seed 7), {args.nl_min}..{args.nl_max} wavelengths each (" + str(slices) +
                        " slices), GRF recipe, 8 cascades, W0=4, branching 4, interval0=1",
                        "storage": args.precision,
@@ -716,7 +740,7 @@ def run_batched(args):
                        "autotune": not args.no_autotune, "create_seconds": round(t_create, 2)},
             "sequential_ms_per_step": round(ms_seq, 3),
             "batched_speedup": round(ms_seq / ms, 3),
-            "cell_wavelengths_per_s": round(sum(s * s * nl for s, nl, _ in doms) / (ms / 1e3), 1),
+            "cell_wavelengths_per_s": round(sum(s * s * nl for s, nl, _ in all_doms) / (ms / 1e3), 1),
             "clocks": clk}
     if have_cross:
         line["roofline"] = {"bound": "hbm", "achieved": round(alg / (ms / 1e3) / 1e9, 1),

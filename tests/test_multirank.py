@@ -148,3 +148,21 @@ def test_lambda_range_partitions_the_wavelengths():
         assert sum(c for _, c in got) == n
         assert [b for b, _ in got] == [sum(c for _, c in got[:r]) for r in range(world)]
         assert max(c for _, c in got) - min(c for _, c in got) <= 1
+
+
+def test_batched_domains_are_dealt_out_by_cost():
+    """The batched workload over N ranks: every domain goes to exactly one rank, and the
+    largest rank's cost (side^2 x wavelengths) is within the largest single domain of the
+    mean (greedy largest-first assignment)."""
+    sys.path.insert(0, ROOT)
+    import bench
+    from paper_2408_14425_b300 import workloads
+    doms = workloads.batched_domains()
+    cost = [s * s * nl for s, nl, _ in doms]
+    for world in (1, 2, 4, 8):
+        parts = [bench.rank_domains(r, world, doms) for r in range(world)]
+        flat = sorted(d for p in parts for d in p)
+        assert flat == list(range(len(doms)))
+        loads = [sum(cost[d] for d in p) for p in parts]
+        assert max(loads) - sum(loads) / world <= max(cost)
+    assert bench.rank_domains(0, 1, doms) == list(range(len(doms)))

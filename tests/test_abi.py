@@ -85,3 +85,13 @@ def test_null_arguments(lib):
 def test_march_mode_setter_rejects_bad_arguments(lib):
     assert lib.rc_plan_set_march(None, 1) == -1
     assert lib.rc_plan_get_march(None, None) == -1
+
+
+def test_new_entry_points_reject_null_arguments(lib):
+    """The pipelined host solve, its wait and the two halves of the statistical equilibrium
+    return RC_ERR_ARG on NULL handles before any device work."""
+    assert lib.rc_formal_solve_host_async(None, None, None, 4, None, None) == -1
+    assert lib.rc_plan_wait(None) == -1
+    assert lib.rc_line_integrals(None, None, None, None, 0, 1, 16, None, None) == -1
+    assert lib.rc_stat_eq_integrals(None, None, None, None, None, 16, None, None, None) == -1
+    assert b"NULL" in lib.rc_last_error() or b"plan" in lib.rc_last_error()

@@ -8,7 +8,9 @@ equilibrium.  This module strings the calls together:
   whose line-centre values are three of the network's six features;
 * ``training_pairs`` -- features at LTE and log departure coefficients of the converged
   populations of one atmosphere;
-* ``solve`` -- the iteration from LTE (``net=None``) or from the network's seed, timed.
+* ``solve`` -- the iteration from LTE (``net=None``) or from the network's seed, timed;
+* ``train_stepped`` -- Adam through the library with the learning rate halved over equal
+  segments.
 """
 from __future__ import annotations
 
@@ -56,3 +58,19 @@ def solve(plan, atom, T, nH, net=None, tol=1e-3, max_iter=2000):
     torch.cuda.synchronize()
     return dict(pops=pops, converged=conv, iterations=it, seconds=time.perf_counter() - t0,
                 history=hist, fallback=fallback, ne=ne, n_atom=na)
+
+
+def train_stepped(net, X, Y, steps: int, batch: int = 4096, lr0: float = 4e-3, segments: int = 4):
+    """Adam (the library's kernels) for `steps` minibatch steps in `segments` equal parts, the
+    learning rate halved from one part to the next (lr0, lr0/2, ...).  Returns the recorded
+    minibatch losses."""
+    hist = []
+    per = max(1, steps // segments)
+    done = 0
+    for k in range(segments):
+        n = per if k < segments - 1 else steps - done
+        if n <= 0:
+            break
+        hist += net.train(X, Y, batch=batch, steps=n, lr=lr0 * 0.5 ** k)
+        done += n
+    return hist

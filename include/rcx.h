@@ -259,15 +259,22 @@ rc_status rc_plan_get_lane_layout(rc_plan_t plan, int* lambda_block, int* lambda
  * lane layout and no bilinear fix; other plans keep the lane-group march.  All modes give
  * identical results.  Takes effect at the next solve.  Errors: RC_ERR_ARG.
  */
-enum { RC_MARCH_LANE_GROUP = 0, RC_MARCH_SHARED_DDA = 1, RC_MARCH_SHARED_DDA_ALL = 2 };
+enum { RC_MARCH_LANE_GROUP = 0, RC_MARCH_SHARED_DDA = 1, RC_MARCH_SHARED_DDA_ALL = 2,
+       RC_MARCH_TUNED = 3 };
 rc_status rc_plan_set_march(rc_plan_t plan, int mode);
 rc_status rc_plan_get_march(rc_plan_t plan, int* mode);
+/* Bit i of *mask set: cascade i takes the shared-DDA march under the plan's current mode.
+ * RC_MARCH_TUNED is set by rc_plan_autotune (a per-cascade choice by timing); setting another
+ * mode with rc_plan_set_march discards it.  Errors: RC_ERR_ARG. */
+rc_status rc_plan_get_march_cascades(rc_plan_t plan, unsigned* mask);
 
 /*
  * rc_plan_autotune -- times the formal solution of these inputs (device buffers as
  * rc_formal_solve; J is overwritten) with each candidate lane layout (16/4, 8/4, 32/4, 8/2,
  * 4/4, 4/2, 4/1, 2/2, 1/1 wavelengths per ray / per lane; blocks wider than twice n_lambda
- * skipped), keeps the fastest on the plan and reports it.  Synchronous.
+ * skipped), keeps the fastest on the plan and reports it.  Then, unless the plan's march is
+ * RC_MARCH_LANE_GROUP, it times every cascade with both marches and keeps the faster per
+ * cascade (mode RC_MARCH_TUNED; rc_plan_get_march_cascades reports the choice).  Synchronous.
  * Errors: RC_ERR_ARG, RC_ERR_OOM, RC_ERR_CUDA.
  */
 rc_status rc_plan_autotune(rc_plan_t plan, const float* chi, const float* eta, int n_lambda,

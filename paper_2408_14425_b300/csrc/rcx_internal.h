@@ -194,6 +194,7 @@ struct rc_plan_s {
     int LB = 4;                      // wavelengths per lane group (one ray)
     int VL = 1;                      // wavelengths per lane
     int march = RC_MARCH_SHARED_DDA; // cascades >= 1: shared-DDA march where it applies
+    unsigned march_tuned = 0;        // RC_MARCH_TUNED: bit i = cascade i takes the shared DDA
     int n_incl = 1;                  // inclination quadrature (2D invariance)
     float* d_incl = nullptr;         // [r_j (n_incl)][w_j (n_incl)]
     float* d_vout = nullptr;         // per-inclination cascade-0 outputs before the reduction

@@ -2,6 +2,7 @@
 // launch sequence of the formal solution (C ABI declared in include/rcx.h).
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <string>
@@ -161,6 +162,7 @@ bool use_shared_dda(const rc_plan_s* p, int i, const rcx::LevelArgs& a) {
     if (i == 0 || p->march == RC_MARCH_LANE_GROUP || !rcx::level_sdda_supported(p->LB, p->VL, a))
         return false;
     if (p->march == RC_MARCH_SHARED_DDA_ALL) return true;
+    if (p->march == RC_MARCH_TUNED) return (p->march_tuned >> i) & 1u;
     return p->lv[i].b - p->lv[i].a <= kSdMaxInterval;
 }
 
@@ -783,10 +785,80 @@ rc_status rc_plan_get_march(rc_plan_t p, int* mode) {
     return RC_OK;
 }
 
+rc_status rc_plan_get_march_cascades(rc_plan_t p, unsigned* mask) {
+    if (!p || !mask) return fail(RC_ERR_ARG, "rc_plan_get_march_cascades: NULL argument");
+    *mask = 0;
+    for (int i = 1; i < p->C && i < 32; ++i) {
+        const rcx::LevelArgs a = rcx::level_args(p, i, 1, nullptr, nullptr, nullptr, nullptr);
+        if (use_shared_dda(p, i, a)) *mask |= 1u << i;
+    }
+    return RC_OK;
+}
+
 rc_status rc_plan_get_lane_layout(rc_plan_t p, int* lambda_block, int* lambda_per_lane) {
     if (!p) return fail(RC_ERR_ARG, "rc_plan_get_lane_layout: plan is NULL");
     if (lambda_block) *lambda_block = p->LB;
     if (lambda_per_lane) *lambda_per_lane = p->VL;
+    return RC_OK;
+}
+
+// Per-cascade choice between the two marches: each is timed per cascade (the tracing events,
+// best of two solves after a warm-up) and every cascade keeps the faster.  Leaves the plan in
+// RC_MARCH_TUNED when a cascade can take the shared DDA at all.
+static rc_status tune_march(rc_plan_t p, const float* chi, const float* eta, int n_lambda,
+                            float* J, cudaStream_t s) {
+    unsigned can = 0;
+    for (int i = 1; i < p->C && i < 32; ++i) {
+        const rcx::LevelArgs a = rcx::level_args(p, i, n_lambda, nullptr, nullptr, nullptr, nullptr);
+        if (rcx::level_sdda_supported(p->LB, p->VL, a)) can |= 1u << i;
+    }
+    if (!can) return RC_OK;
+    const bool timing_was = p->timing;
+    const size_t need = (size_t)p->C + 7;
+    while (p->ev.size() < need) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(RC_ERR_CUDA, "rc_plan_autotune: event creation");
+        }
+        p->ev.push_back(e);
+    }
+    std::vector<float> best[2];
+    const int modes[2] = {RC_MARCH_LANE_GROUP, RC_MARCH_SHARED_DDA_ALL};
+    rc_status st = RC_OK;
+    for (int m = 0; m < 2 && st == RC_OK; ++m) {
+        p->march = modes[m];
+        best[m].assign(p->C, INFINITY);
+        p->timing = false;
+        st = solve_device(p, chi, eta, n_lambda, J, nullptr, s);      // warm-up
+        for (int r = 0; r < 2 && st == RC_OK; ++r) {
+            p->timing = true;
+            st = solve_device(p, chi, eta, n_lambda, J, nullptr, s);
+            if (st != RC_OK) break;
+            if (cudaEventSynchronize(p->ev[p->timed_launches]) != cudaSuccess) {
+                cudaGetLastError();
+                st = fail(RC_ERR_CUDA, "rc_plan_autotune: timing");
+                break;
+            }
+            for (int j = 0; j < p->timed_launches; ++j) {
+                const std::string& nm = p->launch_names[j];
+                if (nm.rfind("cascade ", 0) != 0) continue;
+                const int i = std::atoi(nm.c_str() + 8);
+                float ms = 0.0f;
+                cudaEventElapsedTime(&ms, p->ev[j], p->ev[j + 1]);
+                if (i >= 0 && i < p->C) best[m][i] = std::min(best[m][i], ms);
+            }
+        }
+    }
+    p->timing = timing_was;
+    if (st != RC_OK) {
+        p->march = RC_MARCH_SHARED_DDA;
+        return st;
+    }
+    p->march_tuned = 0;
+    for (int i = 1; i < p->C && i < 32; ++i)
+        if (((can >> i) & 1u) && best[1][i] < best[0][i]) p->march_tuned |= 1u << i;
+    p->march = RC_MARCH_TUNED;
     return RC_OK;
 }
 
@@ -836,6 +908,7 @@ rc_status rc_plan_autotune(rc_plan_t p, const float* chi, const float* eta, int 
     p->timing = timing_was;
     rc_status st = rcx::plan_set_layout(p, bLB, bVL);
     if (st == RC_OK) st = ensure_scratch(p, n_lambda);
+    if (st == RC_OK && p->march != RC_MARCH_LANE_GROUP) st = tune_march(p, chi, eta, n_lambda, J, s);
     if (lambda_block) *lambda_block = bLB;
     if (lambda_per_lane) *lambda_per_lane = bVL;
     cudaError_t err = cudaGetLastError();

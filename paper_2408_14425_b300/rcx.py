@@ -29,7 +29,7 @@ EXPORTS = [
     "rc_formal_solve_mali", "rc_atom_create", "rc_atom_destroy", "rc_atom_n_lambda", "rc_lte",
     "rc_emis_opac", "rc_stat_eq", "rc_nlte_solve", "rc_plan_set_lane_layout",
     "rc_plan_set_march", "rc_plan_get_march", "rc_line_integrals", "rc_stat_eq_integrals",
-    "rc_formal_solve_host_async", "rc_plan_wait",
+    "rc_formal_solve_host_async", "rc_plan_wait", "rc_plan_get_march_cascades",
     "rc_plan_get_lane_layout", "rc_plan_autotune", "rc_batch_create", "rc_batch_run",
     "rc_batch_info", "rc_batch_destroy", "rc_formal_solve_batched", "rc_mlp_create",
     "rc_mlp_destroy", "rc_mlp_n_params", "rc_mlp_set_params", "rc_mlp_get_params",
@@ -159,6 +159,8 @@ def load():
     L.rc_plan_set_march.restype = ctypes.c_int
     L.rc_plan_get_march.argtypes = [_vp, _ip]
     L.rc_plan_get_march.restype = ctypes.c_int
+    L.rc_plan_get_march_cascades.argtypes = [_vp, ctypes.POINTER(ctypes.c_uint)]
+    L.rc_plan_get_march_cascades.restype = ctypes.c_int
     L.rc_plan_autotune.argtypes = [_vp, _vp, _vp, ctypes.c_int, _vp, _vp, _ip, _ip]
     L.rc_plan_autotune.restype = ctypes.c_int
     _pp = ctypes.POINTER(_vp)
@@ -353,7 +355,13 @@ class Plan:
         check(load().rc_plan_get_lane_layout(self._h, ctypes.byref(a), ctypes.byref(b)))
         return a.value, b.value
 
-    MARCH_LANE_GROUP, MARCH_SHARED_DDA, MARCH_SHARED_DDA_ALL = 0, 1, 2
+    MARCH_LANE_GROUP, MARCH_SHARED_DDA, MARCH_SHARED_DDA_ALL, MARCH_TUNED = 0, 1, 2, 3
+
+    def march_cascades(self):
+        """rc_plan_get_march_cascades: the cascades that take the shared-DDA march."""
+        m = ctypes.c_uint()
+        check(load().rc_plan_get_march_cascades(self._h, ctypes.byref(m)))
+        return [i for i in range(self.n_cascades) if (m.value >> i) & 1]
 
     def set_march(self, mode: int):
         """rc_plan_set_march: 0 lane-group DDA everywhere, 1 shared DDA on the short cascades

@@ -164,3 +164,23 @@ def test_uneven_domain_workload_full_size_sampled():
     torch.cuda.synchronize()
     assert torch.equal(J_single, Js[big]), float((J_single - Js[big]).abs().max())
     batch.close()
+
+
+def test_plan_autotune_chooses_the_march_per_cascade():
+    """rc_plan_autotune times every cascade with both marches and keeps the faster one per
+    cascade (RC_MARCH_TUNED); the choice changes timing only, so J is bit-identical to the
+    default plan's."""
+    rcx = _rcx()
+    chi, eta = W.grf_fields(256, 32)
+    dchi, deta = torch.from_numpy(chi).cuda(), torch.from_numpy(eta).cuda()
+    ref = rcx.Plan(256, 256, 7).formal_solve(dchi, deta).cpu()
+    plan = rcx.Plan(256, 256, 7)
+    J = torch.empty_like(dchi)
+    lb, vl = plan.autotune(dchi, deta, J)
+    if (lb, vl) == (16, 4):
+        assert plan.march() == rcx.Plan.MARCH_TUNED
+        assert set(plan.march_cascades()) <= set(range(1, 7))
+    J2 = plan.formal_solve(dchi, deta).cpu()
+    assert torch.equal(J2, ref) or (lb, vl) != (16, 4)
+    if (lb, vl) != (16, 4):      # another layout: same results within the parity tolerance
+        assert float(((J2 - ref).abs() / ref.abs().clamp_min(1e-30)).max()) < 1e-5

@@ -236,6 +236,10 @@ def run_ours(args):
                     "shared-dda-all": rcx.Plan.MARCH_SHARED_DDA_ALL}[args.march])
     plan.reserve(n_lambda)
     stream = torch.cuda.current_stream()
+    tuned = None
+    if args.autotune:   # lane layout, then the march per cascade, by timing these inputs
+        lb, vl = plan.autotune(chi, eta, J)
+        tuned = {"lane_layout": [lb, vl], "shared_dda_cascades": plan.march_cascades()}
 
     for _ in range(args.warmup):
         plan.formal_solve(chi, eta, J)
@@ -326,6 +330,7 @@ def run_ours(args):
     khash = _kernel_hash()
     # the ncu summary was taken on the headline configuration only (its kernels and crossings)
     headline = ((n_side, n_lambda, n_casc) == (N_SIDE, N_LAMBDA, N_CASC) and not args.bilinear_fix
+                and not args.autotune
                 and args.n_incl == 1 and args.precision == "f32" and args.march == "shared-dda"
                 and args.lambda_block in (0, 16) and args.lambda_per_lane in (0, 4))
     traffic = _ncu_traffic(khash) if headline else None
@@ -397,7 +402,7 @@ def run_ours(args):
                    "n_lambda_per_gpu": n_lambda, "n_cascades": n_casc, "dirs0": 4, "branching": 4,
                    "interval0": 1.0, "storage": args.precision,
                    "bilinear_fix": bool(args.bilinear_fix), "n_incl": args.n_incl,
-                   "march": args.march,
+                   "march": args.march, "autotuned": tuned,
                    "lambda_block": args.lambda_block or 16,
                    "lambda_per_lane": args.lambda_per_lane or min(args.lambda_block or 16, 4),
                    "l2": (f"inputs (chi+eta {2 * n_lambda * n_side * n_side * 4 / 1e6:.0f} MB per GPU) "
@@ -910,6 +915,8 @@ def main():
     ap.add_argument("--n-lambda", type=int, default=N_LAMBDA, help="wavelengths per GPU")
     ap.add_argument("--n-cascades", type=int, default=N_CASC)
     ap.add_argument("--precision", default="f32", choices=["f32", "f16", "bf16"])
+    ap.add_argument("--autotune", action="store_true",
+                    help="formal solution: rc_plan_autotune before timing (layout, march per cascade)")
     ap.add_argument("--march", choices=["shared-dda", "lane-group", "shared-dda-all"],
                     default="shared-dda",
                     help="cascades >= 1: shared-DDA march on the short cascades (default), "

@@ -155,8 +155,9 @@ rc_status rc_formal_solve_host(rc_plan_t plan, const float* chi_host, const floa
                                int n_lambda, float* J_host, float* alo_host);
 
 /*
- * rc_formal_solve_host_async -- rc_formal_solve_host without the wait at the end: the copies
- * and solves are enqueued on the plan's three streams and the call returns.  Consecutive calls
+ * rc_formal_solve_host_async -- rc_formal_solve_host without the wait at the end (a
+ * deployment variant with no counterpart in the paper; the solve itself is rc_formal_solve's):
+ * the copies and solves are enqueued on the plan's three streams and the call returns.  Consecutive calls
  * on one plan pipeline: a call's first chunk is copied in while the previous call's last chunk
  * is solved, and the previous call's last J is copied out while this call's first chunk is
  * solved (the staging buffers alternate across calls).  The host buffers of a call must stay

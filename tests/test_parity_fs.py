@@ -451,3 +451,22 @@ def test_pipelined_host_solves_equal_blocking_ones():
         J_ref, alo_ref = plan.formal_solve_host(chi, eta, want_alo=True)
         np.testing.assert_array_equal(J, J_ref)
         np.testing.assert_array_equal(alo, alo_ref)
+
+
+def test_march_modes_agree_at_full_size():
+    """The headline grid (1024^2, 8 cascades, cascade 5 strip-split automatically) with 32
+    wavelengths (two 16-wavelength blocks): the lane-group march, the default (shared DDA on
+    the short cascades) and the shared DDA everywhere (its strip kernels included) give the
+    same J bit for bit."""
+    rcx = _rcx()
+    from paper_2408_14425_b300 import workloads
+    chi, eta = workloads.grf_fields(1024, 32)
+    dchi, deta = torch.from_numpy(chi).cuda(), torch.from_numpy(eta).cuda()
+    out = []
+    for mode in (rcx.Plan.MARCH_LANE_GROUP, rcx.Plan.MARCH_SHARED_DDA,
+                 rcx.Plan.MARCH_SHARED_DDA_ALL):
+        p = rcx.Plan(1024, 1024, 8)
+        p.set_march(mode)
+        out.append(p.formal_solve(dchi, deta).cpu())
+        p.close()
+    assert torch.equal(out[0], out[1]) and torch.equal(out[0], out[2])

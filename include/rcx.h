@@ -160,7 +160,8 @@ rc_status rc_formal_solve_host(rc_plan_t plan, const float* chi_host, const floa
  * the copies and solves are enqueued on the plan's three streams and the call returns.  Consecutive calls
  * on one plan pipeline: a call's first chunk is copied in while the previous call's last chunk
  * is solved, and the previous call's last J is copied out while this call's first chunk is
- * solved (the staging buffers alternate across calls).  The host buffers of a call must stay
+ * solved (the staging buffers alternate across calls); chunks are whole wavelength blocks of
+ * up to 64 wavelengths (one solve per call at 64 wavelengths and 16 per block).  The host buffers of a call must stay
  * valid, and chi / eta unmodified, until the call has completed: after rc_plan_wait, or after
  * a later rc_formal_solve_host on the same plan returns.  Until then the plan must not be used
  * by other calls on other streams (rc_formal_solve and friends share its scratch).

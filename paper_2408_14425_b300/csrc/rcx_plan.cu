@@ -1001,20 +1001,27 @@ rc_status rc_formal_solve_mali(rc_plan_t p, const float* chi, const float* eta, 
 
 // Enqueues a host-buffer solve on the plan's three streams without waiting for it.
 static rc_status enqueue_host_solve(rc_plan_t p, const float* chi_h, const float* eta_h,
-                                    int n_lambda, float* J_h, float* alo_h, const char* who) {
+                                    int n_lambda, float* J_h, float* alo_h, bool pipelined,
+                                    const char* who) {
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, (std::string(who) + ": pending CUDA error").c_str());
 
-    // Chunks of whole lambda blocks; chunk c's copies overlap chunk c-1's solve.  The first
-    // chunk (whose copy in nothing hides) and the last (whose copy out nothing hides) are
-    // the small unit of about 16 wavelengths; the ones between are twice that, so fewer
-    // solves (fewer launch tails) cover the middle.
+    // Chunks of whole lambda blocks; chunk c's copies overlap chunk c-1's solve.  In a
+    // blocking call the first chunk (whose copy in nothing hides) and the last (whose copy
+    // out nothing hides) are the small unit of about 16 wavelengths; the ones between are
+    // twice that, so fewer solves (fewer launch tails) cover the middle.  Pipelined calls
+    // hide those copies behind the neighbouring calls' solves instead, so they take chunks of
+    // up to four units (one solve per 64 wavelengths).
     const size_t ncell = (size_t)p->nx * p->nz;
     const int LB = p->LB;
     const int unit = std::max(LB, ((16 + LB - 1) / LB) * LB);
     std::vector<int> bounds{0};                                // chunk c: [bounds[c], bounds[c+1])
     while (bounds.back() < n_lambda) {
         const int l0 = bounds.back(), left = n_lambda - l0;
+        if (pipelined) {
+            bounds.push_back(l0 + std::min(4 * unit, left));
+            continue;
+        }
         // middle chunks: whole blocks, leaving at least one unit for the last chunk
         const int mid = std::min(2 * unit, (left - unit) / LB * LB);
         bounds.push_back(l0 + ((l0 == 0 || mid <= unit) ? std::min(unit, left) : mid));
@@ -1119,7 +1126,7 @@ rc_status rc_formal_solve_host(rc_plan_t p, const float* chi_h, const float* eta
     if (st != RC_OK || n_lambda == 0) return st;
     DeviceGuard dg(p->device);
     if (!dg.ok) return fail(RC_ERR_CUDA, "rc_formal_solve_host: cannot select the plan's device");
-    st = enqueue_host_solve(p, chi_h, eta_h, n_lambda, J_h, alo_h, "rc_formal_solve_host");
+    st = enqueue_host_solve(p, chi_h, eta_h, n_lambda, J_h, alo_h, false, "rc_formal_solve_host");
     const rc_status sw = wait_host_solves(p, "rc_formal_solve_host");
     return st != RC_OK ? st : sw;
 }
@@ -1131,7 +1138,8 @@ rc_status rc_formal_solve_host_async(rc_plan_t p, const float* chi_h, const floa
     if (st != RC_OK || n_lambda == 0) return st;
     DeviceGuard dg(p->device);
     if (!dg.ok) return fail(RC_ERR_CUDA, "rc_formal_solve_host_async: cannot select the plan's device");
-    return enqueue_host_solve(p, chi_h, eta_h, n_lambda, J_h, alo_h, "rc_formal_solve_host_async");
+    return enqueue_host_solve(p, chi_h, eta_h, n_lambda, J_h, alo_h, true,
+                              "rc_formal_solve_host_async");
 }
 
 rc_status rc_plan_wait(rc_plan_t p) {

@@ -825,6 +825,7 @@ static rc_status tune_march(rc_plan_t p, const float* chi, const float* eta, int
     }
     std::vector<float> best[2];
     const int modes[2] = {RC_MARCH_LANE_GROUP, RC_MARCH_SHARED_DDA_ALL};
+    const int mode_was = p->march;
     rc_status st = RC_OK;
     for (int m = 0; m < 2 && st == RC_OK; ++m) {
         p->march = modes[m];
@@ -852,7 +853,7 @@ static rc_status tune_march(rc_plan_t p, const float* chi, const float* eta, int
     }
     p->timing = timing_was;
     if (st != RC_OK) {
-        p->march = RC_MARCH_SHARED_DDA;
+        p->march = mode_was;
         return st;
     }
     p->march_tuned = 0;

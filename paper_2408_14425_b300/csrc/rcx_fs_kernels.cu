@@ -29,26 +29,26 @@
 
 #include "rcx_internal.h"
 
-// Resident CTAs per SM the cascade kernels are compiled for (register budget
-// 65536 / (256 threads x this)).  6 (40 registers) measured 7% faster than 5 (48
-// registers) on the 1024^2 x 64 x 8-cascade workload: the extra resident warps hide more
-// of the gather latency.
+// Resident CTAs per SM the cascade kernels are compiled for, in units of 8 warps per SM
+// (register budget 65536 / (32 x kWarpsPerCta threads x this)).  48 warps (40 registers)
+// measured 7% faster than 40 (48 registers) on the 1024^2 x 64 x 8-cascade workload: the
+// extra resident warps hide more of the gather latency.
 #ifndef RCX_MIN_CTAS
-#define RCX_MIN_CTAS 6
+#define RCX_MIN_CTAS (48 / RCX_WARPS_PER_CTA)
 #endif
 // With 8 wavelengths per lane the field data in flight alone takes 16 registers: a 40-register
 // budget spills inside the march loop, so those instantiations get a budget of their own
-// (4 CTAs/SM: 676 slices/s at 1024^2 x 64, 565 at 5 CTAs/SM with spills, 803 with 4 per lane).
+// (32 warps/SM: 676 slices/s at 1024^2 x 64, 565 at 40 warps with spills, 803 with 4 per lane).
 #ifndef RCX_MIN_CTAS_VL8
-#define RCX_MIN_CTAS_VL8 4
+#define RCX_MIN_CTAS_VL8 (32 / RCX_WARPS_PER_CTA)
 #endif
-// Cascade 0 for J alone (no operator outputs, dense): 4 CTAs/SM measured 0.98 ms per 1024^2
-// 64-wavelength step against 1.03 ms at 3.
+// Cascade 0 for J alone (no operator outputs, dense): 32 warps/SM measured 0.98 ms per 1024^2
+// 64-wavelength step against 1.03 ms at 24.
 #ifndef RCX_MIN_CTAS_L0J
-#define RCX_MIN_CTAS_L0J 4
+#define RCX_MIN_CTAS_L0J (32 / RCX_WARPS_PER_CTA)
 #endif
 #ifndef RCX_MIN_CTAS_L0
-#define RCX_MIN_CTAS_L0 3
+#define RCX_MIN_CTAS_L0 (24 / RCX_WARPS_PER_CTA)
 #endif
 
 namespace rcx {

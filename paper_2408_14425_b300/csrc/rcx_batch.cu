@@ -83,8 +83,8 @@ rc_status build(rc_batch_s* b, bool first_block_only = false) {
         if (st != RC_OK) return st;
     }
     // domains that fill the GPU alone: every live cascade has kSoloWaves waves of CTAs (the
-    // march kernels keep up to 6 CTAs on an SM)
-    constexpr int kSoloWaves = 4, kCtasPerSm = 6;
+    // march kernels keep up to 48 warps on an SM)
+    constexpr int kSoloWaves = 4, kCtasPerSm = 48 / rcx::kWarpsPerCta;
     const int G_rays = 32 / (LB / b->VL) * rcx::kWarpsPerCta;
     int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device);

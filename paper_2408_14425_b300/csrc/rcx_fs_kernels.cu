@@ -29,10 +29,10 @@
 
 #include "rcx_internal.h"
 
-// Resident CTAs per SM the cascade kernels are compiled for, in units of 8 warps per SM
-// (register budget 65536 / (32 x kWarpsPerCta threads x this)).  48 warps (40 registers)
-// measured 7% faster than 40 (48 registers) on the 1024^2 x 64 x 8-cascade workload: the
-// extra resident warps hide more of the gather latency.
+// Resident CTAs per SM the cascade kernels are compiled for (register budget
+// 65536 / (32 x kWarpsPerCta threads x this)), set for 48 warps per SM.  48 warps (40
+// registers) measured 7% faster than 40 (48 registers) on the 1024^2 x 64 x 8-cascade
+// workload: the extra resident warps hide more of the gather latency.
 #ifndef RCX_MIN_CTAS
 #define RCX_MIN_CTAS (48 / RCX_WARPS_PER_CTA)
 #endif

@@ -271,6 +271,23 @@ rc_status rc_plan_get_march(rc_plan_t plan, int* mode);
 rc_status rc_plan_get_march_cascades(rc_plan_t plan, unsigned* mask);
 
 /*
+ * The highest launched cascade has no cascade above it (those above lie in free space,
+ * Sec. 3.4), so a ray whose interval misses the domain has R = 0 there.  At creation a
+ * plan lists the CTAs of that cascade holding a ray whose interval comes within one voxel
+ * of the box (an FP64 test, conservative against the FP32 march); when the list leaves
+ * out at least half of them, each solve clears the cascade's merged intervals and marches
+ * the listed CTAs alone.  The result is bit-identical to marching every CTA.  The list
+ * serves the default lane layout (16 wavelengths per ray, 4 per lane) with the lane-group
+ * march on a dense plan without the bilinear fix; any other solve marches every CTA.
+ * rc_plan_set_top_list(plan, 0) turns it off, (plan, 1) back on (the default).
+ * rc_plan_get_top_list reports the cascade (-1: no list), the listed CTAs and the CTAs of
+ * that cascade (any pointer may be NULL).  Errors: RC_ERR_ARG.
+ */
+rc_status rc_plan_set_top_list(rc_plan_t plan, int enable);
+rc_status rc_plan_get_top_list(rc_plan_t plan, int* cascade, long long* listed,
+                               long long* total);
+
+/*
  * rc_plan_autotune -- times the formal solution of these inputs (device buffers as
  * rc_formal_solve; J is overwritten) with each candidate lane layout (16/4, 8/4, 32/4, 8/2,
  * 4/4, 4/2, 4/1, 2/2, 1/1 wavelengths per ray / per lane; blocks wider than twice n_lambda
@@ -287,7 +304,7 @@ rc_status rc_plan_autotune(rc_plan_t plan, const float* chi, const float* eta, i
  * domains are independent).  A batch binds n plans (same n_cascades, storage precision and
  * device; every plan is switched to the first plan's lane layout) to fixed device buffers
  * chi[d], eta[d], J[d] ([n_lambda[d]][nz_d][nx_d]).  A domain large enough to fill the GPU
- * on its own (at least 4 waves of CTAs, counted at 6 per SM, in every cascade that is not in
+ * on its own (at least 4 waves of CTAs, counted at 12 per SM, in every cascade that is not in
  * free space) keeps its own launch sequence, that of rc_formal_solve.  For the other
  * domains each cascade is ONE launch over a work list of CTA-sized chunks of every (domain,
  * wavelength block), sorted by estimated cost (interval length a ray can march, longest

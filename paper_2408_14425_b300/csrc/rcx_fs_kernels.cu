@@ -584,6 +584,46 @@ level_kernel(const LevelArgs A) {
     level_body<LB, VL, TS, HAS_UP, FIX, FAST>(A, blockIdx.y, blockIdx.x);
 }
 
+// The highest launched cascade (no upper) over a list of its CTAs.  A ray that misses the
+// box stores 0 there (I = 0 and nothing above it), so the CTAs left out of the list, whose
+// rays all miss, are covered by the caller clearing the output first.
+template <int LB, int VL, typename TS>
+__global__ void __launch_bounds__(kWarpsPerCta * 32, min_ctas<VL>())
+level_list_kernel(const LevelArgs A, const int* __restrict__ cta_list) {
+    level_body<LB, VL, TS, false, false, true>(A, blockIdx.y, cta_list[blockIdx.x]);
+}
+
+// flags[ray / per_cta] = 1 when the ray's interval [a, b] comes within one voxel of the box
+// [0, nx] x [0, nz].  FP64 slab test on the march's own probe centre and FP32 direction: the
+// FP32 entry test of march_interval errs by far less than the one-voxel margin, so a CTA
+// left unflagged has no ray that the march enters the box with.
+__global__ void __launch_bounds__(256) top_hits_kernel(const LevelArgs A, int per_cta,
+                                                       unsigned char* __restrict__ flags) {
+    const long long ray = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (ray >= A.rays) return;
+    const int k = (int)(ray & (A.W - 1));
+    const long long probe = ray >> A.Wshift;
+    const int px = (int)(probe % A.Px), pz = (int)(probe / A.Px);
+    const float2 d = A.dirs[k];
+    const double o[2] = {(double)(((float)px + 0.5f) * A.spacing),
+                         (double)(((float)pz + 0.5f) * A.spacing)};
+    const double w[2] = {(double)d.x, (double)d.y};
+    const double hi[2] = {(double)A.nx + 1.0, (double)A.nz + 1.0};
+    double tlo = (double)A.a, thi = (double)A.b;   // b = +inf on the plan's top cascade
+    bool miss = false;
+#pragma unroll
+    for (int ax = 0; ax < 2; ++ax) {
+        if (w[ax] == 0.0) {
+            miss |= o[ax] < -1.0 || o[ax] > hi[ax];
+        } else {
+            const double t0 = (-1.0 - o[ax]) / w[ax], t1 = (hi[ax] - o[ax]) / w[ax];
+            tlo = fmax(tlo, fmin(t0, t1));
+            thi = fmin(thi, fmax(t0, t1));
+        }
+    }
+    if (!miss && tlo <= thi) flags[ray / per_cta] = 1;
+}
+
 // ---------------------------------------------------------------------------
 // strip-split cascade: when a cascade's rays are long and one lambda block of the field
 // does not fit in L2, the domain is cut into n_strips vertical strips and the cascade runs
@@ -1111,7 +1151,17 @@ __global__ void __launch_bounds__(256) pack_kernel(const PackArgs P) {
             v[l] = make_float2(c, s);
         }
         float2* o = P.out + ((size_t)lb * P.ncell + cell) * LB;
-        if constexpr (LB % 2 == 0) {
+        if constexpr (LB % 4 == 0) {
+            // 32-byte stores (a cell's LB pairs start on a 32-byte boundary): a warp's store
+            // fills whole sectors, where 16-byte ones leave every sector half written until
+            // the next store
+#pragma unroll
+            for (int l = 0; l < LB; l += 4)
+                asm volatile("st.global.v8.f32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};"
+                             :: "l"(o + l), "f"(v[l].x), "f"(v[l].y), "f"(v[l + 1].x), "f"(v[l + 1].y),
+                                "f"(v[l + 2].x), "f"(v[l + 2].y), "f"(v[l + 3].x), "f"(v[l + 3].y)
+                             : "memory");
+        } else if constexpr (LB % 2 == 0) {
 #pragma unroll
             for (int l = 0; l < LB; l += 2)
                 reinterpret_cast<float4*>(o)[l / 2] = make_float4(v[l].x, v[l].y, v[l + 1].x, v[l + 1].y);
@@ -1588,6 +1638,34 @@ cudaError_t launch_level(int LB, int VL, int precision, bool level0, bool has_up
         case 32: return level_v<32>(VL, precision, level0, has_up, n_lblk, a, s);
     }
     return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_top_hits(const LevelArgs& a, int per_cta, unsigned char* flags,
+                            cudaStream_t s) {
+    if (a.Wshift < 0 || per_cta < 1) return cudaErrorInvalidValue;
+    if (a.rays == 0) return cudaSuccess;
+    top_hits_kernel<<<(unsigned)((a.rays + 255) / 256), 256, 0, s>>>(a, per_cta, flags);
+    return cudaGetLastError();
+}
+
+bool level_list_supported(int LB, int VL, const LevelArgs& a) {
+    return LB == 16 && VL == 4 && a.Wshift >= 0 && !a.probe_list && !a.bilinear_fix;
+}
+
+cudaError_t launch_level_list(int LB, int VL, int precision, int n_lblk, const LevelArgs& a,
+                              const int* cta_list, long long n_cta, cudaStream_t s) {
+    if (!level_list_supported(LB, VL, a) || n_cta > 0x7fffffffLL) return cudaErrorInvalidValue;
+    if (n_cta == 0) return cudaSuccess;
+    const dim3 grid((unsigned)n_cta, (unsigned)n_lblk), block(kWarpsPerCta * 32);
+    switch (precision) {
+        case RC_STORE_F32: level_list_kernel<16, 4, float><<<grid, block, 0, s>>>(a, cta_list); break;
+        case RC_STORE_F16: level_list_kernel<16, 4, __half><<<grid, block, 0, s>>>(a, cta_list); break;
+        case RC_STORE_BF16:
+            level_list_kernel<16, 4, __nv_bfloat16><<<grid, block, 0, s>>>(a, cta_list);
+            break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
 }
 
 }  // namespace rcx

@@ -147,6 +147,16 @@ cudaError_t launch_level_split(int LB, int VL, int precision, bool has_up, const
 bool level_split_supported(int LB, int VL);
 cudaError_t launch_level(int LB, int VL, int precision, bool level0, bool has_up, int n_lblk,
                          const LevelArgs& a, cudaStream_t s);
+// The highest launched cascade (no upper) over a list of CTAs: flags[c] = 1 (flags zeroed
+// by the caller) for every CTA c of per_cta consecutive rays holding a ray whose interval
+// comes within one voxel of the box (FP64, so a CTA left out has no ray that the FP32
+// march can enter the box with); then launch_level over the n_cta listed CTAs only
+// (lane-group march, a.Wshift >= 0, no sparse list, no bilinear fix).
+cudaError_t launch_top_hits(const LevelArgs& a, int per_cta, unsigned char* flags,
+                            cudaStream_t s);
+bool level_list_supported(int LB, int VL, const LevelArgs& a);
+cudaError_t launch_level_list(int LB, int VL, int precision, int n_lblk, const LevelArgs& a,
+                              const int* cta_list, long long n_cta, cudaStream_t s);
 // The shared-DDA march of a cascade >= 1 (one warp walks the DDA of 32 rays into shared
 // memory and replays it for their wavelengths): whether a launch can take it, the unsplit
 // launch and one phase of a strip-split cascade (arguments as launch_level(_split)).
@@ -211,6 +221,14 @@ struct rc_plan_s {
     std::vector<const int*> probe_list;    // per cascade
     std::vector<long long> n_flagged;      // per cascade
     std::vector<rcx::LevelGeom> lv;
+    // The highest launched cascade has no upper cascade, so a ray that misses the domain
+    // stores 0.  Where most of its CTAs hold only such rays (long intervals from probes
+    // near the edges), the solve clears its output and launches the listed CTAs alone.
+    int* d_top_list = nullptr;       // CTAs with a ray that can reach the box, ascending
+    long long top_hits = -1;         // their count; -1: no list (launch every CTA)
+    int top_cascade = -1;            // the cascade the list is for
+    int top_per_cta = 0;             // rays per CTA the list was made for
+    bool top_list_on = true;         // rc_plan_set_top_list
     std::vector<size_t> dir_off;     // offset of each cascade's table in d_dirs
     float2* d_dirs = nullptr;
     // scratch

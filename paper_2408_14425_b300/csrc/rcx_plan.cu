@@ -253,6 +253,47 @@ int live_cascades(const rc_plan_s* p) {
     return live;
 }
 
+// Rays per CTA of the lane-group march in the plan's current layout.
+int lane_group_rays_per_cta(const rc_plan_s* p) {
+    return 32 / (p->LB / p->VL) * rcx::kWarpsPerCta;
+}
+
+// Lists the CTAs of the highest launched cascade that hold a ray able to reach the box
+// (plan creation, synchronous).  The list is kept only when it leaves out at least half
+// of the CTAs; otherwise, and on any error, that cascade launches every CTA as before.
+void build_top_list(rc_plan_s* p) {
+    if (p->opt.bilinear_fix) return;
+    const int top = live_cascades(p) - 1;
+    if (top < 1) return;
+    const rcx::LevelArgs a = rcx::level_args(p, top, 0, nullptr, nullptr, nullptr, nullptr);
+    if (!rcx::level_list_supported(p->LB, p->VL, a)) return;
+    const int per_cta = lane_group_rays_per_cta(p);
+    const long long n_cta = (a.rays + per_cta - 1) / per_cta;
+    if (n_cta < 2 || n_cta > 0x7fffffffLL) return;
+    // flags, then the count in its own aligned word
+    const size_t count_at = ((size_t)n_cta + 15) & ~(size_t)15;
+    unsigned char* flags = nullptr;
+    int* list = nullptr;
+    int hits = -1;
+    cudaError_t e = cudaMalloc(&flags, count_at + sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&list, (size_t)n_cta * sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(flags, 0, count_at + sizeof(int));
+    int* d_count = reinterpret_cast<int*>(flags + count_at);
+    if (e == cudaSuccess) e = rcx::launch_top_hits(a, per_cta, flags, nullptr);
+    if (e == cudaSuccess) e = rcx::launch_compact(flags, n_cta, list, d_count, nullptr);
+    if (e == cudaSuccess) e = cudaMemcpy(&hits, d_count, sizeof(int), cudaMemcpyDeviceToHost);
+    cudaFree(flags);
+    if (e != cudaSuccess || hits < 0 || 2LL * hits > n_cta) {
+        cudaFree(list);
+        cudaGetLastError();
+        return;
+    }
+    p->d_top_list = list;
+    p->top_hits = hits;
+    p->top_cascade = top;
+    p->top_per_cta = per_cta;
+}
+
 rc_status solve_device(rc_plan_s* p, const float* chi, const float* eta, int n_lambda,
                        float* J, float* alo, cudaStream_t s, float* J_eff = nullptr,
                        float* alo_c = nullptr) {
@@ -354,6 +395,18 @@ rc_status solve_device(rc_plan_s* p, const float* chi, const float* eta, int n_l
                     if (e != cudaSuccess) return cuda_fail(e, "cascade launch (strips)");
                     ++launches;
                 }
+        } else if (!sdda && !has_up && p->top_list_on && i == p->top_cascade && p->top_hits >= 0 &&
+                   !p->sparse &&
+                   p->top_per_cta == lane_group_rays_per_cta(p) &&
+                   rcx::level_list_supported(LB, p->VL, a)) {
+            // the CTAs whose rays all miss the box would store zeros: clear, then march the rest
+            const size_t esz = p->opt.precision == RC_STORE_F32 ? 4 : 2;   // FP32, or FP16/BF16
+            if ((e = cudaMemsetAsync(a.R_out, 0, (size_t)n_lblk * a.R_out_lstride * esz, s)) != cudaSuccess)
+                return cuda_fail(e, "memset");
+            e = rcx::launch_level_list(LB, p->VL, p->opt.precision, n_lblk, a, p->d_top_list,
+                                       p->top_hits, s);
+            if (e != cudaSuccess) return cuda_fail(e, "cascade launch (listed CTAs)");
+            if (p->top_hits > 0) ++launches;
         } else {
             e = sdda ? rcx::launch_level_sdda(LB, p->VL, p->opt.precision, has_up, n_lblk, a, s)
                      : rcx::launch_level(LB, p->VL, p->opt.precision, i == 0, has_up, n_lblk, a, s);
@@ -598,6 +651,7 @@ rc_status rc_plan(const rc_grid* grid, int n_cascades, int dirs0, int branching,
         return e == cudaErrorMemoryAllocation ? fail(RC_ERR_OOM, "rc_plan: direction table allocation failed")
                                               : cuda_fail(e, "rc_plan: direction table upload");
     }
+    build_top_list(p);
     *out = p;
     return RC_OK;
 }
@@ -608,6 +662,7 @@ void rc_plan_destroy(rc_plan_t p) {
     cudaDeviceSynchronize();
     free_scratch(p);
     cudaFree(p->d_dirs);
+    cudaFree(p->d_top_list);
     cudaFree(p->d_incl);
     cudaFree(p->d_vout);
     cudaFree(p->d_active);
@@ -792,6 +847,23 @@ rc_status rc_plan_get_march_cascades(rc_plan_t p, unsigned* mask) {
         const rcx::LevelArgs a = rcx::level_args(p, i, 1, nullptr, nullptr, nullptr, nullptr);
         if (use_shared_dda(p, i, a)) *mask |= 1u << i;
     }
+    return RC_OK;
+}
+
+rc_status rc_plan_set_top_list(rc_plan_t p, int enable) {
+    if (!p) return fail(RC_ERR_ARG, "rc_plan_set_top_list: plan is NULL");
+    if (enable != 0 && enable != 1) return fail(RC_ERR_ARG, "rc_plan_set_top_list: enable must be 0 or 1");
+    p->top_list_on = enable != 0;
+    return RC_OK;
+}
+
+rc_status rc_plan_get_top_list(rc_plan_t p, int* cascade, long long* listed, long long* total) {
+    if (!p) return fail(RC_ERR_ARG, "rc_plan_get_top_list: plan is NULL");
+    const bool has = p->top_hits >= 0;
+    if (cascade) *cascade = has ? p->top_cascade : -1;
+    if (listed) *listed = has ? p->top_hits : 0;
+    if (total)
+        *total = has ? (p->lv[p->top_cascade].rays() + p->top_per_cta - 1) / p->top_per_cta : 0;
     return RC_OK;
 }
 

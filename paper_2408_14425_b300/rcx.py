@@ -30,6 +30,7 @@ EXPORTS = [
     "rc_emis_opac", "rc_stat_eq", "rc_nlte_solve", "rc_plan_set_lane_layout",
     "rc_plan_set_march", "rc_plan_get_march", "rc_line_integrals", "rc_stat_eq_integrals",
     "rc_formal_solve_host_async", "rc_plan_wait", "rc_plan_get_march_cascades",
+    "rc_plan_set_top_list", "rc_plan_get_top_list",
     "rc_plan_get_lane_layout", "rc_plan_autotune", "rc_batch_create", "rc_batch_run",
     "rc_batch_info", "rc_batch_destroy", "rc_formal_solve_batched", "rc_mlp_create",
     "rc_mlp_destroy", "rc_mlp_n_params", "rc_mlp_set_params", "rc_mlp_get_params",
@@ -161,6 +162,11 @@ def load():
     L.rc_plan_get_march.restype = ctypes.c_int
     L.rc_plan_get_march_cascades.argtypes = [_vp, ctypes.POINTER(ctypes.c_uint)]
     L.rc_plan_get_march_cascades.restype = ctypes.c_int
+    L.rc_plan_set_top_list.argtypes = [_vp, ctypes.c_int]
+    L.rc_plan_set_top_list.restype = ctypes.c_int
+    L.rc_plan_get_top_list.argtypes = [_vp, _ip, ctypes.POINTER(ctypes.c_longlong),
+                                       ctypes.POINTER(ctypes.c_longlong)]
+    L.rc_plan_get_top_list.restype = ctypes.c_int
     L.rc_plan_autotune.argtypes = [_vp, _vp, _vp, ctypes.c_int, _vp, _vp, _ip, _ip]
     L.rc_plan_autotune.restype = ctypes.c_int
     _pp = ctypes.POINTER(_vp)
@@ -372,6 +378,17 @@ class Plan:
         m = ctypes.c_int()
         check(load().rc_plan_get_march(self._h, ctypes.byref(m)))
         return m.value
+
+    def set_top_list(self, enable: bool):
+        """rc_plan_set_top_list: march only the listed CTAs of the highest launched cascade
+        (default) or every CTA."""
+        check(load().rc_plan_set_top_list(self._h, 1 if enable else 0))
+
+    def top_list(self):
+        """rc_plan_get_top_list: (cascade or -1, listed CTAs, CTAs of that cascade)."""
+        c, n, t = ctypes.c_int(), ctypes.c_longlong(), ctypes.c_longlong()
+        check(load().rc_plan_get_top_list(self._h, ctypes.byref(c), ctypes.byref(n), ctypes.byref(t)))
+        return c.value, n.value, t.value
 
     def autotune(self, chi, eta, J, stream=None):
         """rc_plan_autotune: keep the fastest lane layout for these inputs; returns it."""

@@ -87,6 +87,12 @@ def test_march_mode_setter_rejects_bad_arguments(lib):
     assert lib.rc_plan_get_march(None, None) == -1
 
 
+def test_top_list_calls_reject_a_null_plan(lib):
+    assert lib.rc_plan_set_top_list(None, 1) == -1
+    assert lib.rc_plan_get_top_list(None, None, None, None) == -1
+    assert b"plan is NULL" in lib.rc_last_error()
+
+
 def test_new_entry_points_reject_null_arguments(lib):
     """The pipelined host solve, its wait and the two halves of the statistical equilibrium
     return RC_ERR_ARG on NULL handles before any device work."""

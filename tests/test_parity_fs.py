@@ -470,3 +470,41 @@ def test_march_modes_agree_at_full_size():
         out.append(p.formal_solve(dchi, deta).cpu())
         p.close()
     assert torch.equal(out[0], out[1]) and torch.equal(out[0], out[2])
+
+
+@pytest.mark.parametrize("nx,nz,C,prec,nl", [
+    (1024, 1024, 8, "f32", 16), (1100, 900, 8, "bf16", 16), (300, 260, 6, "f16", 33),
+    (280, 280, 6, "f32", 5)])
+def test_top_cascade_over_listed_ctas_equals_every_cta(nx, nz, C, prec, nl):
+    """The highest launched cascade marches only the CTAs with a ray that can reach the box
+    (the others store R = 0 through a cleared buffer).  J and the operator outputs equal
+    those of marching every CTA bit for bit: at the headline grid (cascade 6 of 8), on a
+    ragged grid whose top probes sit outside the domain, and where the top cascade is the
+    plan's last one (b = inf), with 16-bit storage and a partial wavelength block."""
+    rcx = _rcx()
+    rng = np.random.default_rng(nx * 3 + nz)
+    chi = (10 ** rng.uniform(-4, 1.5, (nl, nz, nx))).astype(np.float32)
+    eta = (chi * 10 ** rng.uniform(-1, 1, chi.shape)).astype(np.float32)
+    dchi, deta = torch.from_numpy(chi).cuda(), torch.from_numpy(eta).cuda()
+    p = rcx.Plan(nx, nz, C, precision=prec)
+    top, listed, total = p.top_list()
+    assert top >= 1 and 0 <= 2 * listed <= total, (top, listed, total)
+    with_list = [t.cpu() for t in p.formal_solve_mali(dchi, deta)]
+    p.set_top_list(False)
+    every = [t.cpu() for t in p.formal_solve_mali(dchi, deta)]
+    p.set_top_list(True)
+    again = [t.cpu() for t in p.formal_solve_mali(dchi, deta)]
+    p.close()
+    for a, b, c in zip(with_list, every, again):
+        assert torch.equal(a, b), f"max abs diff {(a - b).abs().max().item():.3e}"
+        assert torch.equal(a, c)
+
+
+def test_no_top_list_where_most_top_rays_reach_the_box():
+    """200^2 with 6 cascades: cascade 5 starts beyond every probe's farthest corner, so the
+    top launched cascade is 4, whose rays mostly cross the domain: no list is kept and the
+    solve marches every CTA (the 1e-3 oracle parity of that plan is the ragged-shape test)."""
+    rcx = _rcx()
+    p = rcx.Plan(200, 200, 6)
+    assert p.top_list() == (-1, 0, 0)
+    p.close()

@@ -1127,47 +1127,65 @@ emergent_kernel(const EmergentArgs A) {
 // With n_incl > 1 the packed wavelengths are virtual: l' = l n_incl + j carries the
 // wavelength l with the opacity scaled by the inclination's 1/sqrt(1 - mu_j^2) (Sec. 3.1:
 // same x-z projection, longer path per projected length; S is unchanged).
+// A cell's LB wavelengths are split over kPackThreads<LB> neighbouring threads (8 each), so
+// a thread holds 8 pairs and more CTAs are resident to keep loads in flight.
+template <int LB>
+constexpr int kPackThreads = LB >= 8 ? LB / 8 : 1;
+
 template <int LB>
 __global__ void __launch_bounds__(256) pack_kernel(const PackArgs P) {
-    const long long cell = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    constexpr int TPC = kPackThreads<LB>, PL = LB / TPC;   // threads per cell, pairs per thread
+    const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long cell = g / TPC;
+    const int part = (int)(g % TPC);
     const int lb = blockIdx.y;
     float smax = 0.0f;
     if (cell < P.ncell) {
-        float2 v[LB];
+        // every load of this thread first (2 PL independent requests in flight), then the
+        // arithmetic: the divisions' slow-path branches would otherwise hold each
+        // wavelength's loads back until the previous one is done
+        const bool cell_on = !P.active || P.active[cell];
+        const int l0 = lb * LB + part * PL;                 // first (virtual) wavelength
+        float chi[PL], eta[PL];
 #pragma unroll
-        for (int l = 0; l < LB; ++l) {
-            const int vlam = lb * LB + l;
+        for (int l = 0; l < PL; ++l) {
+            const int lam = (l0 + l) / P.n_incl;
+            const bool on = cell_on && lam < P.n_lambda;
+            chi[l] = on ? __ldg(P.chi + (size_t)lam * P.ncell + cell) : 0.0f;
+            eta[l] = on ? __ldg(P.eta + (size_t)lam * P.ncell + cell) : 0.0f;
+        }
+        float2 v[PL];
+#pragma unroll
+        for (int l = 0; l < PL; ++l) {
+            const int vlam = l0 + l;
             const int lam = vlam / P.n_incl;
             float c = 0.0f, s = 0.0f;
-            if (lam < P.n_lambda && (!P.active || P.active[cell])) {
-                const float chi = __ldg(P.chi + (size_t)lam * P.ncell + cell);
-                const float eta = __ldg(P.eta + (size_t)lam * P.ncell + cell);
-                const float cv = fmaxf(chi * P.voxel, kChiFloor);
-                s = (eta * P.voxel) / cv;
+            if (cell_on && lam < P.n_lambda) {
+                const float cv = fmaxf(chi[l] * P.voxel, kChiFloor);
+                s = (eta[l] * P.voxel) / cv;
                 c = cv * kLog2e;
                 if (P.incl_r) c *= P.incl_r[vlam - lam * P.n_incl];
                 smax = fmaxf(smax, s);
             }
             v[l] = make_float2(c, s);
         }
-        float2* o = P.out + ((size_t)lb * P.ncell + cell) * LB;
-        if constexpr (LB % 4 == 0) {
-            // 32-byte stores (a cell's LB pairs start on a 32-byte boundary): a warp's store
-            // fills whole sectors, where 16-byte ones leave every sector half written until
-            // the next store
+        float2* o = P.out + ((size_t)lb * P.ncell + cell) * LB + part * PL;
+        if constexpr (PL % 4 == 0) {
+            // 32-byte stores (the thread's pairs start on a 32-byte boundary): a warp's
+            // stores fill whole sectors of consecutive cells
 #pragma unroll
-            for (int l = 0; l < LB; l += 4)
+            for (int l = 0; l < PL; l += 4)
                 asm volatile("st.global.v8.f32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};"
                              :: "l"(o + l), "f"(v[l].x), "f"(v[l].y), "f"(v[l + 1].x), "f"(v[l + 1].y),
                                 "f"(v[l + 2].x), "f"(v[l + 2].y), "f"(v[l + 3].x), "f"(v[l + 3].y)
                              : "memory");
-        } else if constexpr (LB % 2 == 0) {
+        } else if constexpr (PL % 2 == 0) {
 #pragma unroll
-            for (int l = 0; l < LB; l += 2)
+            for (int l = 0; l < PL; l += 2)
                 reinterpret_cast<float4*>(o)[l / 2] = make_float4(v[l].x, v[l].y, v[l + 1].x, v[l + 1].y);
         } else {
 #pragma unroll
-            for (int l = 0; l < LB; ++l) o[l] = v[l];
+            for (int l = 0; l < PL; ++l) o[l] = v[l];
         }
     }
     if (P.smax_bits) {
@@ -1308,7 +1326,7 @@ __global__ void scales_kernel(int n, const unsigned int* smax_bits, float* scale
 // ---------------------------------------------------------------------------
 template <int LB>
 static cudaError_t pack_t(int n_lblk, const PackArgs& a, cudaStream_t s) {
-    dim3 grid((unsigned)((a.ncell + 255) / 256), (unsigned)n_lblk);
+    dim3 grid((unsigned)((a.ncell * kPackThreads<LB> + 255) / 256), (unsigned)n_lblk);
     pack_kernel<LB><<<grid, 256, 0, s>>>(a);
     return cudaGetLastError();
 }

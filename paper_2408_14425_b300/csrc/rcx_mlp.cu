@@ -255,7 +255,7 @@ struct TcSmem {
     alignas(1024) unsigned char b[TC_SMEM_B];
     float w1[NH * NI], b1[NH], b2[NH], w3[NO * NH], b3[NO];
     float mean[NI], istd[NI];
-    float h2[TILE * LD];
+    float part[2][TILE][NO];   // output layer over each half of h2's columns
     alignas(8) unsigned long long mbar;
     unsigned tmem_base;
 };
@@ -340,24 +340,42 @@ mlp_forward_tc_kernel(const float* __restrict__ wbf, const float* __restrict__ n
         S.mean[tid] = norm[tid];
         S.istd[tid] = 1.0f / norm[NI + tid];
     }
-    // W2 [out n][in k] is already K-major for D[m][n] = sum_k A[m][k] B[n][k]
-    for (int i = tid; i < NH * NH; i += THREADS) {
-        const int n = i / NH, k = i % NH;
-        *reinterpret_cast<__nv_bfloat16*>(S.b + core_offset(n, k)) = __float2bfloat16_rn(wbf[OFF_W2 + i]);
+    // W2 [out n][in k] is already K-major for D[m][n] = sum_k A[m][k] B[n][k]; four
+    // consecutive k of a row share one 8-byte row of a core matrix
+    for (int i = tid; i < NH * NH / 4; i += THREADS) {
+        const int n = (4 * i) / NH, k = (4 * i) % NH;
+        const float* w = wbf + OFF_W2 + 4 * i;
+        const __nv_bfloat162 lo = __floats2bfloat162_rn(w[0], w[1]);
+        const __nv_bfloat162 hi = __floats2bfloat162_rn(w[2], w[3]);
+        *reinterpret_cast<uint2*>(S.b + core_offset(n, k)) =
+            make_uint2(*reinterpret_cast<const unsigned*>(&lo), *reinterpret_cast<const unsigned*>(&hi));
     }
     __syncthreads();
-    // h1 = tanh(W1 xn + b1) as bf16 into the A operand
-    for (int i = tid; i < TILE * NH; i += THREADS) {
-        const int r = i / NH, o = i % NH;
-        float a = 0.0f;
-        if (r < nvalid) {
-            a = S.b1[o];
+    // h1 = tanh(W1 xn + b1) as bf16 into the A operand: two threads per sample, 32 outputs
+    // each, the sample's standardised inputs computed once
+    {
+        static_assert(THREADS == 2 * TILE, "two threads per sample row");
+        const int r = tid >> 1, obase = (tid & 1) * (NH / 2);
+        const bool rv = r < nvalid;
+        float xn[NI];
 #pragma unroll
-            for (int f = 0; f < NI; ++f)
-                a = fmaf(S.w1[o * NI + f], (X[(s0 + r) * NI + f] - S.mean[f]) * S.istd[f], a);
-            a = tanhf(a);
+        for (int f = 0; f < NI; ++f) xn[f] = rv ? (X[(s0 + r) * NI + f] - S.mean[f]) * S.istd[f] : 0.0f;
+#pragma unroll 4
+        for (int o = obase; o < obase + NH / 2; o += 2) {
+            float h[2];
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                float a = 0.0f;
+                if (rv) {
+                    a = S.b1[o + q];
+#pragma unroll
+                    for (int f = 0; f < NI; ++f) a = fmaf(S.w1[(o + q) * NI + f], xn[f], a);
+                    a = tanhf(a);
+                }
+                h[q] = a;
+            }
+            *reinterpret_cast<__nv_bfloat162*>(S.a + core_offset(r, o)) = __floats2bfloat162_rn(h[0], h[1]);
         }
-        *reinterpret_cast<__nv_bfloat16*>(S.a + core_offset(r, o)) = __float2bfloat16_rn(a);
     }
     // generic-proxy stores -> visible to the tensor core (async proxy)
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -405,10 +423,17 @@ mlp_forward_tc_kernel(const float* __restrict__ wbf, const float* __restrict__ n
               "=r"(v[31])
             : "r"(taddr));
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        // h2 = tanh(D + b2) stays in registers: this warp's share of the 64 -> 3 layer
         const int r = rbase + lane;
+        float p[NO] = {0.0f, 0.0f, 0.0f};
 #pragma unroll
-        for (int c = 0; c < 32; ++c)
-            S.h2[r * LD + cbase + c] = tanhf(__uint_as_float(v[c]) + S.b2[cbase + c]);
+        for (int c = 0; c < 32; ++c) {
+            const float h = tanhf(__uint_as_float(v[c]) + S.b2[cbase + c]);
+#pragma unroll
+            for (int o = 0; o < NO; ++o) p[o] = fmaf(S.w3[o * NH + cbase + c], h, p[o]);
+        }
+#pragma unroll
+        for (int o = 0; o < NO; ++o) S.part[warp >> 2][r][o] = p[o];
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
@@ -430,10 +455,7 @@ mlp_forward_tc_kernel(const float* __restrict__ wbf, const float* __restrict__ n
     if (!done) return;
     for (int i = tid; i < TILE * NO; i += THREADS) {
         const int r = i / NO, o = i % NO;
-        if (r >= nvalid) continue;
-        float a = S.b3[o];
-        for (int k = 0; k < NH; ++k) a = fmaf(S.w3[o * NH + k], S.h2[r * LD + k], a);
-        Y[(s0 + r) * NO + o] = a;
+        if (r < nvalid) Y[(s0 + r) * NO + o] = S.b3[o] + S.part[0][r][o] + S.part[1][r][o];
     }
 }
 

@@ -508,3 +508,17 @@ def test_no_top_list_where_most_top_rays_reach_the_box():
     p = rcx.Plan(200, 200, 6)
     assert p.top_list() == (-1, 0, 0)
     p.close()
+
+
+def test_listed_top_cascade_matches_oracle():
+    """300 x 260 with 6 cascades: cascade 5 (the plan's last, b = inf) runs over its listed
+    CTAs, a small share of them (rays from the corner probes that still reach the domain);
+    J within 1e-3 of the oracle, 17 wavelengths (a ragged second block)."""
+    rcx = _rcx()
+    p = rcx.Plan(300, 260, 6)
+    top, listed, total = p.top_list()
+    p.close()
+    assert top == 5 and 0 < listed and 4 * listed < total, (top, listed, total)
+    chi, eta = W.grf_fields(300, 17, nz=260)
+    J = _solve(chi, eta, 6)
+    _assert_close(J, _oracle(chi, eta, 6), 1e-3, "J 300x260, listed top cascade")

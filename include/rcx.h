@@ -98,8 +98,10 @@ void rc_options_default(rc_options* opt);
  *   opt         NULL for defaults.
  * Cascade i has probes at ((k+1/2) 2^i, (m+1/2) 2^i), ceil(n/2^i) per axis, W_0 4^i directions,
  * and the interval [a_i, b_i] of interval_rule.  The plan copies its direction tables to the
- * current device (one small allocation); scratch for the solves is allocated on first use or by
- * rc_plan_reserve.  On success *out owns the plan (free with rc_plan_destroy).
+ * current device (one small allocation) and lists the CTAs of its highest launched cascade
+ * that can reach the domain (rc_plan_set_top_list: two small kernels on the default stream
+ * and a read-back, so creation is synchronous); scratch for the solves is allocated on first
+ * use or by rc_plan_reserve.  On success *out owns the plan (free with rc_plan_destroy).
  * Errors: RC_ERR_ARG (bad sizes, NULL out), RC_ERR_UNSUPPORTED (branching != 4),
  * RC_ERR_OOM, RC_ERR_CUDA.
  */

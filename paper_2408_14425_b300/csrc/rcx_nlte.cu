@@ -69,13 +69,27 @@ rc_status ncuda(cudaError_t e, const char* what) {
 // device helpers
 // ---------------------------------------------------------------------------
 
-// e^y E1(y) through the power series of E1 (Abramowitz & Stegun 5.1.11) for y < 1.
+// 1 / (k k!), the coefficient of (-y)^k in the power series of E1 (evaluated at compile time)
+__host__ __device__ constexpr double e1_coef(int k) {
+    double f = 1.0;
+    for (int i = 2; i <= k; ++i) f *= (double)i;
+    return 1.0 / ((double)k * f);
+}
+
+// sum_{k=K..N} (-y)^(k-K) / (k k!) by Horner's rule in z = -y (FMAs only: FP64 divisions are
+// an order of magnitude dearer than FMAs, and this runs for every line of every hot cell)
+template <int K, int N>
+__device__ __forceinline__ double e1_horner(double z) {
+    constexpr double c = e1_coef(K);
+    if constexpr (K == N) return c;
+    else return fma(e1_horner<K + 1, N>(z), z, c);
+}
+
+// e^y E1(y) through the power series of E1 (Abramowitz & Stegun 5.1.11) for y < 1:
+// E1(y) = -gamma - ln y - sum_{k>=1} (-y)^k / (k k!), 30 terms (the 30th is below 1e-33).
 __device__ double exp_e1_small(double y) {
-    double term = 1.0, sum = 0.0;
-    for (int k = 1; k <= 30; ++k) {
-        term *= -y / (double)k;            // (-y)^k / k!
-        sum += term / (double)k;
-    }
+    const double z = -y;
+    const double sum = z * e1_horner<1, 30>(z);
     return exp(y) * (-kEulerGamma - log(y) - sum);
 }
 
@@ -89,15 +103,24 @@ __device__ double van_regemorter_p(double y) {
 // The Gaussian exp(-(dnu_k / dD)^2) on a line's uniform grid symmetric about nu0, walked
 // from the centre outwards: with offsets u_j = (j + d) h (h = step / dD, d = 0 for an odd
 // point count, 1/2 for an even one), e_{j+1} = e_j r_j and r_{j+1} = r_j exp(-2 h^2), so
-// three exponentials per line replace one per point (FP64 exponentials are the cost of
-// these kernels); after j products the relative error is a few j ulps.  Calls f(k, e_k)
-// for every grid index k.
+// one exponential per line replaces one per point (FP64 exponentials are the cost of
+// these kernels): for an odd count r_0 = exp(-h^2) and exp(-2 h^2) = r_0^2; for an even one
+// e_0 = exp(-h^2 / 4) and r_0 = exp(-2 h^2) = e_0^8.  After j products the relative error
+// is a few j ulps.  Calls f(k, e_k) for every grid index k.
 template <class F>
 __device__ __forceinline__ void for_each_gauss(int n, double h, F&& f) {
     const bool odd = n & 1;
-    double e = odd ? 1.0 : exp(-0.25 * h * h);           // e_0 = exp(-(d h)^2)
-    double r = exp(-(odd ? 1.0 : 2.0) * h * h);           // e_1 / e_0 = exp(-(2d + 1) h^2)
-    const double q = exp(-2.0 * h * h);
+    double e, r, q;
+    if (odd) {
+        e = 1.0;                                          // e_0 = exp(0)
+        r = exp(-h * h);                                  // e_1 / e_0 = exp(-h^2)
+        q = r * r;                                        // exp(-2 h^2)
+    } else {
+        e = exp(-0.25 * h * h);                           // e_0 = exp(-(h / 2)^2)
+        const double e2 = e * e, e4 = e2 * e2;
+        r = e4 * e4;                                      // e_1 / e_0 = exp(-2 h^2)
+        q = r;
+    }
     const int hi = n / 2, lo = odd ? n / 2 : n / 2 - 1;    // the centre point(s)
     for (int j = 0; hi + j < n; ++j) {
         f(hi + j, e);
@@ -169,8 +192,11 @@ __device__ double solve_cell(const AtomDev& A, long long c, long long ncell, dou
         const double Rlu = L.Blu * Jb[li];
         const double Rul = L.A * Lc[li] + L.Bul * Jb[li];
         const double y = L.y_T / t;
-        const double Clu = nec * L.coll * van_regemorter_p(y) / sqT * exp(-y);
-        const double Cul = Clu * L.glo_gup * exp(y);
+        // detailed balance: C_ul = C_lu (g_l / g_u) e^{y}, so the common factor carries no
+        // exponential and C_ul needs none
+        const double base = nec * L.coll * van_regemorter_p(y) / sqT;
+        const double Clu = base * exp(-y);
+        const double Cul = base * L.glo_gup;
         G[L.up][L.lo] += Rlu + Clu;                  // lo -> up, per atom in lo
         G[L.lo][L.up] += Rul + Cul;                  // up -> lo, per atom in up
     }

@@ -103,6 +103,19 @@ def _kernel_hash():
     return h.hexdigest()[:16]
 
 
+def _batched_ncu_summary(kernel_hash, n_domains, layout):
+    """The committed ncu instruction count of the batched workload's step, if it was taken
+    on the current kernel source with this domain count and lane layout; else {}."""
+    p = os.path.join(ROOT, "profiles", "traffic_batched_uneven_domains.json")
+    if not os.path.exists(p):
+        return {}
+    with open(p) as f:
+        d = json.load(f)
+    ok = (d.get("kernel_source_sha256_16") == kernel_hash and d.get("n_domains") == n_domains
+          and d.get("lane_layout") == list(layout))
+    return d if ok else {}
+
+
 def _ncu_summary(kernel_hash):
     """The committed ncu summary of the march kernels, if it was taken on the current
     kernel source; else {}."""
@@ -680,7 +693,10 @@ def run_batched(args):
     plans, chis, etas, Js = [], [], [], []
     for side, nl, sb in doms:
         chi, eta = workloads.grf_fields(side, nl, seed_base=sb)
-        plans.append(rcx.Plan(side, side, 8, precision=args.precision))
+        # --lambda-block / --lambda-per-lane fix the lane layout (with --no-autotune the batch
+        # keeps it; the default lets the batch's autotuner choose)
+        plans.append(rcx.Plan(side, side, 8, precision=args.precision,
+                              lambda_block=args.lambda_block, lambda_per_lane=args.lambda_per_lane))
         chis.append(torch.from_numpy(chi).cuda())
         etas.append(torch.from_numpy(eta).cuda())
         Js.append(torch.empty_like(chis[-1]))
@@ -723,6 +739,7 @@ def run_batched(args):
     slices = sum(nl for _, nl, _ in all_doms)
     alg = 0
     have_cross = world == 1        # the byte model needs every domain's plan
+    lam_cross = 0
     for (side, nl, _), p in zip(doms if have_cross else [], plans):
         try:
             cross = _load_crossings(side, 8)
@@ -730,6 +747,7 @@ def run_batched(args):
             have_cross = False
             break
         alg += sum(_algorithmic_bytes(cross, p, nl, side)[0])
+        lam_cross += sum(cross["per_cascade"]) * nl
     peak, peak_kind = _peaks()
     line = {"metric": "RC wavelength-slices/s, batched uneven domains", "value": round(slices / (ms / 1e3), 2),
             "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -749,13 +767,29 @@ def run_batched(args):
             "cell_wavelengths_per_s": round(sum(s * s * nl for s, nl, _ in all_doms) / (ms / 1e3), 1),
             "clocks": clk}
     if have_cross:
-        line["roofline"] = {"bound": "hbm", "achieved": round(alg / (ms / 1e3) / 1e9, 1),
-                            "peak": peak, "unit": "GB/s", "frac": round(alg / (ms / 1e3) / 1e9 / peak, 4),
-                            "peak_kind": peak_kind, "traffic": None,
-                            "kernel": "whole step (graph: the launch sequences of the domains "
-                                      "that fill the GPU alone, then batched pack and cascade "
-                                      "launches over the others)",
-                            "algorithmic_bytes_per_step": alg}
+        # issue bound as for the headline: warp instructions per wavelength-crossing counted by
+        # ncu over every launch of this workload's step, on the same kernel source and layout
+        summ = _batched_ncu_summary(_kernel_hash(), len(all_doms),
+                                    [info["lambda_block"], info["lambda_per_lane"]])
+        ipc = summ.get("warp_inst_per_lambda_crossing")
+        achieved = lam_cross / (ms / 1e3)
+        gbps = alg / (ms / 1e3) / 1e9
+        line["roofline"] = {
+            "bound": "alu", "unit": "wavelength-crossings/s", "achieved": round(achieved, 1),
+            "peak": round(_issue_peak() / ipc, 1) if ipc else None,
+            "frac": round(achieved * ipc / _issue_peak(), 4) if ipc else None,
+            "traffic": None, "warp_inst_per_lambda_crossing": ipc,
+            "peak_kind": "derived: SMs x 4 warp instructions/clk x 2032 MHz (max SM clock) / "
+                         "ncu-counted warp instructions per wavelength-crossing of this step "
+                         "(profiles/traffic_batched_uneven_domains.json; null if absent or "
+                         "taken on another kernel source or layout)",
+            "kernel": "whole step (graph: the launch sequences of the domains that fill the GPU "
+                      "alone, then batched pack and cascade launches over the others)",
+            "gather_model": {"bound": "l2", "unit": "GB/s", "algorithmic_bytes_per_step": alg,
+                             "achieved": round(gbps, 1), "hbm_peak": peak,
+                             "hbm_peak_kind": peak_kind, "ratio_to_hbm": round(gbps / peak, 4),
+                             "bytes_model": "8 B per voxel crossing + merged intervals + J, "
+                                            "served by L1/L2: not an HBM fraction"}}
     print(json.dumps(line), flush=True)
 
 

@@ -251,9 +251,11 @@ __device__ __forceinline__ bool march_interval(const float2* __restrict__ F, int
     ix = min(max(ix, x0), x1 - 1);
     iz = min(max(iz, 0), nz - 1);
 
-    // face parameters: first face after entry and spacing between faces
+    // face parameters: first face after entry and spacing between faces (+inf along an axis
+    // the ray does not move on: it never crosses those faces, and their exit term never binds)
     const float fx0 = (float)(upx ? ix + 1 : ix), fz0 = (float)(upz ? iz + 1 : iz);
-    const float tfx = (fx0 - ox) * invx, tfz = (fz0 - oz) * invz;
+    const float tfx = wx != 0.0f ? (fx0 - ox) * invx : INFINITY;
+    const float tfz = wz != 0.0f ? (fz0 - oz) * invz : INFINITY;
     const float dtx = fabsf(invx), dtz = fabsf(invz);
     // exit: last face inside the domain, with the same expression as the walk
     const float kx_end = (float)(upx ? x1 - 1 - ix : ix - x0);
@@ -766,8 +768,8 @@ struct DdaWalk {
         ix = min(max(ix, x0), x1 - 1);
         iz = min(max(iz, 0), nz - 1);
         const float fx0 = (float)(upx ? ix + 1 : ix), fz0 = (float)(upz ? iz + 1 : iz);
-        tfx = (fx0 - ox) * invx;
-        tfz = (fz0 - oz) * invz;
+        tfx = wx != 0.0f ? (fx0 - ox) * invx : INFINITY;   // as in march_interval
+        tfz = wz != 0.0f ? (fz0 - oz) * invz : INFINITY;
         dtx = fabsf(invx);
         dtz = fabsf(invz);
         const float kx_end = (float)(upx ? x1 - 1 - ix : ix - x0);
@@ -1121,6 +1123,72 @@ emergent_kernel(const EmergentArgs A) {
         if (j < n_valid) A.I[(size_t)(lam0 + j) * A.n_rays + ray] = I[j];
 }
 
+// Emergent intensity without the contribution function, each ray's span inside the box cut
+// into K pieces of equal parameter length that neighbouring lane groups march at once (a
+// launch of a few ten thousand long rays otherwise holds only a few waves of warps, whose
+// tail is the longest rays).  The pieces compose front to back by Eq. 11 applied to
+// adjacent pieces, I = I_0 + T_0 (I_1 + T_1 (I_2 + ...)), through shuffles within the warp.
+template <int LB, int K>
+__global__ void __launch_bounds__(kWarpsPerCta * 32)
+emergent_pieces_kernel(const EmergentArgs A) {
+    constexpr int VL = 4;
+    constexpr int LPR = LB / VL;            // lanes per (ray, piece)
+    constexpr int GP = 32 / LPR;            // (ray, piece) groups per warp
+    static_assert(LB % VL == 0 && GP % K == 0, "whole rays per warp");
+    constexpr int RPW = GP / K;             // rays per warp
+    const int lane = threadIdx.x & 31;
+    const int grp = lane / LPR, q = lane % LPR;
+    const int rw = grp / K, piece = grp % K;
+    const long long ray = ((long long)blockIdx.x * kWarpsPerCta + (threadIdx.x >> 5)) * RPW + rw;
+    const bool valid = ray < A.n_rays;
+    const int lb = blockIdx.y;
+    const float2* F = A.field + (size_t)lb * A.ncell * LB;
+    const int lane_off = q * VL;
+    const int lam0 = lb * LB + lane_off;
+    float I[VL], T[VL], I0[VL];
+#pragma unroll
+    for (int j = 0; j < VL; ++j) {
+        I[j] = 0.0f;
+        T[j] = 1.0f;
+    }
+    if (valid) {
+        const float4 r = __ldg(reinterpret_cast<const float4*>(A.rays) + ray);
+        // the ray's span [tlo, thi] inside the box [0, nx] x [0, nz], t >= 0
+        const float invx = r.z != 0.0f ? 1.0f / r.z : 1e30f;
+        const float invz = r.w != 0.0f ? 1.0f / r.w : 1e30f;
+        const float tx0 = (0.0f - r.x) * invx, tx1 = ((float)A.nx - r.x) * invx;
+        const float tz0 = (0.0f - r.y) * invz, tz1 = ((float)A.nz - r.y) * invz;
+        const float tlo = fmaxf(0.0f, fmaxf(fminf(tx0, tx1), fminf(tz0, tz1)));
+        const float thi = fminf(fmaxf(tx0, tx1), fmaxf(tz0, tz1));
+        if (tlo < thi) {
+            const float len = (thi - tlo) / (float)K;
+            const float a = piece == 0 ? 0.0f : fmaf((float)piece, len, tlo);
+            const float b = piece == K - 1 ? INFINITY : fmaf((float)(piece + 1), len, tlo);
+            march_interval<LB, VL>(F, A.nx, A.nz, 0, A.nx, r.x, r.y, r.z, r.w, a, b, lane_off,
+                                   A.max_steps, I, T, I0);
+        }
+    }
+    // compose from the back: R = I_{K-1}; R = I_p + T_p R for p = K-2 .. 0
+    const int base = rw * K * LPR + q;
+    float R[VL];
+#pragma unroll
+    for (int j = 0; j < VL; ++j) {
+        R[j] = __shfl_sync(0xffffffffu, I[j], base + (K - 1) * LPR);
+#pragma unroll
+        for (int p = K - 2; p >= 0; --p) {
+            const float Ip = __shfl_sync(0xffffffffu, I[j], base + p * LPR);
+            const float Tp = __shfl_sync(0xffffffffu, T[j], base + p * LPR);
+            R[j] = fmaf(Tp, R[j], Ip);
+        }
+    }
+    if (valid && piece == 0) {
+        const int n_valid = max(0, min(VL, A.n_lambda - lam0));
+#pragma unroll
+        for (int j = 0; j < VL; ++j)
+            if (j < n_valid) A.I[(size_t)(lam0 + j) * A.n_rays + ray] = R[j];
+    }
+}
+
 // ---------------------------------------------------------------------------
 // packing [lambda][cell] (chi, eta) -> [lambda block][cell][LB] (chi' = chi voxel log2 e, S)
 // ---------------------------------------------------------------------------
@@ -1366,6 +1434,16 @@ template <int LB>
 static cudaError_t emergent_t(int n_lblk, const EmergentArgs& a, cudaStream_t s) {
     constexpr int VL = LB < 4 ? LB : 4;
     const long long per_cta = (long long)(32 / (LB / VL)) * kWarpsPerCta;
+    if constexpr (LB == 16) {
+        if (!a.contrib) {
+            // 4 pieces per ray: 2 rays per warp
+            constexpr int K = 4;
+            const long long rays_per_cta = (long long)(32 / (LB / 4) / K) * kWarpsPerCta;
+            const dim3 g2((unsigned)((a.n_rays + rays_per_cta - 1) / rays_per_cta), (unsigned)n_lblk);
+            emergent_pieces_kernel<LB, K><<<g2, kWarpsPerCta * 32, 0, s>>>(a);
+            return cudaGetLastError();
+        }
+    }
     dim3 grid((unsigned)((a.n_rays + per_cta - 1) / per_cta), (unsigned)n_lblk);
     if (a.contrib) emergent_kernel<LB, true><<<grid, kWarpsPerCta * 32, 0, s>>>(a);
     else emergent_kernel<LB, false><<<grid, kWarpsPerCta * 32, 0, s>>>(a);

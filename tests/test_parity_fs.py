@@ -304,6 +304,37 @@ def test_emergent_intensity_and_contribution_function(mu):
         assert C[lam].sum() == pytest.approx(I[lam].sum(), rel=1e-4, abs=0)
 
 
+@pytest.mark.parametrize("mu", [0.0, 0.5])
+def test_emergent_intensity_in_pieces(mu):
+    """Without the contribution function each ray's span in the box is marched as 4 pieces by
+    neighbouring lane groups and composed front to back (Eq. 11).  I matches the oracle and
+    the single-pass march (the contribution-function call) to FP32 rounding, for rays that
+    start outside or inside the domain, run along an axis, graze a corner or miss it, with 17
+    wavelengths (a ragged second block)."""
+    rcx = _rcx()
+    nl = 17
+    chi, eta = W.grf_fields(64, nl, nz=48)
+    rng = np.random.default_rng(9)
+    rays = [(x + 0.5, -0.5, 0.0, 1.0) for x in range(0, 64, 7)]          # along z
+    rays += [(-0.5, z + 0.25, 1.0, 0.0) for z in range(0, 48, 5)]        # along x
+    rays += [(-1.0, -1.0, 0.6, 0.8), (70.0, 60.0, -0.8, -0.6), (-5.0, 50.0, 1.0, 0.0),
+             (64.0, 0.0, 0.7071068, -0.7071068)]                         # corner, miss
+    for _ in range(60):
+        a = rng.uniform(0, 2 * np.pi)
+        rays.append((rng.uniform(-4, 68), rng.uniform(-4, 52), np.cos(a), np.sin(a)))
+    rays = np.array(rays, dtype=np.float32)
+    p = rcx.Plan(64, 48, 3)
+    dchi, deta, drays = (torch.from_numpy(x).cuda() for x in (chi, eta, rays))
+    I = p.emergent(dchi, deta, drays, mu=mu, want_contrib=False).cpu().numpy()
+    I1, _ = p.emergent(dchi, deta, drays, mu=mu, want_contrib=True)
+    I1 = I1.cpu().numpy()
+    _assert_close(I[None], I1[None], 1e-4, "pieces vs single pass")
+    for lam in (0, 8, 16):
+        I_ref = oracle.emergent(chi[lam].astype(np.float64), eta[lam].astype(np.float64),
+                                rays.astype(np.float64), mu=mu, want_contrib=False)
+        _assert_close(I[lam][None, None], I_ref[None, None], 1e-3, f"I lambda {lam}")
+
+
 @pytest.mark.parametrize("n,C,launched", [(64, 5, 4), (64, 7, 4), (1024, 8, 7), (100, 4, 4)])
 def test_free_space_cascades_are_not_launched(n, C, launched):
     """Sec. 3.4: an interval beyond the farthest box corner from every probe of its cascade

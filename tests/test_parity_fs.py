@@ -250,6 +250,30 @@ def test_sparse_matches_oracle(nx, nz, C):
     assert [int(r) // w for r, w in zip(rays, dirs)] == counts
 
 
+@pytest.mark.parametrize("nx,nz,C,nl", [(96, 70, 6, 20), (160, 128, 7, 16)])
+def test_sparse_march_equals_dense_march_on_the_masked_field(nx, nz, C, nl):
+    """A sparse plan packs inactive cells as chi' = S = 0 and marches only the flagged probes.
+    A dense plan marching the field with chi = eta = 0 outside the active set packs those
+    cells at the opacity floor with S = 0, where a step changes nothing (e^{-dtau} rounds to
+    1).  J on the active cells is bit-identical between the two, as are J_eff and
+    1 - Lambda*: the flagged probes carry every interval the active cells merge."""
+    rcx = _rcx()
+    chi, eta = W.grf_fields(nx, nl, nz=nz)
+    m = _mask(nx, nz)
+    chi0, eta0 = chi * m[None], eta * m[None]
+    sp = rcx.Plan(nx, nz, C)
+    sp.set_active(torch.from_numpy(m.astype(np.uint8)).cuda())
+    dn = rcx.Plan(nx, nz, C)
+    out_s = sp.formal_solve_mali(torch.from_numpy(chi).cuda(), torch.from_numpy(eta).cuda())
+    out_d = dn.formal_solve_mali(torch.from_numpy(chi0).cuda(), torch.from_numpy(eta0).cuda())
+    mm = torch.from_numpy(m).cuda()
+    for a, b in zip(out_s, out_d):
+        a, b = a[:, mm].cpu(), b[:, mm].cpu()
+        assert torch.equal(a, b), f"max abs diff {(a - b).abs().max().item():.3e}"
+    sp.close()
+    dn.close()
+
+
 def test_sparse_cleared_is_dense_again():
     rcx = _rcx()
     chi, eta = W.grf_fields(48, 2)

@@ -166,6 +166,14 @@ bool use_shared_dda(const rc_plan_s* p, int i, const rcx::LevelArgs& a) {
     return p->lv[i].b - p->lv[i].a <= kSdMaxInterval;
 }
 
+// A wavelength block of the packed field above RCX_SPLIT_MIN_MIB is marched in strips of
+// about RCX_STRIP_MIB each on the cascades whose intervals reach half the domain.
+#ifndef RCX_SPLIT_MIN_MIB
+#define RCX_SPLIT_MIN_MIB 96
+#endif
+#ifndef RCX_STRIP_MIB
+#define RCX_STRIP_MIB 64
+#endif
 int strips_for_impl(const rc_plan_s* p, int i) {
     if (i == 0 || p->opt.bilinear_fix || p->opt.strips == 1 ||
         !rcx::level_split_supported(p->LB, p->VL))
@@ -175,7 +183,8 @@ int strips_for_impl(const rc_plan_s* p, int i) {
     const double len = std::min(g.b, far_corner(p, i)) - g.a;   // longest piece in the domain
     if (len < 0.5 * std::max(p->nx, p->nz)) return 1;
     const double block = (double)p->nx * p->nz * p->LB * sizeof(float2);
-    constexpr double kSplitMin = 96.0 * (1 << 20), kStrip = 64.0 * (1 << 20);
+    constexpr double kSplitMin = RCX_SPLIT_MIN_MIB * double(1 << 20);
+    constexpr double kStrip = RCX_STRIP_MIB * double(1 << 20);
     if (block <= kSplitMin) return 1;
     return std::min(std::min(16, p->nx), std::max(2, (int)std::lround(block / kStrip)));
 }

@@ -287,7 +287,7 @@ void build_top_list(rc_plan_s* p) {
     cudaError_t e = cudaMalloc(&flags, count_at + sizeof(int));
     if (e == cudaSuccess) e = cudaMalloc(&list, (size_t)n_cta * sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(flags, 0, count_at + sizeof(int));
-    int* d_count = reinterpret_cast<int*>(flags + count_at);
+    int* d_count = e == cudaSuccess ? reinterpret_cast<int*>(flags + count_at) : nullptr;
     if (e == cudaSuccess) e = rcx::launch_top_hits(a, per_cta, flags, nullptr);
     if (e == cudaSuccess) e = rcx::launch_compact(flags, n_cta, list, d_count, nullptr);
     if (e == cudaSuccess) e = cudaMemcpy(&hits, d_count, sizeof(int), cudaMemcpyDeviceToHost);

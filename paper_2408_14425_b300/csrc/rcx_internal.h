@@ -18,7 +18,8 @@ namespace rcx {
 constexpr float kChiFloor = 1e-30f;
 // Warps per CTA of the march kernels.  4 (at 12 resident CTAs/SM, 40 registers) measured
 // 824-827 slices/s at 1024^2 x 64 wavelengths against 795, 793, 785, 797 and 810 with 2, 3,
-// 5, 6 and 8 (same 40 registers, 45-48 warps per SM): a CTA keeps its slot until its slowest warp ends, and smaller CTAs waste less of it.
+// 5, 6 and 8 (same 40 registers, 45-48 warps per SM): a CTA keeps its slot until its
+// slowest warp ends, and smaller CTAs waste less of it.
 #ifndef RCX_WARPS_PER_CTA
 #define RCX_WARPS_PER_CTA 4
 #endif

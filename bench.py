@@ -104,16 +104,16 @@ def _kernel_hash():
 
 
 def _batched_ncu_summary(kernel_hash, n_domains, layout):
-    """The committed ncu instruction count of the batched workload's step, if it was taken
-    on the current kernel source with this domain count and lane layout; else {}."""
+    """The committed ncu instruction count of the batched workload's step for this lane
+    layout, if it was taken on the current kernel source with this domain count; else {}."""
     p = os.path.join(ROOT, "profiles", "traffic_batched_uneven_domains.json")
     if not os.path.exists(p):
         return {}
     with open(p) as f:
         d = json.load(f)
-    ok = (d.get("kernel_source_sha256_16") == kernel_hash and d.get("n_domains") == n_domains
-          and d.get("lane_layout") == list(layout))
-    return d if ok else {}
+    if d.get("kernel_source_sha256_16") != kernel_hash or d.get("n_domains") != n_domains:
+        return {}
+    return d.get("by_lane_layout", {}).get(f"{layout[0]}x{layout[1]}", {})
 
 
 def _ncu_summary(kernel_hash):

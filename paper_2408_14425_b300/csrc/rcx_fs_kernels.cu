@@ -55,6 +55,13 @@ namespace rcx {
 
 template <int VL>
 constexpr int min_ctas() { return VL >= 8 ? RCX_MIN_CTAS_VL8 : RCX_MIN_CTAS; }
+// The strip kernel in CTAs of WPC warps, at the same warps per SM (same registers).  Strips
+// of 4 and more per cascade run in 8-warp CTAs: at 2048^2 (8 strips) cascade 5 took 349.7 ms
+// per 64-wavelength step with 8-warp CTAs against 386.8 with 4; at 1024^2 (2 strips) 4-warp
+// CTAs are faster (32.8 against 33.5 ms).
+constexpr int kSplitWideWarps = 8, kSplitWideFrom = 4;   // warps per CTA, from this many strips
+template <int VL, int WPC>
+constexpr int min_ctas_w() { return (VL >= 8 ? 32 : 48) / WPC; }
 
 // ---------------------------------------------------------------------------
 // storage of merged intervals: FP32, or FP16/BF16 with a per-block scale
@@ -638,14 +645,17 @@ __global__ void __launch_bounds__(256) top_hits_kernel(const LevelArgs A, int pe
 // ---------------------------------------------------------------------------
 // FIRST / LAST: this launch is the first / last strip (never both: at least 2 strips).
 // FAST as for level_body.
-template <int LB, int VL, typename TS, bool HAS_UP, bool FIRST, bool LAST, bool FAST>
-__global__ void __launch_bounds__(kWarpsPerCta * 32, min_ctas<VL>())
+template <int LB, int VL, typename TS, bool HAS_UP, bool FIRST, bool LAST, bool FAST, int WPC>
+__global__ void __launch_bounds__(WPC * 32, min_ctas_w<VL, WPC>())
 level_split_kernel(const LevelArgs A) {
     constexpr int LPR = LB / VL;
     constexpr int G = 32 / LPR;
+    // the merge's group-of-four sum stays within a warp (its shared-memory path is sized for
+    // kWarpsPerCta)
+    static_assert(G >= 4, "whole groups of four sibling rays per warp");
     const int lane = threadIdx.x & 31;
     const int g = lane / LPR, q = lane % LPR;
-    const long long ray = ((long long)blockIdx.x * kWarpsPerCta + (threadIdx.x >> 5)) * G + g;
+    const long long ray = ((long long)blockIdx.x * WPC + (threadIdx.x >> 5)) * G + g;
     const int lane_off = q * VL;
     const int lb = A.split_lb + (int)blockIdx.y;
     const bool valid = ray < A.rays;
@@ -1595,31 +1605,34 @@ cudaError_t launch_batched_pack(int LB, const BatchPackArgs& b, int grid, cudaSt
     return cudaGetLastError();
 }
 
-template <int LB, int VL, typename TS, bool FAST>
-static cudaError_t split_phase(bool has_up, const LevelArgs& a, dim3 grid, cudaStream_t s) {
-    const dim3 block(kWarpsPerCta * 32);
+template <int LB, int VL, typename TS, bool FAST, int WPC>
+static cudaError_t split_phase(bool has_up, const LevelArgs& a, cudaStream_t s) {
+    constexpr int G = 32 / (LB / VL);
+    const long long per_cta = (long long)G * WPC;
+    const dim3 grid((unsigned)((a.rays + per_cta - 1) / per_cta), (unsigned)a.split_nblk);
+    const dim3 block(WPC * 32);
     const bool first = a.phase == 0, last = a.phase == a.n_strips - 1;
     if (has_up) {
-        if (first) level_split_kernel<LB, VL, TS, true, true, false, FAST><<<grid, block, 0, s>>>(a);
-        else if (last) level_split_kernel<LB, VL, TS, true, false, true, FAST><<<grid, block, 0, s>>>(a);
-        else level_split_kernel<LB, VL, TS, true, false, false, FAST><<<grid, block, 0, s>>>(a);
+        if (first) level_split_kernel<LB, VL, TS, true, true, false, FAST, WPC><<<grid, block, 0, s>>>(a);
+        else if (last) level_split_kernel<LB, VL, TS, true, false, true, FAST, WPC><<<grid, block, 0, s>>>(a);
+        else level_split_kernel<LB, VL, TS, true, false, false, FAST, WPC><<<grid, block, 0, s>>>(a);
     } else {
-        if (first) level_split_kernel<LB, VL, TS, false, true, false, FAST><<<grid, block, 0, s>>>(a);
-        else if (last) level_split_kernel<LB, VL, TS, false, false, true, FAST><<<grid, block, 0, s>>>(a);
-        else level_split_kernel<LB, VL, TS, false, false, false, FAST><<<grid, block, 0, s>>>(a);
+        if (first) level_split_kernel<LB, VL, TS, false, true, false, FAST, WPC><<<grid, block, 0, s>>>(a);
+        else if (last) level_split_kernel<LB, VL, TS, false, false, true, FAST, WPC><<<grid, block, 0, s>>>(a);
+        else level_split_kernel<LB, VL, TS, false, false, false, FAST, WPC><<<grid, block, 0, s>>>(a);
     }
     return cudaGetLastError();
 }
 
 template <int LB, int VL, typename TS>
 static cudaError_t level_split_t(bool has_up, const LevelArgs& a, cudaStream_t s) {
-    constexpr int G = 32 / (LB / VL);
     if (a.rays == 0) return cudaSuccess;
-    const long long per_cta = (long long)G * kWarpsPerCta;
-    const dim3 grid((unsigned)((a.rays + per_cta - 1) / per_cta), (unsigned)a.split_nblk);
     const bool fast = a.Wshift >= 0 && !a.probe_list;
-    if (fast) return split_phase<LB, VL, TS, true>(has_up, a, grid, s);
-    return split_phase<LB, VL, TS, false>(has_up, a, grid, s);
+    const bool wide = a.n_strips >= kSplitWideFrom;
+    if (fast && wide) return split_phase<LB, VL, TS, true, kSplitWideWarps>(has_up, a, s);
+    if (fast) return split_phase<LB, VL, TS, true, kWarpsPerCta>(has_up, a, s);
+    if (wide) return split_phase<LB, VL, TS, false, kSplitWideWarps>(has_up, a, s);
+    return split_phase<LB, VL, TS, false, kWarpsPerCta>(has_up, a, s);
 }
 
 template <int LB, int VL>
